@@ -1,0 +1,219 @@
+/*
+ * muffin.h -- C ABI of the GB300 (sm_103a) MUFFIN library.
+ *
+ * MUFFIN (Ammanouil, Ferrari, Mary, Ferrari, Loi 2019) restores a
+ * multispectral sky cube X (L bands of n x n pixels) from dirty images
+ * Y = H X* + W by minimising (Eqs. probopt, RegAll)
+ *
+ *   sum_l 1/2 ||y_l - H_l x_l||^2 + 1_{R+}(X)
+ *       + sum_l mu_l ||W_s x_l||_1 + sum_n gamma_n ||W_lambda x^n||_1
+ *
+ * with the primal-dual (Vu-Condat) iteration of Algorithm 2, and tunes the
+ * two regularisation weights (mu, gamma) online with ADA-PT (Algorithm 5):
+ * SUGAR-FDMC gradients (Eq. SUGAR) of the PSURE-FDMC risk (Eq. PSURE0) from
+ * the derivative iterates of Algorithms 3 and 4.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Cubes are float32, band-major, row-major: element (l, y, x) at
+ *   l*n*n + y*n + x.  H_l is the circular convolution by psf_l with the PSF
+ *   origin at pixel (0, 0) (Eq. model).  W_s is the unscaled union of the
+ *   periodised orthonormal Daubechies bases db1..dbK with J levels (Sec.
+ *   4.2.1); W_lambda is the orthonormal DCT-II along bands.
+ * - mu_l = mu * beta_l and gamma_n = gamma * alpha_n (Eq. 2regpar).
+ * - Array arguments may live in host memory or in device memory of the
+ *   plan's device; the library detects which (cudaPointerGetAttributes).
+ *   Host arrays are copied in and out synchronously inside the call.
+ *   Device arrays are read/written on the plan's stream.
+ * - The caller owns every array it passes; the plan owns its internal state
+ *   (primal/dual iterates, spectra, scratch) and frees it in
+ *   muffin_plan_destroy.
+ * - Every call returns a status; on failure muffin_last_error() describes
+ *   it.  After MUFFIN_ECUDA the plan must be destroyed.  Calls are
+ *   synchronous (the plan's stream is synchronised before returning), and a
+ *   plan must not be used from two threads at once.
+ */
+#ifndef MUFFIN_H
+#define MUFFIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MUFFIN_API __attribute__((visibility("default")))
+#else
+#define MUFFIN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct muffin_plan_s *muffin_plan;
+
+typedef enum {
+  MUFFIN_OK = 0,
+  MUFFIN_EINVAL = 1,   /* invalid argument or shape */
+  MUFFIN_ENOMEM = 2,   /* device or host allocation failed */
+  MUFFIN_ECUDA = 3,    /* CUDA runtime error; destroy the plan */
+  MUFFIN_ETIMEOUT = 4, /* a bounded device wait gave up */
+  MUFFIN_ENUMERIC = 5, /* NaN/Inf detected in the state */
+  MUFFIN_ESTATE = 6    /* call not valid in the plan's current state */
+} muffin_status;
+
+/* Plan parameters (Sec. 2.2 step condition, Sec. 4.2.1 settings). */
+typedef struct {
+  int32_t n;          /* image side, power of two, 2 <= n <= 2048 */
+  int32_t nbands;     /* L >= 1 */
+  int32_t n_wavelets; /* K in 1..8: W_s = [db1; ...; dbK] (default 8) */
+  int32_t levels;     /* J >= 0 with 2^J <= n (default 3); 0 = identity bases */
+  double sigma;       /* dual step sigma > 0 (default 10, Sec. 4.2.1) */
+  int32_t step_rule;  /* 0: tau from the paper's sum form (default);
+                         1: from ||L||^2 = K max mu_l^2 + max gamma_n^2 */
+  double tau_safety;  /* tau = safety / (beta/2 + sigma ||L||^2), default 0.99 */
+  int32_t positivity; /* 1 (default): projection of Eq. projpos; 0 skips it */
+  int32_t sure;       /* 1: also allocate the ADA-PT chains (needed by
+                         muffin_sure_tune); 0: plain MUFFIN only */
+} muffin_params;
+
+/* Fill *p with the defaults above for an n x n x nbands cube. */
+MUFFIN_API void muffin_params_default(muffin_params *p, int32_t n, int32_t nbands);
+
+/*
+ * Create a plan: validates p, allocates the device state, computes the PSF
+ * spectra h_hat_l = F psf_l (FP64), beta = max_l ||H_l||^2 =
+ * max_{l,k} |h_hat_l(k)|^2 (the Lipschitz constant of the least-squares
+ * gradient, Sec. 2.2), the Daubechies filters and the DCT-II tables.
+ *   psf   [L][n][n] float32, host or device; read during the call only.
+ *   alpha [n*n] pixel weights alpha_n, or NULL for all ones (Eq. 2regpar).
+ *   beta  [L]   band weights beta_l, or NULL for all ones.
+ *   stream  a cudaStream_t (NULL = legacy default stream) used for all work.
+ * Errors: EINVAL (shape, NULL out, PSF all zero), ENOMEM, ECUDA.
+ */
+MUFFIN_API muffin_status muffin_plan_create(const muffin_params *p, const float *psf,
+                                 const float *alpha, const float *beta,
+                                 void *stream, muffin_plan *out);
+
+MUFFIN_API void muffin_plan_destroy(muffin_plan plan);
+
+/* Device bytes held by the plan (state + scratch). */
+MUFFIN_API size_t muffin_plan_device_bytes(muffin_plan plan);
+
+/* beta = max_l ||H_l||^2 computed at plan creation (FP64). */
+MUFFIN_API muffin_status muffin_plan_lipschitz(muffin_plan plan, double *beta);
+
+typedef struct {
+  int32_t iters_done; /* iterations run by this call */
+  double tau;         /* primal step used (last window for ADA-PT) */
+  double sigma;       /* dual step */
+  double lipschitz;   /* beta */
+  double mu, gamma;   /* regularisation weights at the end of the call */
+  int32_t records;    /* ADA-PT trace records written by this call */
+} muffin_info;
+
+#define MUFFIN_WARM 1 /* continue from the plan's current state (x ignored
+                         on input; dirty may be NULL to keep the last one) */
+
+/*
+ * Plain MUFFIN: run `iters` iterations of Algorithm 2 with fixed (mu, gamma).
+ *   dirty [L][n][n] dirty cube y (NULL with MUFFIN_WARM: keep the last one).
+ *   x     [L][n][n] in: X0 (ignored with MUFFIN_WARM), out: X after iters.
+ *   Without MUFFIN_WARM the duals start at U = V = T = 0.
+ *   tau is derived from (mu, gamma) by the plan's step rule.
+ *   info  optional (NULL allowed).
+ * Errors: EINVAL (iters < 0, NULL x, NULL dirty without warm state, negative
+ * mu/gamma), ECUDA.
+ */
+MUFFIN_API muffin_status muffin_solve(muffin_plan plan, const float *dirty, float *x,
+                           int32_t iters, double mu, double gamma,
+                           int32_t flags, muffin_info *info);
+
+/* ADA-PT settings (Algorithm 5, Eq. adaptgrad). */
+typedef struct {
+  int32_t iters;             /* ADA-PT iterations (all 6 chains advance) */
+  int32_t window;            /* Delta: theta is updated after every Delta
+                                completed iterations (default 10) */
+  double eta_mu, eta_gamma;  /* gradient steps for mu and gamma */
+  double theta_min;          /* lower clamp of mu and gamma (default 1e-8) */
+  int32_t reset_each_window; /* 1 (default): derivative iterates restart at
+                                0 at every window; 0 carries them over */
+  double eps;                /* FDMC step epsilon > 0 (Eq. PSURE0) */
+} muffin_sure_params;
+
+MUFFIN_API void muffin_sure_params_default(muffin_sure_params *s);
+
+/* One record per theta update. */
+typedef struct {
+  int32_t k;                   /* completed iterations at the update */
+  double mu, gamma;            /* theta used during the window */
+  double sugar_mu, sugar_gamma;/* Eq. SUGAR summed over bands */
+  double psure;                /* Eq. PSURE (per-band noise variances) */
+  double tau;                  /* tau used during the window */
+} muffin_sure_record;
+
+/*
+ * ADA-PT'ed MUFFIN (Algorithm 5): advances the primal chain on y, the
+ * primal chain on y_bar = y + eps*delta and the four derivative chains
+ * dX/dmu, dX/dgamma, dXbar/dmu, dXbar/dgamma (Algorithms 3, 4) in lockstep;
+ * after every `window` iterations computes SUGAR, updates
+ * theta <- max(theta - eta * SUGAR, theta_min), recomputes tau and restarts
+ * the derivative iterates.
+ *   dirty     [L][n][n] y.   delta [L][n][n] N(0,1) probe.
+ *   noise_var [L] host array, sigma_l^2 of each band.
+ *   x         [L][n][n] in: X0 for both primal chains (ignored with
+ *             MUFFIN_WARM), out: X of the chain on y.
+ *   theta     host double[2] in: (mu, gamma), out: tuned (mu, gamma).
+ *   trace     host array of iters/window records, or NULL.
+ * The plan must have been created with p.sure = 1.
+ * Errors: EINVAL, ESTATE (plan without SURE chains), ECUDA.
+ */
+MUFFIN_API muffin_status muffin_sure_tune(muffin_plan plan, const float *dirty,
+                               const float *delta, const double *noise_var,
+                               const muffin_sure_params *sp, float *x,
+                               double *theta, muffin_sure_record *trace,
+                               int32_t flags, muffin_info *info);
+
+/* ---- checkpoint / resume ------------------------------------------------
+ * The state blob holds the iterates (X, U, V, T of every chain), the
+ * dirty-cube terms and theta; importing it into a plan created with the
+ * same parameters and PSF continues bit-identically (MUFFIN_WARM calls). */
+MUFFIN_API muffin_status muffin_state_size(muffin_plan plan, size_t *bytes);
+MUFFIN_API muffin_status muffin_state_export(muffin_plan plan, void *host_buf,
+                                  size_t bytes);
+MUFFIN_API muffin_status muffin_state_import(muffin_plan plan, const void *host_buf,
+                                  size_t bytes);
+
+/* ---- single operators, for checking the kernels one by one -------------
+ * All cubes [L][n][n] unless stated; coefficients [L][K][n][n] in the Mallat
+ * layout of each basis.  They use the same kernels as the iteration. */
+
+/* g = H_l^T (H_l x_l - y_l) per band when dirty != NULL, else H_l^T H_l x_l
+ * (Alg. 2 eq. grad2). */
+MUFFIN_API muffin_status muffin_op_gradient(muffin_plan plan, const float *x,
+                                 const float *dirty, float *g);
+/* u = W_s x (analysis over the K bases). */
+MUFFIN_API muffin_status muffin_op_analysis(muffin_plan plan, const float *x, float *u);
+/* x = W_s^T u (synthesis summed over the K bases). */
+MUFFIN_API muffin_status muffin_op_synthesis(muffin_plan plan, const float *u, float *x);
+/* v^n = C x^n for every pixel (inverse = 0) or x^n = C^T v^n (inverse = 1),
+ * C the orthonormal DCT-II (3xTF32 tensor-core products). */
+MUFFIN_API muffin_status muffin_op_dct(muffin_plan plan, const float *x, float *v,
+                            int32_t inverse);
+
+/* ---- host-only tables (no GPU needed) -----------------------------------
+ * The FP64 tables the kernels are built from, for inspection and tests. */
+/* h[0 .. 2p-1]: db<p> scaling filter by spectral factorisation, 1 <= p <= 8. */
+MUFFIN_API muffin_status muffin_filter_taps(int32_t p, double *h);
+/* C[k*L + l]: orthonormal DCT-II matrix, L >= 1. */
+MUFFIN_API muffin_status muffin_dct_table(int32_t L, double *C);
+
+/* Thread-local description of the last error (never NULL). */
+MUFFIN_API const char *muffin_last_error(void);
+
+/* Library version string. */
+MUFFIN_API const char *muffin_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUFFIN_H */

@@ -1,0 +1,185 @@
+"""MUFFIN multispectral deconvolution with ADA-PT tuning on GB300 (sm_103a).
+
+Python binding of the C ABI in ``include/muffin.h``: argument marshalling
+only, every step of the iteration runs in ``libmuffin.so``.  Arrays may be
+CUDA torch tensors (used in place, on the current torch stream) or host
+arrays (numpy or CPU tensors, copied by the library inside the call); all
+cubes are float32 ``[L, n, n]``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import native
+from .native import MUFFIN_WARM, MuffinError, SureRecord
+
+__all__ = ["Plan", "MuffinError", "filter_taps", "dct_table", "library"]
+
+
+def library():
+    return native.load()
+
+
+def _ptr(a, keep: list, dtype=np.float32):
+    """Raw pointer of a contiguous float32 array (torch tensor or numpy)."""
+    if a is None:
+        return None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float32 or not a.is_contiguous():
+                raise TypeError("tensors must be contiguous float32")
+            keep.append(a)
+            return ctypes.c_void_p(a.data_ptr())
+    except ImportError:
+        pass
+    arr = np.asarray(a)
+    if arr.dtype != dtype or not arr.flags.c_contiguous:
+        raise TypeError(f"arrays must be C-contiguous {np.dtype(dtype).name}")
+    keep.append(arr)
+    return ctypes.c_void_p(arr.ctypes.data)
+
+
+def _stream_handle():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def filter_taps(p: int) -> np.ndarray:
+    """db<p> scaling filter as built by the library (host FP64)."""
+    h = (ctypes.c_double * (2 * p))()
+    native.check(library().muffin_filter_taps(p, h))
+    return np.array(h[:], dtype=np.float64)
+
+
+def dct_table(L: int) -> np.ndarray:
+    C = (ctypes.c_double * (L * L))()
+    native.check(library().muffin_dct_table(L, C))
+    return np.array(C[:], dtype=np.float64).reshape(L, L)
+
+
+class Plan:
+    """A MUFFIN plan for L bands of n x n pixels (see ``muffin_plan_create``)."""
+
+    def __init__(self, n: int, nbands: int, psf, *, n_wavelets: int = 8,
+                 levels: int = 3, sigma: float = 10.0, step_rule: int = 0,
+                 tau_safety: float = 0.99, positivity: bool = True,
+                 sure: bool = False, alpha=None, beta=None, stream=None):
+        lib = library()
+        self._lib = lib
+        self.n, self.L, self.K = n, nbands, n_wavelets
+        p = native.Params()
+        lib.muffin_params_default(ctypes.byref(p), n, nbands)
+        p.n_wavelets, p.levels, p.sigma = n_wavelets, levels, sigma
+        p.step_rule, p.tau_safety = step_rule, tau_safety
+        p.positivity, p.sure = int(positivity), int(sure)
+        keep = []
+        handle = ctypes.c_void_p()
+        st = stream if stream is not None else _stream_handle()
+        native.check(lib.muffin_plan_create(
+            ctypes.byref(p), _ptr(psf, keep), _ptr(alpha, keep), _ptr(beta, keep),
+            st, ctypes.byref(handle)))
+        self._h = handle
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.muffin_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- queries
+    @property
+    def device_bytes(self) -> int:
+        return int(self._lib.muffin_plan_device_bytes(self._h))
+
+    @property
+    def lipschitz(self) -> float:
+        b = ctypes.c_double()
+        native.check(self._lib.muffin_plan_lipschitz(self._h, ctypes.byref(b)))
+        return b.value
+
+    # -- solvers
+    def solve(self, dirty, x, iters: int, mu: float, gamma: float,
+              warm: bool = False) -> native.Info:
+        keep, info = [], native.Info()
+        native.check(self._lib.muffin_solve(
+            self._h, _ptr(dirty, keep), _ptr(x, keep), int(iters), float(mu),
+            float(gamma), MUFFIN_WARM if warm else 0, ctypes.byref(info)))
+        return info
+
+    def sure_tune(self, dirty, delta, noise_var, x, theta, iters: int, *,
+                  window: int = 10, eta=(1e-3, 1e-3), theta_min: float = 1e-8,
+                  reset: bool = True, eps: float, warm: bool = False):
+        """Returns (theta, trace, info); trace is a list of dicts per window."""
+        keep = []
+        sp = native.SureParams()
+        self._lib.muffin_sure_params_default(ctypes.byref(sp))
+        sp.iters, sp.window = int(iters), int(window)
+        sp.eta_mu, sp.eta_gamma = float(eta[0]), float(eta[1])
+        sp.theta_min, sp.reset_each_window, sp.eps = theta_min, int(reset), float(eps)
+        th = (ctypes.c_double * 2)(float(theta[0]), float(theta[1]))
+        nrec = max(1, int(iters) // int(window) + 1)
+        rec = (SureRecord * nrec)()
+        nv = None
+        if noise_var is not None:
+            nv_arr = np.ascontiguousarray(noise_var, dtype=np.float64)
+            keep.append(nv_arr)
+            nv = ctypes.c_void_p(nv_arr.ctypes.data)
+        info = native.Info()
+        native.check(self._lib.muffin_sure_tune(
+            self._h, _ptr(dirty, keep), _ptr(delta, keep), nv, ctypes.byref(sp),
+            _ptr(x, keep), th, rec, MUFFIN_WARM if warm else 0, ctypes.byref(info)))
+        trace = [dict(k=r.k, mu=r.mu, gamma=r.gamma, sugar_mu=r.sugar_mu,
+                      sugar_gamma=r.sugar_gamma, psure=r.psure, tau=r.tau)
+                 for r in rec[: info.records]]
+        return (th[0], th[1]), trace, info
+
+    # -- checkpoints
+    def state_export(self) -> bytes:
+        sz = ctypes.c_size_t()
+        native.check(self._lib.muffin_state_size(self._h, ctypes.byref(sz)))
+        buf = ctypes.create_string_buffer(sz.value)
+        native.check(self._lib.muffin_state_export(self._h, buf, sz.value))
+        return buf.raw
+
+    def state_import(self, blob: bytes) -> None:
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        native.check(self._lib.muffin_state_import(self._h, buf, len(blob)))
+
+    # -- single operators
+    def op_gradient(self, x, g, dirty=None):
+        keep = []
+        native.check(self._lib.muffin_op_gradient(
+            self._h, _ptr(x, keep), _ptr(dirty, keep), _ptr(g, keep)))
+
+    def op_analysis(self, x, u):
+        keep = []
+        native.check(self._lib.muffin_op_analysis(self._h, _ptr(x, keep), _ptr(u, keep)))
+
+    def op_synthesis(self, u, x):
+        keep = []
+        native.check(self._lib.muffin_op_synthesis(self._h, _ptr(u, keep), _ptr(x, keep)))
+
+    def op_dct(self, x, v, inverse: bool = False):
+        keep = []
+        native.check(self._lib.muffin_op_dct(self._h, _ptr(x, keep), _ptr(v, keep),
+                                             int(inverse)))

@@ -1,0 +1,240 @@
+// Spectral step of Algorithm 2 (eqs. vt, v, upt), run for every pixel n:
+//     v~ = v + sigma gamma_n C (2 x~^n - x^n);   v = sat(v~);   t = gamma_n C^T v
+// with C the orthonormal L x L DCT-II (Sec. 4.2.1).  Over a tile of PT pixels
+// both products are dense [L x L] x [L x PT] contractions, run on the tensor
+// cores as 3xTF32 split products (a_hi b_hi + a_hi b_lo + a_lo b_hi, FP32
+// accumulation), which keeps FP32 accuracy.  C is pre-split on the host; the
+// B operand is split in registers.
+//
+// ADA-PT groups (C = 3 chains) reuse the primal's mask Pi(v~) and add the
+// inhomogeneous terms of Algorithm 4:
+//     v~'_gamma = v'_gamma + sigma alpha_n C (2x~ - x + gamma (2x~' - x'))
+//     t'_gamma  = alpha_n C^T (gamma v'_gamma + v)
+// while Algorithm 3's spectral step is the homogeneous one.
+//
+// Layout: every cube is band-major [L][N], so the tile [L x PT] is PT
+// consecutive pixels of each band (coalesced rows); the band<->pixel
+// "exchange" of the paper's master/slave split becomes this access pattern.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.h"
+
+namespace muffin {
+
+namespace {
+
+constexpr int DT = 128;   // threads (4 warps)
+
+__device__ __forceinline__ uint32_t to_tf32(float f) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4],
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+struct DctKArgs {
+  int n, L, Lp, inverse;
+  const float *a1hi, *a1lo;   // first product: C (or C^T for the inverse operator)
+  const float *a2hi, *a2lo;   // second product: C^T
+  const float *alpha;
+  const DevScalars *sc;
+  const float *xt, *x;        // iterate inputs [C][L][N]
+  float *v, *t;               // iterate state [C][L][N]
+  const float *in;            // operator input [L][N]
+  float *out;                 // operator output [L][N]
+};
+
+// acc[nt][e] (e: c0..c3) = sum_k A[m0 + row(e)][k] * B[k][nt*8 + col(e)]
+template <int PT>
+__device__ __forceinline__ void tile_gemm(const float *__restrict__ Ahi,
+                                          const float *__restrict__ Alo, int Lp,
+                                          int m0, const float *B, int PP,
+                                          float (&acc)[PT / 8][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < PT / 8; ++nt)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+  for (int k0 = 0; k0 < Lp; k0 += 8) {
+    uint32_t ah[4], al[4];
+    const int r0 = (m0 + g) * Lp + k0 + t, r1 = (m0 + g + 8) * Lp + k0 + t;
+    ah[0] = __float_as_uint(__ldg(Ahi + r0));
+    ah[1] = __float_as_uint(__ldg(Ahi + r1));
+    ah[2] = __float_as_uint(__ldg(Ahi + r0 + 4));
+    ah[3] = __float_as_uint(__ldg(Ahi + r1 + 4));
+    al[0] = __float_as_uint(__ldg(Alo + r0));
+    al[1] = __float_as_uint(__ldg(Alo + r1));
+    al[2] = __float_as_uint(__ldg(Alo + r0 + 4));
+    al[3] = __float_as_uint(__ldg(Alo + r1 + 4));
+    const float *b0p = B + (k0 + t) * PP + g;
+    const float *b1p = B + (k0 + t + 4) * PP + g;
+#pragma unroll
+    for (int nt = 0; nt < PT / 8; ++nt) {
+      const float f0 = b0p[nt * 8], f1 = b1p[nt * 8];
+      const uint32_t h0 = to_tf32(f0), h1 = to_tf32(f1);
+      const uint32_t l0 = to_tf32(f0 - __uint_as_float(h0));
+      const uint32_t l1 = to_tf32(f1 - __uint_as_float(h1));
+      mma_tf32(acc[nt], al, h0, h1);
+      mma_tf32(acc[nt], ah, l0, l1);
+      mma_tf32(acc[nt], ah, h0, h1);
+    }
+  }
+}
+
+template <int CH, int MODE, int PT>
+__global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
+  extern __shared__ float sm[];
+  constexpr int PP = PT + 8;
+  const int Lp = a.Lp, L = a.L;
+  float *zin = sm;                       // [CH][Lp][PP]
+  float *vo = zin + CH * Lp * PP;        // [CH][Lp][PP]
+  const size_t N = (size_t)a.n * a.n;
+  const size_t CS = (size_t)L * N;
+  const size_t n0 = (size_t)blockIdx.x * PT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const float gamma = (MODE == WAVE_ITERATE) ? (float)a.sc->gamma : 0.f;
+  const float sigma = (MODE == WAVE_ITERATE) ? (float)a.sc->sigma : 0.f;
+
+  for (int it = threadIdx.x; it < Lp * PT; it += DT) {
+    const int l = it / PT, p = it - l * PT;
+    const size_t pix = n0 + p;
+    const bool ok = l < L && pix < N;
+    const size_t j = (size_t)l * N + pix;
+    float z[CH];
+    if (MODE == WAVE_TRANSFORM) {
+      z[0] = ok ? a.in[j] : 0.f;
+    } else {
+#pragma unroll
+      for (int c = 0; c < CH; ++c) z[c] = ok ? 2.f * a.xt[c * CS + j] - a.x[c * CS + j] : 0.f;
+      if (CH == 3) z[2] = fmaf(gamma, z[2], z[0]);   // Algorithm 4 input
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) zin[(c * Lp + l) * PP + p] = z[c];
+  }
+  __syncthreads();
+
+  const int nmt = Lp >> 4;
+  for (int mt = warp; mt < nmt; mt += DT / 32) {
+    uint32_t mask = 0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      float acc[PT / 8][4];
+      tile_gemm<PT>(a.a1hi, a.a1lo, Lp, mt * 16, zin + c * Lp * PP, PP, acc);
+#pragma unroll
+      for (int nt = 0; nt < PT / 8; ++nt) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = mt * 16 + g + (e >= 2 ? 8 : 0);
+          const int p = nt * 8 + 2 * t + (e & 1);
+          const size_t pix = n0 + p;
+          const bool valid = k < L && pix < N;
+          const size_t j = (size_t)k * N + pix;
+          if (MODE == WAVE_TRANSFORM) {
+            if (valid) a.out[j] = acc[nt][e];
+            continue;
+          }
+          float vn = 0.f;
+          if (valid) {
+            const float al = a.alpha[pix];
+            const float s1 = (c == 2) ? sigma * al : sigma * gamma * al;
+            const float vt = fmaf(s1, acc[nt][e], a.v[c * CS + j]);
+            if (c == 0) {
+              vn = satf(vt);
+              if (fabsf(vt) <= 1.f) mask |= 1u << (nt * 4 + e);
+            } else {
+              vn = ((mask >> (nt * 4 + e)) & 1u) ? vt : 0.f;
+            }
+            a.v[c * CS + j] = vn;
+          }
+          vo[(c * Lp + k) * PP + p] = vn;
+        }
+      }
+    }
+  }
+  if (MODE == WAVE_TRANSFORM) return;
+  __syncthreads();
+  if (CH == 3) {
+    for (int it = threadIdx.x; it < Lp * PT; it += DT) {
+      const int l = it / PT, p = it - l * PT;
+      float *d = vo + (2 * Lp + l) * PP + p;
+      *d = fmaf(gamma, *d, vo[l * PP + p]);     // gamma v'_gamma + v
+    }
+    __syncthreads();
+  }
+  for (int mt = warp; mt < nmt; mt += DT / 32) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      float acc[PT / 8][4];
+      tile_gemm<PT>(a.a2hi, a.a2lo, Lp, mt * 16, vo + c * Lp * PP, PP, acc);
+#pragma unroll
+      for (int nt = 0; nt < PT / 8; ++nt) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int l = mt * 16 + g + (e >= 2 ? 8 : 0);
+          const int p = nt * 8 + 2 * t + (e & 1);
+          const size_t pix = n0 + p;
+          if (l < L && pix < N) {
+            const float al = a.alpha[pix];
+            const float s2 = (c == 2) ? al : gamma * al;
+            a.t[c * CS + (size_t)l * N + pix] = s2 * acc[nt][e];
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int CH, int MODE, int PT>
+cudaError_t launch_dct(const DctKArgs &a, cudaStream_t st) {
+  const size_t sm = (size_t)2 * CH * a.Lp * (PT + 8) * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dct<CH, MODE, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr = true;
+  }
+  const size_t N = (size_t)a.n * a.n;
+  k_dct<CH, MODE, PT><<<(unsigned)((N + PT - 1) / PT), DT, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int CH, int MODE>
+cudaError_t launch_dct_pt(const DctKArgs &a, cudaStream_t st) {
+  // largest pixel tile whose two [CH][Lp][PT+8] buffers fit in ~160 KB
+  const size_t per32 = (size_t)2 * CH * a.Lp * 40 * sizeof(float);
+  if (per32 <= 160 * 1024) return launch_dct<CH, MODE, 32>(a, st);
+  return launch_dct<CH, MODE, 16>(a, st);
+}
+
+}  // namespace
+
+cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st) {
+  DctKArgs a{};
+  a.n = d.n; a.L = d.L; a.Lp = d.Lp;
+  a.a1hi = d.chi; a.a1lo = d.clo; a.a2hi = d.cthi; a.a2lo = d.ctlo;
+  a.alpha = d.alpha; a.sc = d.sc;
+  a.xt = gr.xt; a.x = gr.x; a.v = gr.v; a.t = gr.t;
+  if (gr.C == 3) return launch_dct_pt<3, WAVE_ITERATE>(a, st);
+  return launch_dct_pt<1, WAVE_ITERATE>(a, st);
+}
+
+cudaError_t dct_op(const DctArgs &d, const float *in, float *out, int inverse,
+                   cudaStream_t st) {
+  DctKArgs a{};
+  a.n = d.n; a.L = d.L; a.Lp = d.Lp; a.inverse = inverse;
+  a.a1hi = inverse ? d.cthi : d.chi;
+  a.a1lo = inverse ? d.ctlo : d.clo;
+  a.in = in; a.out = out;
+  return launch_dct_pt<1, WAVE_TRANSFORM>(a, st);
+}
+
+}  // namespace muffin

@@ -1,0 +1,256 @@
+// Least-squares gradient H_l^T (H_l x_l - y_l) of Algorithm 2 (eq. grad2)
+// and H_l^T H_l x'_l of Algorithms 3/4, by 2D FFT (Eq. model read as a
+// circular convolution).  Since H_l^T H_l = F^-1 diag(|h_hat_l|^2) F and
+// b_l = H_l^T y_l is fixed per call, the hot path computes
+//     g = F^-1 ( |h_hat|^2 . F x ) - b
+// in three FP32 passes over the cube:
+//   1. rows:    pairs of real rows packed as one complex row, FFT, split into
+//               the two half spectra (n/2+1 bins), stored kx-major ("columns
+//               contiguous") so that pass 2 reads whole columns;
+//   2. columns: forward FFT of each column, multiply by |h_hat|^2 / n^2,
+//               inverse FFT, in place;
+//   3. rows:    rebuild the Hermitian row spectra of two rows at a time,
+//               inverse FFT, subtract b, store.
+// The FP64 2D transform at the bottom is used only when a plan or call is
+// set up (PSF spectra, H^T y, H^T delta).
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace muffin {
+
+namespace {
+
+constexpr int kRowBlock = 8;   // rows per CTA in passes 1 and 3 (even)
+constexpr int kColBlock = 4;   // columns per CTA in pass 2
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads)
+k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S, int n, int RB,
+           const float2 *__restrict__ tw) {
+  extern __shared__ float2 sm2[];
+  const int img = blockIdx.y;
+  const int y0 = blockIdx.x * RB;
+  const int nq = RB >> 1, nh = (n >> 1) + 1;
+  float2 *a = sm2, *b = sm2 + nq * n;
+  const float *xi = x + (size_t)img * n * n + (size_t)y0 * n;
+  for (int i = threadIdx.x; i < nq * n; i += blockDim.x) {
+    const int q = i / n, col = i - q * n;
+    a[i] = make_float2(xi[(2 * q) * n + col], xi[(2 * q + 1) * n + col]);
+  }
+  __syncthreads();
+  const float2 *r = fft_batch<float2, false>(a, b, n, nq, tw);
+  float4 *Si = reinterpret_cast<float4 *>(S + (size_t)img * nh * n);
+  for (int i = threadIdx.x; i < nh * nq; i += blockDim.x) {
+    const int k = i / nq, q = i - k * nq;
+    const float2 Z = r[q * n + k], Zc = r[q * n + ((n - k) & (n - 1))];
+    // row 2q: (Z + conj Zc)/2 ; row 2q+1: (Z - conj Zc)/(2i)
+    float4 o;
+    o.x = 0.5f * (Z.x + Zc.x);
+    o.y = 0.5f * (Z.y - Zc.y);
+    o.z = 0.5f * (Z.y + Zc.y);
+    o.w = 0.5f * (Zc.x - Z.x);
+    Si[((size_t)k * n + y0 + 2 * q) >> 1] = o;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_cols(float2 *__restrict__ S, const float *__restrict__ kspec, int n, int L,
+       int CB, const float2 *__restrict__ tw) {
+  extern __shared__ float2 sm2[];
+  const int img = blockIdx.y, band = img % L;
+  const int nh = (n >> 1) + 1;
+  const int k0 = blockIdx.x * CB;
+  const int ncol = min(CB, nh - k0);
+  float2 *a = sm2, *b = sm2 + CB * n;
+  float2 *Si = S + ((size_t)img * nh + k0) * n;
+  const float *Ki = kspec + ((size_t)band * nh + k0) * n;
+  for (int i = threadIdx.x; i < ncol * n; i += blockDim.x) a[i] = Si[i];
+  __syncthreads();
+  float2 *r = fft_batch<float2, false>(a, b, n, ncol, tw);
+  for (int i = threadIdx.x; i < ncol * n; i += blockDim.x) {
+    const float kk = __ldg(Ki + i);
+    r[i].x *= kk;
+    r[i].y *= kk;
+  }
+  __syncthreads();
+  r = fft_batch<float2, true>(r, r == a ? b : a, n, ncol, tw);
+  for (int i = threadIdx.x; i < ncol * n; i += blockDim.x) Si[i] = r[i];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_rows_inv(const float2 *__restrict__ S, float *__restrict__ g,
+           const float *__restrict__ bdata, int n, int L, int RB,
+           const float2 *__restrict__ tw) {
+  extern __shared__ float2 sm2[];
+  const int img = blockIdx.y, band = img % L;
+  const int y0 = blockIdx.x * RB;
+  const int nq = RB >> 1, nh = (n >> 1) + 1, half = n >> 1;
+  float2 *a = sm2, *b = sm2 + nq * n;
+  const float4 *Si = reinterpret_cast<const float4 *>(S + (size_t)img * nh * n);
+  for (int i = threadIdx.x; i < nh * nq; i += blockDim.x) {
+    const int k = i / nq, q = i - k * nq;
+    float4 v = Si[((size_t)k * n + y0 + 2 * q) >> 1];   // Xa = (x,y), Xb = (z,w)
+    if (k == 0 || k == half) { v.y = 0.f; v.w = 0.f; }
+    a[q * n + k] = make_float2(v.x - v.w, v.y + v.z);    // Xa + i Xb
+    if (k > 0 && k < half)
+      a[q * n + n - k] = make_float2(v.x + v.w, v.z - v.y);  // conj Xa + i conj Xb
+  }
+  __syncthreads();
+  const float2 *r = fft_batch<float2, true>(a, b, n, nq, tw);
+  const bool sub = (bdata != nullptr) && (img < L);
+  float *gi = g + (size_t)img * n * n + (size_t)y0 * n;
+  const float *bi = sub ? bdata + (size_t)band * n * n + (size_t)y0 * n : nullptr;
+  for (int i = threadIdx.x; i < nq * n; i += blockDim.x) {
+    const int q = i / n, col = i - q * n;
+    const float2 z = r[i];
+    float v0 = z.x, v1 = z.y;
+    if (sub) {
+      v0 -= __ldg(bi + (2 * q) * n + col);
+      v1 -= __ldg(bi + (2 * q + 1) * n + col);
+    }
+    gi[(2 * q) * n + col] = v0;
+    gi[(2 * q + 1) * n + col] = v1;
+  }
+}
+
+// ---------------------------------------------------------------- FP64 set-up
+__global__ void k_fft64_rows(double2 *data, int n, bool inverse,
+                             const double2 *__restrict__ tw) {
+  extern __shared__ double2 sm4[];
+  double2 *a = sm4, *b = sm4 + n;
+  double2 *row = data + ((size_t)blockIdx.y * n + blockIdx.x) * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = row[i];
+  __syncthreads();
+  const double2 *r = inverse ? fft_batch<double2, true>(a, b, n, 1, tw)
+                             : fft_batch<double2, false>(a, b, n, 1, tw);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) row[i] = r[i];
+}
+
+__global__ void k_transpose64(const double2 *__restrict__ in,
+                              double2 *__restrict__ out, int n) {
+  __shared__ double2 tile[32][33];
+  const size_t base = (size_t)blockIdx.z * n * n;
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int y = by + j, x = bx + threadIdx.x;
+    if (y < n && x < n) tile[j][threadIdx.x] = in[base + (size_t)y * n + x];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+    const int y = bx + j, x = by + threadIdx.x;
+    if (y < n && x < n) out[base + (size_t)y * n + x] = tile[threadIdx.x][j];
+  }
+}
+
+__global__ void k_real_to_c64(const float *__restrict__ in,
+                              double2 *__restrict__ out, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = make_double2((double)in[i], 0.0);
+}
+
+__global__ void k_mul_conj_c64(double2 *__restrict__ a,
+                               const double2 *__restrict__ h, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    a[i] = cmulc(a[i], h[i]);
+}
+
+__global__ void k_c64_real_to_f32(const double2 *__restrict__ in,
+                                  float *__restrict__ out, double scale,
+                                  size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)(in[i].x * scale);
+}
+
+__global__ void k_make_kspec(const double2 *__restrict__ hh,
+                             float *__restrict__ kspec, double scale, int n,
+                             int L) {
+  const int nh = (n >> 1) + 1;
+  const size_t total = (size_t)L * nh * n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int ky = (int)(i % n);
+    const size_t r = i / n;
+    const int kx = (int)(r % nh);
+    const int l = (int)(r / nh);
+    const double2 h = hh[((size_t)l * n + ky) * n + kx];
+    kspec[i] = (float)((h.x * h.x + h.y * h.y) * scale);
+  }
+}
+
+inline int grid_for(size_t count) {
+  size_t g = (count + 255) / 256;
+  return (int)(g > 152 * 32 ? 152 * 32 : (g ? g : 1));
+}
+
+}  // namespace
+
+cudaError_t launch_gradient(const float *x, float *g, const float *b,
+                            float2 *S, const float *kspec, const float2 *tw,
+                            int n, int L, int C, cudaStream_t st) {
+  const int nimg = C * L;
+  const int RB = n < kRowBlock ? n : kRowBlock;
+  const int nh = (n >> 1) + 1;
+  const size_t smr = (size_t)RB * n * sizeof(float2);       // 2 buffers of RB/2 rows
+  const size_t smc = (size_t)2 * kColBlock * n * sizeof(float2);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_rows_fwd<<<dim3(n / RB, nimg), kThreads, smr, st>>>(x, S, n, RB, tw);
+  k_cols<<<dim3((nh + kColBlock - 1) / kColBlock, nimg), kThreads, smc, st>>>(
+      S, kspec, n, L, kColBlock, tw);
+  k_rows_inv<<<dim3(n / RB, nimg), kThreads, smr, st>>>(S, g, b, n, L, RB, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t fft2d_c64(double2 *data, double2 *tmp, int n, int nimg,
+                      bool inverse, const double2 *tw64, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fft64_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  const size_t sm = (size_t)2 * n * sizeof(double2);
+  const int thr = n < 256 ? (n < 32 ? 32 : n) : 256;
+  dim3 tg((n + 31) / 32, (n + 31) / 32, nimg), tb(32, 8);
+  k_fft64_rows<<<dim3(n, nimg), thr, sm, st>>>(data, n, inverse, tw64);
+  k_transpose64<<<tg, tb, 0, st>>>(data, tmp, n);
+  k_fft64_rows<<<dim3(n, nimg), thr, sm, st>>>(tmp, n, inverse, tw64);
+  k_transpose64<<<tg, tb, 0, st>>>(tmp, data, n);
+  return cudaGetLastError();
+}
+
+cudaError_t real_to_c64(const float *in, double2 *out, size_t count,
+                        cudaStream_t st) {
+  k_real_to_c64<<<grid_for(count), 256, 0, st>>>(in, out, count);
+  return cudaGetLastError();
+}
+
+cudaError_t mul_conj_c64(double2 *a, const double2 *h, size_t count,
+                         cudaStream_t st) {
+  k_mul_conj_c64<<<grid_for(count), 256, 0, st>>>(a, h, count);
+  return cudaGetLastError();
+}
+
+cudaError_t c64_real_to_f32(const double2 *in, float *out, double scale,
+                            size_t count, cudaStream_t st) {
+  k_c64_real_to_f32<<<grid_for(count), 256, 0, st>>>(in, out, scale, count);
+  return cudaGetLastError();
+}
+
+cudaError_t make_kspec(const double2 *hh, float *kspec, double scale, int n,
+                       int L, cudaStream_t st) {
+  const size_t total = (size_t)L * ((n >> 1) + 1) * n;
+  k_make_kspec<<<grid_for(total), 256, 0, st>>>(hh, kspec, scale, n, L);
+  return cudaGetLastError();
+}
+
+}  // namespace muffin

@@ -1,0 +1,126 @@
+// Host-side launchers of the MUFFIN kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace muffin {
+
+// ------------------------------------------------------------ FFT (fft_conv.cu)
+// FP32 gradient pipeline: g[c][l] = H_l^T H_l x[c][l] - (c == 0 && b ? b[l] : 0)
+// for nimg = C*L images.  S: spectrum scratch [nimg][n/2+1][n] float2.
+// kspec: [L][n/2+1][n] = |h_hat_l(ky, kx)|^2 / n^2 (kx-major).
+cudaError_t launch_gradient(const float *x, float *g, const float *b,
+                            float2 *S, const float *kspec, const float2 *tw,
+                            int n, int L, int C, cudaStream_t st);
+
+// FP64 helpers used when a plan or a call is set up.
+// In-place 2D DFT of nimg complex n x n images; inverse is unnormalised.
+cudaError_t fft2d_c64(double2 *data, double2 *tmp, int n, int nimg, bool inverse,
+                      const double2 *tw64, cudaStream_t st);
+cudaError_t real_to_c64(const float *in, double2 *out, size_t count,
+                        cudaStream_t st);
+// a *= conj(h) elementwise (count elements)
+cudaError_t mul_conj_c64(double2 *a, const double2 *h, size_t count,
+                         cudaStream_t st);
+// out = (float)(scale * in.x)
+cudaError_t c64_real_to_f32(const double2 *in, float *out, double scale,
+                            size_t count, cudaStream_t st);
+// kspec[l][kx][ky] = |hh[l][ky][kx]|^2 * scale for kx < n/2+1
+cudaError_t make_kspec(const double2 *hh, float *kspec, double scale, int n,
+                       int L, cudaStream_t st);
+
+// ------------------------------------------------------------ reductions (reduce.cu)
+// out[0] = max |hh|^2 over count complex values (FP64); scratch >= 1024 doubles
+cudaError_t max_abs2_c64(const double2 *hh, size_t count, double *scratch,
+                         double *out, cudaStream_t st);
+// per-band sum of squares: out[l] = sum y[l]^2 (FP64)
+cudaError_t band_sumsq(const float *y, int L, size_t per_band, double *out,
+                       cudaStream_t st);
+// ybar = y + eps * delta ; hd unchanged
+cudaError_t axpy_f32(const float *y, const float *d, float eps, float *out,
+                     size_t count, cudaStream_t st);
+
+// SURE statistics at a window end (Eqs. SUGAR, PSURE0, rewritten with H^T):
+//   s0 = <grad, x'_mu>        s1 = <grad, x'_gamma>
+//   s2 = sum_l w_l <xbar'_mu - x'_mu, H^T delta>
+//   s3 = sum_l w_l <xbar'_gamma - x'_gamma, H^T delta>
+//   s4 = <x, grad - b>         s5 = sum_l w_l <xbar - x, H^T delta>
+// with w_l = 2 sigma_l^2 / eps.  ga/gb are the y- and ybar-groups (C = 3),
+// grad the gradient at the current x of the y-group primal.
+// partials: [nblocks][6] doubles, deterministic two-pass reduction.
+struct SureStatsArgs {
+  const float *grad;  // [L][n][n] gradient at the y-group primal
+  const float *x;     // y-group X [3][L][n][n] (primal, d/dmu, d/dgamma)
+  const float *xb;    // ybar-group X [3][L][n][n]
+  const float *b;     // [L][n][n] H^T y
+  const float *htd;   // [L][n][n] H^T delta
+  const double *wband;  // [L] 2 sigma_l^2 / eps
+  int n, L;
+};
+cudaError_t sure_stats(const SureStatsArgs &a, double *partials, int *nblocks,
+                       cudaStream_t st);
+
+// Theta update (Eq. adaptgrad) run by one block on the device.
+struct ThetaUpdateArgs {
+  DevScalars *sc;          // in/out
+  const double *partials;  // [nblocks][6]
+  int nblocks;
+  double *record;          // out: 7 doubles {k, mu, gamma, sugar_mu,
+                           //   sugar_gamma, psure, tau} (pre-update theta)
+  int k;
+  double eta_mu, eta_gamma, theta_min;
+  double psure_const;      // sum_l ||y_l||^2 - N sum_l sigma_l^2
+  // tau = safety / (beta/2 + sigma * (K * mu^2 * Bsum + gamma^2 * Asum))
+  double safety, lipschitz, K, Bsum, Asum;
+};
+cudaError_t theta_update(const ThetaUpdateArgs &a, cudaStream_t st);
+
+// ------------------------------------------------------------ wavelets (wavelet.cu)
+// Filters db1..db8: h, g taps (g[i] = (-1)^i h[2p-1-i]) uploaded to constant memory.
+cudaError_t upload_filters(const double h[8][16]);
+
+enum WaveMode { WAVE_TRANSFORM = 0, WAVE_ITERATE = 1 };
+
+struct WaveArgs {
+  int n, L, K, J, C;
+  const float *beta;       // [L] band weights
+  const DevScalars *sc;    // mu, gamma, tau, sigma
+  float *scratch;          // LL scratch: level j (1 <= j < J) holds
+                           // [C][L][K][n>>j][n>>j] at scratch + lvl_off[j]
+  size_t lvl_off[16];
+};
+
+// Synthesis + primal prox (Alg. 2 eqs. adjointspat2, stpm, stpx and the
+// derivative forms of Algs. 3/4): reads gr.u, gr.x, gr.g, gr.t -> gr.xt.
+cudaError_t wavelet_synthesis_prox(const WaveArgs &w, const Group &gr,
+                                   int positivity, cudaStream_t st);
+// Analysis + spatial dual update (eqs. stpp, stpu and derivative forms):
+// reads gr.xt, gr.x, gr.u -> gr.u.
+cudaError_t wavelet_analysis_dual(const WaveArgs &w, const Group &gr,
+                                  cudaStream_t st);
+// Operators: u = W_s x ; x = W_s^T u (C = 1, no weights).
+cudaError_t wavelet_analysis_op(const WaveArgs &w, const float *x, float *u,
+                                cudaStream_t st);
+cudaError_t wavelet_synthesis_op(const WaveArgs &w, const float *u, float *x,
+                                 cudaStream_t st);
+
+// ------------------------------------------------------------ DCT (dct.cu)
+struct DctArgs {
+  int n, L, Lp, C;         // Lp = L rounded up to a multiple of 16
+  const float *chi, *clo;  // [Lp][Lp] C split in TF32 hi + lo (zero padded)
+  const float *cthi, *ctlo;// [Lp][Lp] C^T split
+  const float *alpha;      // [n*n] pixel weights
+  const DevScalars *sc;
+};
+// Spectral dual update and back-projection (Alg. 2 eqs. vt, v, upt and the
+// derivative forms of Algs. 3/4): reads gr.xt, gr.x, gr.v -> gr.v, gr.t.
+cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st);
+// Operator: out^n = C in^n (inverse = 0) or C^T in^n (inverse = 1).
+cudaError_t dct_op(const DctArgs &d, const float *in, float *out, int inverse,
+                   cudaStream_t st);
+
+}  // namespace muffin

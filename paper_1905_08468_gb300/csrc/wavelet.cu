@@ -1,0 +1,666 @@
+// Spatial dictionary kernels: the union W_s of K periodised orthonormal
+// Daubechies bases (Sec. 4.2.1), J-level Mallat layout, fused with the MUFFIN
+// updates that consume them (Algorithm 2 and its derivatives, Algs. 3/4):
+//
+//   synthesis + primal prox:  s = mu_l W_s^T u ; m = x - tau (grad + s + t);
+//                             x~ = (m)_+                    (eqs. adjointspat2,
+//                                                             stpm, stpx)
+//   analysis + dual update:   p = u + sigma mu_l W_s (2 x~ - x); u = sat(p)
+//                                                            (eqs. stpp, stpu)
+//
+// One level per launch.  A CTA owns a tile of TY x TX coefficients of every
+// subband (2TY x 2TX pixels of the level's input) of one band; level 1 keeps
+// its input tile in shared memory and runs all K bases on it, so x~ and x are
+// read once for the 8 bases; coarser levels run one basis per CTA on the
+// approximation left in an LL scratch by the previous level.  Filters live in
+// constant memory and every pass keeps a sliding window of taps' inputs in
+// registers.  Periodic extension is a wrap of the tile's load indices, which
+// also covers levels smaller than a filter (the transform stays the exact
+// periodised one).
+//
+// Chains: a launch advances C = 1 (plain) or C = 3 chains {x, dx/dmu,
+// dx/dgamma} of one ADA-PT group.  The derivative channels use the masks of
+// the primal channel computed in the same thread (U(m) for the prox, Pi(p)
+// for the dual) and the inhomogeneous terms of Algorithm 3:
+//   analysis input   w1 = (2x~ - x) + mu (2x~' - x'),  scale sigma beta_l
+//   synthesis input  u0 + mu u1,                       scale beta_l
+// (Algorithm 4 has its inhomogeneous terms in the spectral step).
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace muffin {
+
+__constant__ float c_h[8][16];
+__constant__ float c_g[8][16];
+
+namespace {
+
+constexpr int TY = 16, TX = 32, PMAX = 8, NT = 256;
+// analysis tiles
+constexpr int A_RH = 2 * TY + 2 * PMAX - 2;          // input rows held
+constexpr int A_IP = (2 * TX + 2 * PMAX - 2) | 1;    // odd pitch: conflict-free rows
+constexpr int A_LP = TX + 1;                         // row-pass output pitch
+constexpr int QX = 4, QY = 2;                        // outputs per thread
+// synthesis tiles
+constexpr int S_CH = TY + PMAX - 1;                  // coefficient rows held
+constexpr int S_CP = (TX + PMAX - 1) | 1;            // coefficient pitch
+constexpr int S_LP = S_CP;                           // column-pass output pitch
+constexpr int QXP = 4, QYP = 2;                      // coefficient pairs per thread
+
+constexpr size_t ana_smem(int ch) {
+  return (size_t)ch * (A_RH * A_IP + 2 * A_RH * A_LP) * sizeof(float);
+}
+constexpr size_t syn_smem(int ch) {
+  return (size_t)ch * (4 * S_CH * S_CP + 2 * (2 * TY) * S_LP) * sizeof(float);
+}
+
+struct AnaArgs {
+  int n, M, L, K, last;
+  const float *in;              // level >= 2: LL_{j-1}; level-1 operator: x
+  const float *xt, *x;          // level-1 iteration inputs
+  float *ll_out;                // LL_j scratch when !last
+  float *u;
+  const float *beta;
+  const DevScalars *sc;
+};
+
+struct SynArgs {
+  int n, M, L, K, top, positivity;   // M: output side of this level
+  const float *ll_in;                // LL_j scratch when !top
+  const float *u;
+  float *ll_out;                     // LL_{j-1} scratch (levels >= 2)
+  const float *x, *g, *t;            // level-1 iteration inputs
+  float *xt;                         // level-1 iteration output
+  float *out;                        // level-1 operator output
+  const float *beta;
+  const DevScalars *sc;
+};
+
+// ------------------------------------------------------------ analysis
+template <int CH, int MODE>
+__device__ __forceinline__ void ana_emit(const AnaArgs &a, int l, int bb,
+                                         int row, int col, const float (&coef)[CH],
+                                         const float (&q)[CH]) {
+  const size_t NN = (size_t)a.n * a.n;
+  const size_t off = (size_t)row * a.n + col;
+  float *u0 = a.u + ((size_t)l * a.K + bb) * NN + off;
+  if (MODE == WAVE_TRANSFORM) {
+    *u0 = coef[0];
+  } else {
+    const float p0 = fmaf(q[0], coef[0], *u0);
+    *u0 = satf(p0);
+    const bool keep = fabsf(p0) <= 1.0f;
+#pragma unroll
+    for (int c = 1; c < CH; ++c) {
+      float *uc = u0 + (size_t)c * a.L * a.K * NN;
+      const float pc = fmaf(q[c], coef[c], *uc);
+      *uc = keep ? pc : 0.0f;
+    }
+  }
+}
+
+template <int P, int CH, int MODE>
+__device__ __forceinline__ void ana_basis(const AnaArgs &a, const float *in_s,
+                                          float *lo_s, float *hi_s, int l,
+                                          int bb, int kx0, int ky0,
+                                          const float (&q)[CH]) {
+  constexpr int RH = 2 * TY + 2 * P - 2;
+  constexpr int NSX = TX / QX;
+  constexpr int NV = 2 * QX + 2 * P - 2;
+  // rows: lo/hi along x
+  for (int it = threadIdx.x; it < CH * RH * NSX; it += NT) {
+    const int r = it % RH;
+    const int rest = it / RH;
+    const int s = rest % NSX;
+    const int c = rest / NSX;
+    const float *src = in_s + (c * A_RH + r) * A_IP + 2 * QX * s;
+    float v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = src[i];
+    float *dl = lo_s + (c * A_RH + r) * A_LP + QX * s;
+    float *dh = hi_s + (c * A_RH + r) * A_LP + QX * s;
+#pragma unroll
+    for (int qq = 0; qq < QX; ++qq) {
+      float lo = 0.f, hi = 0.f;
+#pragma unroll
+      for (int i = 0; i < 2 * P; ++i) {
+        lo = fmaf(c_h[P - 1][i], v[2 * qq + i], lo);
+        hi = fmaf(c_g[P - 1][i], v[2 * qq + i], hi);
+      }
+      dl[qq] = lo;
+      dh[qq] = hi;
+    }
+  }
+  __syncthreads();
+  // columns: four subbands, then the update
+  constexpr int NSY = TY / QY;
+  constexpr int NW = 2 * QY + 2 * P - 2;
+  const int h = a.M >> 1;
+  for (int it = threadIdx.x; it < NSY * TX; it += NT) {
+    const int kx = it % TX, s = it / TX;
+    float cLL[CH][QY], cDY[CH][QY], cDX[CH][QY], cHH[CH][QY];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const float *pl = lo_s + (c * A_RH + 2 * QY * s) * A_LP + kx;
+      const float *ph = hi_s + (c * A_RH + 2 * QY * s) * A_LP + kx;
+      float vl[NW], vh[NW];
+#pragma unroll
+      for (int i = 0; i < NW; ++i) { vl[i] = pl[i * A_LP]; vh[i] = ph[i * A_LP]; }
+#pragma unroll
+      for (int qq = 0; qq < QY; ++qq) {
+        float ll = 0.f, dy = 0.f, dx = 0.f, hh = 0.f;
+#pragma unroll
+        for (int i = 0; i < 2 * P; ++i) {
+          ll = fmaf(c_h[P - 1][i], vl[2 * qq + i], ll);
+          dy = fmaf(c_g[P - 1][i], vl[2 * qq + i], dy);
+          dx = fmaf(c_h[P - 1][i], vh[2 * qq + i], dx);
+          hh = fmaf(c_g[P - 1][i], vh[2 * qq + i], hh);
+        }
+        cLL[c][qq] = ll; cDY[c][qq] = dy; cDX[c][qq] = dx; cHH[c][qq] = hh;
+      }
+    }
+    const int kxg = kx0 + kx;
+    if (kxg < h) {
+#pragma unroll
+      for (int qq = 0; qq < QY; ++qq) {
+        const int ky = ky0 + QY * s + qq;
+        if (ky >= h) continue;
+        float t[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) t[c] = cDX[c][qq];
+        ana_emit<CH, MODE>(a, l, bb, ky, h + kxg, t, q);
+#pragma unroll
+        for (int c = 0; c < CH; ++c) t[c] = cDY[c][qq];
+        ana_emit<CH, MODE>(a, l, bb, h + ky, kxg, t, q);
+#pragma unroll
+        for (int c = 0; c < CH; ++c) t[c] = cHH[c][qq];
+        ana_emit<CH, MODE>(a, l, bb, h + ky, h + kxg, t, q);
+#pragma unroll
+        for (int c = 0; c < CH; ++c) t[c] = cLL[c][qq];
+        if (a.last) {
+          ana_emit<CH, MODE>(a, l, bb, ky, kxg, t, q);
+        } else {
+#pragma unroll
+          for (int c = 0; c < CH; ++c)
+            a.ll_out[(((size_t)(c * a.L + l) * a.K + bb) * h + ky) * h + kxg] = t[c];
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int CH, int MODE>
+__device__ __forceinline__ void ana_dispatch(int p, const AnaArgs &a,
+                                             const float *in_s, float *lo_s,
+                                             float *hi_s, int l, int bb,
+                                             int kx0, int ky0,
+                                             const float (&q)[CH]) {
+  switch (p) {
+    case 1: ana_basis<1, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
+    case 2: ana_basis<2, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
+    case 3: ana_basis<3, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
+    case 4: ana_basis<4, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
+    case 5: ana_basis<5, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
+    case 6: ana_basis<6, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
+    case 7: ana_basis<7, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
+    default: ana_basis<8, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
+  }
+}
+
+template <int CH, int MODE, bool LEVEL1>
+__global__ void __launch_bounds__(NT) k_ana(AnaArgs a) {
+  extern __shared__ float smem[];
+  float *in_s = smem;
+  float *lo_s = in_s + CH * A_RH * A_IP;
+  float *hi_s = lo_s + CH * A_RH * A_LP;
+  const int h = a.M >> 1;
+  const int ntx = (h + TX - 1) / TX;
+  const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
+  const int l = LEVEL1 ? blockIdx.y : blockIdx.y / a.K;
+  const int b = LEVEL1 ? 0 : blockIdx.y % a.K;
+  const int P = LEVEL1 ? a.K : b + 1;
+  const int RH = 2 * TY + 2 * P - 2, RW = 2 * TX + 2 * P - 2;
+  const int Mm = a.M - 1;
+  const size_t NN = (size_t)a.n * a.n;
+  const size_t CS = (size_t)a.L * NN;   // channel stride of images
+  float mu = 0.f;
+  float q[CH];
+  if (MODE == WAVE_ITERATE) {
+    mu = (float)a.sc->mu;
+    const float sb = (float)(a.sc->sigma * (double)a.beta[l]);
+    q[0] = sb * mu;
+    if (CH == 3) { q[1] = sb; q[2] = sb * mu; }
+  } else {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) q[c] = 1.f;
+  }
+  for (int it = threadIdx.x; it < RH * RW; it += NT) {
+    const int r = it / RW, cc = it - r * RW;
+    const int yy = (2 * ky0 + r) & Mm, xx = (2 * kx0 + cc) & Mm;
+    float w[CH];
+    if (LEVEL1) {
+      const size_t pix = (size_t)l * NN + (size_t)yy * a.n + xx;
+      if (MODE == WAVE_TRANSFORM) {
+        w[0] = a.in[pix];
+      } else {
+        float z[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+          z[c] = 2.f * a.xt[c * CS + pix] - a.x[c * CS + pix];
+        w[0] = z[0];
+        if (CH == 3) { w[1] = fmaf(mu, z[1], z[0]); w[2] = z[2]; }
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+        w[c] = a.in[(((size_t)(c * a.L + l) * a.K + b) * a.M + yy) * a.M + xx];
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) in_s[(c * A_RH + r) * A_IP + cc] = w[c];
+  }
+  __syncthreads();
+  if (LEVEL1) {
+    for (int bb = 0; bb < a.K; ++bb)
+      ana_dispatch<CH, MODE>(bb + 1, a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q);
+  } else {
+    ana_dispatch<CH, MODE>(b + 1, a, in_s, lo_s, hi_s, l, b, kx0, ky0, q);
+  }
+}
+
+// ------------------------------------------------------------ synthesis
+// Inverse of one level: lo/hi along y from (LL, DY) and (DX, HH), then the
+// rows.  x[2k+e] = sum_s h[2s+e] a[k-s] + g[2s+e] d[k-s] (transpose of the
+// analysis, indices mod the level size).
+template <int P, int CH>
+__device__ __forceinline__ void syn_basis(const float *cf, float *lo_s,
+                                          float *hi_s, float (&acc)[CH][2 * QXP],
+                                          bool accumulate) {
+  // cf: [4][CH][S_CH][S_CP] subbands LL, DY, DX, HH; row 0 = coefficient ky0-(P-1)
+  constexpr int NCOL = TX + P - 1;
+  constexpr int NSY = TY / QYP;
+  constexpr int NWC = QYP + P - 1;
+  const float *cLL = cf, *cDY = cf + CH * S_CH * S_CP, *cDX = cf + 2 * CH * S_CH * S_CP,
+              *cHH = cf + 3 * CH * S_CH * S_CP;
+  for (int it = threadIdx.x; it < CH * NSY * NCOL; it += NT) {
+    const int kc = it % NCOL;
+    const int rest = it / NCOL;
+    const int sy = rest % NSY, c = rest / NSY;
+    const int base = (c * S_CH + QYP * sy) * S_CP + kc;
+    float vLL[NWC], vDY[NWC], vDX[NWC], vHH[NWC];
+#pragma unroll
+    for (int i = 0; i < NWC; ++i) {
+      vLL[i] = cLL[base + i * S_CP];
+      vDY[i] = cDY[base + i * S_CP];
+      vDX[i] = cDX[base + i * S_CP];
+      vHH[i] = cHH[base + i * S_CP];
+    }
+#pragma unroll
+    for (int qq = 0; qq < QYP; ++qq) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        float lo = 0.f, hi = 0.f;
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+          const int ci = qq + P - 1 - s;
+          lo = fmaf(c_h[P - 1][2 * s + e], vLL[ci], lo);
+          lo = fmaf(c_g[P - 1][2 * s + e], vDY[ci], lo);
+          hi = fmaf(c_h[P - 1][2 * s + e], vDX[ci], hi);
+          hi = fmaf(c_g[P - 1][2 * s + e], vHH[ci], hi);
+        }
+        const int my = 2 * (QYP * sy + qq) + e;
+        lo_s[(c * 2 * TY + my) * S_LP + kc] = lo;
+        hi_s[(c * 2 * TY + my) * S_LP + kc] = hi;
+      }
+    }
+  }
+  __syncthreads();
+  // rows: thread owns output row my, pixels 8 sx .. 8 sx + 7
+  constexpr int NWR = QXP + P - 1;
+  {
+    const int it = threadIdx.x;
+    const int sx = it % (TX / QXP), my = it / (TX / QXP);
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const float *pl = lo_s + (c * 2 * TY + my) * S_LP + QXP * sx;
+      const float *ph = hi_s + (c * 2 * TY + my) * S_LP + QXP * sx;
+      float vl[NWR], vh[NWR];
+#pragma unroll
+      for (int i = 0; i < NWR; ++i) { vl[i] = pl[i]; vh[i] = ph[i]; }
+#pragma unroll
+      for (int qq = 0; qq < QXP; ++qq) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          float o = 0.f;
+#pragma unroll
+          for (int s = 0; s < P; ++s) {
+            const int ci = qq + P - 1 - s;
+            o = fmaf(c_h[P - 1][2 * s + e], vl[ci], o);
+            o = fmaf(c_g[P - 1][2 * s + e], vh[ci], o);
+          }
+          if (accumulate) acc[c][2 * qq + e] += o; else acc[c][2 * qq + e] = o;
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <int CH>
+__device__ __forceinline__ void syn_dispatch(int p, const float *cf, float *lo_s,
+                                             float *hi_s, float (&acc)[CH][2 * QXP],
+                                             bool accumulate) {
+  switch (p) {
+    case 1: syn_basis<1, CH>(cf, lo_s, hi_s, acc, accumulate); break;
+    case 2: syn_basis<2, CH>(cf, lo_s, hi_s, acc, accumulate); break;
+    case 3: syn_basis<3, CH>(cf, lo_s, hi_s, acc, accumulate); break;
+    case 4: syn_basis<4, CH>(cf, lo_s, hi_s, acc, accumulate); break;
+    case 5: syn_basis<5, CH>(cf, lo_s, hi_s, acc, accumulate); break;
+    case 6: syn_basis<6, CH>(cf, lo_s, hi_s, acc, accumulate); break;
+    case 7: syn_basis<7, CH>(cf, lo_s, hi_s, acc, accumulate); break;
+    default: syn_basis<8, CH>(cf, lo_s, hi_s, acc, accumulate); break;
+  }
+}
+
+template <int CH, int MODE>
+__device__ __forceinline__ void syn_load(const SynArgs &a, float *cf, int l,
+                                         int bb, int kx0, int ky0, float mu) {
+  const int P = bb + 1;
+  const int h = a.M >> 1, hm = h - 1;
+  const int R = TY + P - 1, W = TX + P - 1;
+  const size_t NN = (size_t)a.n * a.n;
+  const size_t US = (size_t)a.L * a.K * NN;   // channel stride of U
+  const float *u0 = a.u + ((size_t)l * a.K + bb) * NN;
+  for (int it = threadIdx.x; it < R * W; it += NT) {
+    const int r = it / W, cc = it - r * W;
+    const int ky = (ky0 - (P - 1) + r) & hm, kx = (kx0 - (P - 1) + cc) & hm;
+    const size_t oDX = (size_t)ky * a.n + h + kx, oDY = (size_t)(h + ky) * a.n + kx,
+                 oHH = (size_t)(h + ky) * a.n + h + kx, oLL = (size_t)ky * a.n + kx;
+    float vDX[CH], vDY[CH], vHH[CH], vLL[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const float *uc = u0 + c * US;
+      vDX[c] = uc[oDX]; vDY[c] = uc[oDY]; vHH[c] = uc[oHH];
+      vLL[c] = a.top ? uc[oLL]
+                     : a.ll_in[(((size_t)(c * a.L + l) * a.K + bb) * h + ky) * h + kx];
+    }
+    if (MODE == WAVE_ITERATE && CH == 3) {
+      // Algorithm 3: s' = beta_l W_s^T (u + mu u'_mu); LL from scratch is combined already
+      vDX[1] = fmaf(mu, vDX[1], vDX[0]);
+      vDY[1] = fmaf(mu, vDY[1], vDY[0]);
+      vHH[1] = fmaf(mu, vHH[1], vHH[0]);
+      if (a.top) vLL[1] = fmaf(mu, vLL[1], vLL[0]);
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int o = (c * S_CH + r) * S_CP + cc;
+      cf[o] = vLL[c];
+      cf[CH * S_CH * S_CP + o] = vDY[c];
+      cf[2 * CH * S_CH * S_CP + o] = vDX[c];
+      cf[3 * CH * S_CH * S_CP + o] = vHH[c];
+    }
+  }
+  __syncthreads();
+}
+
+template <int CH, int MODE, bool LEVEL1>
+__global__ void __launch_bounds__(NT) k_syn(SynArgs a) {
+  extern __shared__ float smem[];
+  float *cf = smem;
+  float *lo_s = cf + 4 * CH * S_CH * S_CP;
+  float *hi_s = lo_s + CH * 2 * TY * S_LP;
+  const int h = a.M >> 1;
+  const int ntx = (h + TX - 1) / TX;
+  const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
+  const int l = LEVEL1 ? blockIdx.y : blockIdx.y / a.K;
+  const int b = LEVEL1 ? 0 : blockIdx.y % a.K;
+  const float mu = (MODE == WAVE_ITERATE) ? (float)a.sc->mu : 0.f;
+  float acc[CH][2 * QXP];
+#pragma unroll
+  for (int c = 0; c < CH; ++c)
+#pragma unroll
+    for (int e = 0; e < 2 * QXP; ++e) acc[c][e] = 0.f;
+  if (LEVEL1) {
+    for (int bb = 0; bb < a.K; ++bb) {
+      syn_load<CH, MODE>(a, cf, l, bb, kx0, ky0, mu);
+      syn_dispatch<CH>(bb + 1, cf, lo_s, hi_s, acc, true);
+    }
+  } else {
+    syn_load<CH, MODE>(a, cf, l, b, kx0, ky0, mu);
+    syn_dispatch<CH>(b + 1, cf, lo_s, hi_s, acc, false);
+  }
+  const int sx = threadIdx.x % (TX / QXP), my = threadIdx.x / (TX / QXP);
+  const int yy = 2 * ky0 + my, xx0 = 2 * kx0 + 2 * QXP * sx;
+  if (yy >= a.M) return;
+  const size_t NN = (size_t)a.n * a.n;
+  if (!LEVEL1) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      float *o = a.ll_out + (((size_t)(c * a.L + l) * a.K + b) * a.M + yy) * a.M;
+#pragma unroll
+      for (int e = 0; e < 2 * QXP; ++e)
+        if (xx0 + e < a.M) o[xx0 + e] = acc[c][e];
+    }
+    return;
+  }
+  const size_t row = (size_t)l * NN + (size_t)yy * a.n;
+  if (MODE == WAVE_TRANSFORM) {
+#pragma unroll
+    for (int e = 0; e < 2 * QXP; ++e)
+      if (xx0 + e < a.n) a.out[row + xx0 + e] = acc[0][e];
+    return;
+  }
+  const float tau = (float)a.sc->tau;
+  const float bl = a.beta[l];
+  float sc[CH];
+  sc[0] = bl * mu;
+  if (CH == 3) { sc[1] = bl; sc[2] = bl * mu; }
+  const size_t CS = (size_t)a.L * NN;
+#pragma unroll
+  for (int e = 0; e < 2 * QXP; ++e) {
+    if (xx0 + e >= a.n) continue;
+    const size_t i0 = row + xx0 + e;
+    const float m0 = a.x[i0] - tau * (a.g[i0] + sc[0] * acc[0][e] + a.t[i0]);
+    const bool keep = !a.positivity || m0 > 0.f;
+    a.xt[i0] = keep ? m0 : 0.f;
+#pragma unroll
+    for (int c = 1; c < CH; ++c) {
+      const size_t ic = i0 + c * CS;
+      const float mc = a.x[ic] - tau * (a.g[ic] + sc[c] * acc[c][e] + a.t[ic]);
+      a.xt[ic] = keep ? mc : 0.f;
+    }
+  }
+}
+
+// ------------------------------------------------------------ J = 0 (identity bases)
+template <int CH, int MODE>
+__global__ void k_syn0(SynArgs a) {
+  const size_t NN = (size_t)a.n * a.n;
+  const size_t tot = (size_t)a.L * NN;
+  const size_t US = (size_t)a.L * a.K * NN, CS = (size_t)a.L * NN;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(i / NN);
+    const size_t pix = i - (size_t)l * NN;
+    float acc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) acc[c] = 0.f;
+    const float mu = (MODE == WAVE_ITERATE) ? (float)a.sc->mu : 0.f;
+    for (int bb = 0; bb < a.K; ++bb) {
+      const float *u0 = a.u + ((size_t)l * a.K + bb) * NN + pix;
+      float v[CH];
+#pragma unroll
+      for (int c = 0; c < CH; ++c) v[c] = u0[c * US];
+      if (MODE == WAVE_ITERATE && CH == 3) v[1] = fmaf(mu, v[1], v[0]);
+#pragma unroll
+      for (int c = 0; c < CH; ++c) acc[c] += v[c];
+    }
+    if (MODE == WAVE_TRANSFORM) { a.out[i] = acc[0]; continue; }
+    const float tau = (float)a.sc->tau, bl = a.beta[l];
+    float sc[CH];
+    sc[0] = bl * mu;
+    if (CH == 3) { sc[1] = bl; sc[2] = bl * mu; }
+    const float m0 = a.x[i] - tau * (a.g[i] + sc[0] * acc[0] + a.t[i]);
+    const bool keep = !a.positivity || m0 > 0.f;
+    a.xt[i] = keep ? m0 : 0.f;
+#pragma unroll
+    for (int c = 1; c < CH; ++c) {
+      const size_t ic = i + c * CS;
+      const float mc = a.x[ic] - tau * (a.g[ic] + sc[c] * acc[c] + a.t[ic]);
+      a.xt[ic] = keep ? mc : 0.f;
+    }
+  }
+}
+
+template <int CH, int MODE>
+__global__ void k_ana0(AnaArgs a) {
+  const size_t NN = (size_t)a.n * a.n;
+  const size_t tot = (size_t)a.L * NN, CS = (size_t)a.L * NN;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(i / NN);
+    const size_t pix = i - (size_t)l * NN;
+    float w[CH], q[CH];
+    if (MODE == WAVE_TRANSFORM) {
+      w[0] = a.in[i]; q[0] = 1.f;
+    } else {
+      const float mu = (float)a.sc->mu;
+      const float sb = (float)(a.sc->sigma * (double)a.beta[l]);
+      float z[CH];
+#pragma unroll
+      for (int c = 0; c < CH; ++c) z[c] = 2.f * a.xt[i + c * CS] - a.x[i + c * CS];
+      w[0] = z[0]; q[0] = sb * mu;
+      if (CH == 3) { w[1] = fmaf(mu, z[1], z[0]); w[2] = z[2]; q[1] = sb; q[2] = sb * mu; }
+    }
+    const int row = (int)(pix / a.n), col = (int)(pix % a.n);
+    for (int bb = 0; bb < a.K; ++bb) ana_emit<CH, MODE>(a, l, bb, row, col, w, q);
+  }
+}
+
+// ------------------------------------------------------------ launch helpers
+inline int tiles(int h) { return ((h + TX - 1) / TX) * ((h + TY - 1) / TY); }
+
+template <int CH, int MODE, bool L1>
+cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_ana<CH, MODE, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)ana_smem(CH));
+    attr = true;
+  }
+  k_ana<CH, MODE, L1><<<dim3(tiles(a.M >> 1), nblk_y), NT, ana_smem(CH), st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int CH, int MODE, bool L1>
+cudaError_t launch_syn(const SynArgs &a, int nblk_y, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_syn<CH, MODE, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)syn_smem(CH));
+    attr = true;
+  }
+  k_syn<CH, MODE, L1><<<dim3(tiles(a.M >> 1), nblk_y), NT, syn_smem(CH), st>>>(a);
+  return cudaGetLastError();
+}
+
+inline int grid_elem(size_t count) {
+  size_t g = (count + 255) / 256;
+  return (int)(g > 152 * 16 ? 152 * 16 : (g ? g : 1));
+}
+
+template <int CH, int MODE>
+cudaError_t synthesis_all(const WaveArgs &w, const SynArgs &base, cudaStream_t st) {
+  SynArgs a = base;
+  if (w.J == 0) {
+    a.M = w.n;
+    k_syn0<CH, MODE><<<grid_elem((size_t)w.L * w.n * w.n), 256, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  cudaError_t e = cudaSuccess;
+  for (int j = w.J; j >= 2; --j) {
+    a.M = w.n >> (j - 1);
+    a.top = (j == w.J);
+    a.ll_in = a.top ? nullptr : w.scratch + w.lvl_off[j];
+    a.ll_out = w.scratch + w.lvl_off[j - 1];
+    e = launch_syn<CH, MODE, false>(a, w.L * w.K, st);
+    if (e != cudaSuccess) return e;
+  }
+  a.M = w.n;
+  a.top = (w.J == 1);
+  a.ll_in = a.top ? nullptr : w.scratch + w.lvl_off[1];
+  a.ll_out = nullptr;
+  return launch_syn<CH, MODE, true>(a, w.L, st);
+}
+
+template <int CH, int MODE>
+cudaError_t analysis_all(const WaveArgs &w, const AnaArgs &base, cudaStream_t st) {
+  AnaArgs a = base;
+  if (w.J == 0) {
+    a.M = w.n;
+    k_ana0<CH, MODE><<<grid_elem((size_t)w.L * w.n * w.n), 256, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  a.M = w.n;
+  a.last = (w.J == 1);
+  a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[1];
+  cudaError_t e = launch_ana<CH, MODE, true>(a, w.L, st);
+  for (int j = 2; j <= w.J && e == cudaSuccess; ++j) {
+    a.M = w.n >> (j - 1);
+    a.in = w.scratch + w.lvl_off[j - 1];
+    a.last = (j == w.J);
+    a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[j];
+    e = launch_ana<CH, MODE, false>(a, w.L * w.K, st);
+  }
+  return e;
+}
+
+}  // namespace
+
+cudaError_t upload_filters(const double h[8][16]) {
+  float hf[8][16], gf[8][16];
+  for (int p = 1; p <= 8; ++p)
+    for (int i = 0; i < 16; ++i) {
+      hf[p - 1][i] = i < 2 * p ? (float)h[p - 1][i] : 0.f;
+      gf[p - 1][i] = i < 2 * p ? (float)((i & 1 ? -1.0 : 1.0) * h[p - 1][2 * p - 1 - i]) : 0.f;
+    }
+  cudaError_t e = cudaMemcpyToSymbol(c_h, hf, sizeof(hf));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_g, gf, sizeof(gf));
+}
+
+cudaError_t wavelet_synthesis_prox(const WaveArgs &w, const Group &gr,
+                                   int positivity, cudaStream_t st) {
+  SynArgs a{};
+  a.n = w.n; a.L = w.L; a.K = w.K; a.positivity = positivity;
+  a.u = gr.u; a.x = gr.x; a.g = gr.g; a.t = gr.t; a.xt = gr.xt;
+  a.beta = w.beta; a.sc = w.sc;
+  if (gr.C == 3) return synthesis_all<3, WAVE_ITERATE>(w, a, st);
+  return synthesis_all<1, WAVE_ITERATE>(w, a, st);
+}
+
+cudaError_t wavelet_analysis_dual(const WaveArgs &w, const Group &gr,
+                                  cudaStream_t st) {
+  AnaArgs a{};
+  a.n = w.n; a.L = w.L; a.K = w.K;
+  a.xt = gr.xt; a.x = gr.x; a.u = gr.u; a.beta = w.beta; a.sc = w.sc;
+  if (gr.C == 3) return analysis_all<3, WAVE_ITERATE>(w, a, st);
+  return analysis_all<1, WAVE_ITERATE>(w, a, st);
+}
+
+cudaError_t wavelet_analysis_op(const WaveArgs &w, const float *x, float *u,
+                                cudaStream_t st) {
+  AnaArgs a{};
+  a.n = w.n; a.L = w.L; a.K = w.K; a.in = x; a.u = u;
+  return analysis_all<1, WAVE_TRANSFORM>(w, a, st);
+}
+
+cudaError_t wavelet_synthesis_op(const WaveArgs &w, const float *u, float *x,
+                                 cudaStream_t st) {
+  SynArgs a{};
+  a.n = w.n; a.L = w.L; a.K = w.K; a.u = u; a.out = x;
+  return synthesis_all<1, WAVE_TRANSFORM>(w, a, st);
+}
+
+}  // namespace muffin

@@ -1,0 +1,105 @@
+"""Parity of ADA-PT'ed MUFFIN (Algorithm 5 with Algorithms 3/4 fused into
+the primal kernels) against the FP64 oracle.  Tolerances: restored cube
+relative L2 1e-5, tuned (mu, gamma) relative 1e-3, per-window SUGAR and
+PSURE relative 1e-3."""
+import numpy as np
+import pytest
+
+from oracle import muffin as om, sure as osure
+from synth import fdmc_eps, make_cube, make_workload
+from tests.gpu_util import cuda, dev, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_tune(c, theta0, iters, window, eta, eps, x0=None, reset=True, **kw):
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    x = dev(np.zeros_like(c.dirty) if x0 is None else x0, torch)
+    with pkg.Plan(c.n, c.L, c.psf, sure=True, **kw) as plan:
+        th, trace, info = plan.sure_tune(dev(c.dirty, torch), dev(c.delta, torch),
+                                         c.noise_var, x, theta0, iters, window=window,
+                                         eta=eta, eps=eps, reset=reset)
+    return host(x), np.array(th), trace, info
+
+
+def oracle_tune(c, theta0, iters, window, eta, eps, reset=True, n_wavelets=8, levels=3):
+    prob = om.make_problem(c.dirty, c.psf, n_wavelets=n_wavelets, J=levels)
+    return osure.ada_pt(prob, c.delta, eps, c.noise_var, theta0, iters, Delta=window,
+                        eta=eta, reset=reset)
+
+
+def check(c, theta0, iters, window, eta, reset=True, **kw):
+    eps = fdmc_eps(c.noise_var)
+    xg, th, trace, _ = gpu_tune(c, theta0, iters, window, eta, eps, reset=reset, **kw)
+    ref = oracle_tune(c, theta0, iters, window, eta, eps, reset=reset, **kw)
+    assert len(trace) == len(ref.trace) == iters // window
+    for tg, to in zip(trace, ref.trace):
+        assert tg["k"] == to["k"]
+        assert tg["sugar_mu"] == pytest.approx(to["sugar"][0], rel=1e-3, abs=1e-6)
+        assert tg["sugar_gamma"] == pytest.approx(to["sugar"][1], rel=1e-3, abs=1e-6)
+        assert tg["psure"] == pytest.approx(to["psure"], rel=1e-3)
+    th_rel = np.max(np.abs(th - ref.theta) / np.abs(ref.theta))
+    e = rel_l2(xg, ref.x)
+    print(f"theta gpu {th} oracle {ref.theta} rel {th_rel:.2e}; cube rel L2 {e:.2e}")
+    assert th_rel <= 1e-3, th_rel
+    assert e <= 1e-5, e
+    assert not np.allclose(ref.theta, theta0)    # the tuning moved theta
+    return ref
+
+
+def test_sure_small():
+    c = make_cube(32, 8, 10, 2, 800, seed=12)
+    check(c, (0.05, 0.05), 20, 5, (2e-4, 2e-4))
+
+
+def test_sure_c1_workload():
+    c = make_workload("c1_64x64x8")
+    check(c, (1e-2, 1e-2), 60, 10, (5e-5, 5e-5))
+
+
+def test_sure_no_reset_and_short_windows():
+    c = make_cube(16, 4, 6, 1, 400, seed=13)
+    check(c, (0.05, 0.02), 12, 3, (1e-4, 1e-4), reset=False, n_wavelets=3, levels=2)
+
+
+def test_sure_crop_of_the_tuning_workload():
+    """256^2 x 16 crop with the 1024^2 x 64 cube's densities, window 10."""
+    c = make_cube(256, 16, 125, 6, 12500, seed=3)
+    check(c, (1e-2, 1e-2), 20, 10, (2e-5, 2e-5))
+
+
+def test_eta_zero_primal_equals_plain_solve():
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    c = make_cube(64, 4, 10, 2, 1500, seed=14)
+    eps = fdmc_eps(c.noise_var)
+    xs, th, _, _ = gpu_tune(c, (1e-2, 1e-2), 20, 5, (0.0, 0.0), eps)
+    assert tuple(th) == (1e-2, 1e-2)
+    x = dev(np.zeros_like(c.dirty), torch)
+    with pkg.Plan(64, 4, c.psf) as plan:
+        plan.solve(dev(c.dirty, torch), x, 20, 1e-2, 1e-2)
+    assert np.array_equal(xs, host(x))
+
+
+def test_sure_warm_and_resume_bitwise():
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    c = make_cube(32, 4, 8, 1, 700, seed=15)
+    eps = fdmc_eps(c.noise_var)
+    d, de = dev(c.dirty, torch), dev(c.delta, torch)
+    args = dict(window=4, eta=(1e-4, 1e-4), eps=eps)
+    x_full = torch.zeros_like(d)
+    with pkg.Plan(32, 4, c.psf, sure=True) as p:
+        th_full, tr_full, _ = p.sure_tune(d, de, c.noise_var, x_full, (0.03, 0.03), 24, **args)
+    x_part = torch.zeros_like(d)
+    with pkg.Plan(32, 4, c.psf, sure=True) as p:
+        p.sure_tune(d, de, c.noise_var, x_part, (0.03, 0.03), 10, **args)
+        blob = p.state_export()
+    with pkg.Plan(32, 4, c.psf, sure=True) as p:
+        p.state_import(blob)
+        th_res, tr_res, _ = p.sure_tune(None, None, None, x_part, (0, 0), 14, warm=True, **args)
+    assert torch.equal(x_full, x_part)
+    assert th_full == th_res
+    assert [t["k"] for t in tr_res] == [12, 16, 20, 24]
+    assert tr_res[-1] == tr_full[-1]
