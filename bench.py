@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput of ADA-PT'ed MUFFIN on GB300: voxel-iterations per second.
+
+Workload (default): the 1024 x 1024 x 64 cube of the synthetic recipe
+(2000 point sources, 100 blobs, 200000 uv points, 20 dB per band), MUFFIN
+with SURE/SUGAR auto-tuning of (mu, gamma).  One step = one
+``muffin_sure_tune`` call of 300 ADA-PT iterations (window 10, so 30 theta
+updates) from X0 = 0; a voxel-iteration advances one pixel of one band by one
+iteration in all six chains (primal and FDMC primal, four derivative chains).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores instead, on a bounded crop of the same workload.
+Multi-GPU (torchrun): every rank solves its own cube (replicas, weak scaling,
+no collective on the data path); the timed region is bracketed by barriers
+and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iters/s (px x bands x iters) at 1024^2 x 64, ADA-PT'ed MUFFIN"
+UNIT = "voxel-iters/s"
+THETA0 = (1e-2, 1e-2)
+ETA = (1e-12, 1e-12)
+CROP = dict(n=256, L=8, iters=1)      # oracle sample: top-left 256^2 x 8 bands
+
+
+# ------------------------------------------------------------------ ranks
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+    rank, _, world = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29512")
+        dist.init_process_group(backend, rank=rank, world_size=world)
+    return dist
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(v: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(v)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
+# ------------------------------------------------------------------ clocks
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={CLOCK_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        return parse_clocks(self.f.read())
+
+
+def parse_clocks(text: str) -> dict:
+    sm, mx, reasons = [], [], set()
+    for line in text.strip().splitlines():
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for name, val in zip(REASONS, parts[5:9]):
+            if val.lower() == "active":
+                reasons.add(name)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle leg
+ORACLE_SAMPLE = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from synth import make_workload, fdmc_eps
+from oracle import muffin as om, sure as osure
+c = make_workload({name!r})
+n, L, iters = {n}, {L}, {iters}
+sl = (slice(0, L), slice(0, n), slice(0, n))
+prob = om.make_problem(c.dirty[sl], c.psf[sl])
+nv = c.noise_var[:L]
+t0 = time.perf_counter()
+osure.ada_pt(prob, c.delta[sl], fdmc_eps(nv), nv, {theta0!r}, iters, Delta=10, eta=(0.0, 0.0))
+dt = time.perf_counter() - t0
+print(json.dumps(dict(seconds=dt, voxels=n * n * L, iters=iters)))
+"""
+
+
+def oracle_sample(name: str) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+               MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SAMPLE.format(root=ROOT, name=name, theta0=THETA0, **CROP)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                       env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle sample failed: {r.stderr[-2000:]}")
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    d["value"] = d["voxels"] * d["iters"] / d["seconds"]
+    return d
+
+
+def cpu_baseline_obj(d: dict) -> dict:
+    return {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 NumPy oracle, {d['iters']} ADA-PT iteration(s) (6 chains) "
+                       f"on the top-left {CROP['n']}x{CROP['n']} x {CROP['L']}-band crop "
+                       f"of the 1024^2 x 64 cube, 1 thread, {d['seconds']:.1f} s")}
+
+
+def run_reference(args) -> None:
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(args.workload)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        d = oracle_sample(args.workload)
+        vals.append(d["value"])
+        secs += d["seconds"]
+    v = statistics.mean(vals)
+    last = dict(d, value=v)
+    out = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": workload_config(args, oracle=True),
+           "cpu_baseline": cpu_baseline_obj(last),
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+def workload_config(args, oracle=False) -> dict:
+    from synth import WORKLOADS
+    n, L, n_src, n_blob, n_uv, seed = WORKLOADS[args.workload]
+    cfg = {"workload": f"ADA-PT'ed MUFFIN {n}x{n} px x {L} bands",
+           "n": n, "bands": L, "sources": n_src, "blobs": n_blob, "uv_points": n_uv,
+           "snr_db": 20, "seed": seed, "iters_per_step": args.iters,
+           "window": args.window, "wavelets": "db1..db8, 3 levels",
+           "spectral": "DCT-II (3xTF32 tensor cores)", "chains": 6,
+           "theta0": list(THETA0), "eta": list(ETA),
+           "l2": "inputs larger than L2 (state ~26 GB per cube)"}
+    if oracle:
+        cfg["oracle_sample"] = dict(CROP)
+    return cfg
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="muffin", choices=["muffin", "reference"])
+    ap.add_argument("--workload", default="c3_1024x1024x64")
+    ap.add_argument("--iters", type=int, default=300)
+    ap.add_argument("--window", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import numpy as np
+    import torch
+    from synth import fdmc_eps, make_workload
+    import paper_1905_08468_gb300 as pkg
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist_init("nccl")
+    dev = torch.device("cuda", local_rank)
+    c = make_workload(args.workload)
+    eps = fdmc_eps(c.noise_var)
+    vox = c.voxels
+    psf = torch.from_numpy(c.psf).to(dev)
+    dirty = torch.from_numpy(c.dirty).to(dev)
+    delta = torch.from_numpy(c.delta).to(dev)
+    x = torch.zeros_like(dirty)
+    plan = pkg.Plan(c.n, c.L, psf, sure=True)
+    del psf
+    kw = dict(window=args.window, eta=ETA, eps=eps)
+
+    def step(xb, d, dl):
+        return plan.sure_tune(d, dl, c.noise_var, xb, THETA0, args.iters, **kw)
+
+    for _ in range(args.warmup):
+        x.zero_()
+        step(x, dirty, delta)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    plan.profile(True)
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        x.zero_()
+        theta, trace, info = step(x, dirty, delta)
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms, dev)
+    stats = plan.profile_stats()
+    plan.profile(False)
+    secs = ms / 1e3
+    value = job_value(vox * args.iters * args.steps, world, secs)
+    launches = sum(s["launches"] for s in stats)
+    dom = max(stats, key=lambda s: s["total_ms"])
+    tot_ms = sum(s["total_ms"] for s in stats)
+    avg_ms = dom["total_ms"] / dom["launches"]
+    peak, peak_kind = measured_peak_gbs()
+    achieved = dom["bytes_per_launch"] / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved,
+                "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "bytes_per_launch": dom["bytes_per_launch"],
+                "avg_launch_ms": avg_ms, "share": dom["total_ms"] / tot_ms}
+    kernels = sorted(({"name": s["name"], "launches": s["launches"],
+                       "ms": round(s["total_ms"], 3),
+                       "GBps": round(s["bytes_per_launch"] * s["launches"] /
+                                     (s["total_ms"] / 1e3) / 1e9, 1) if s["total_ms"] else None}
+                      for s in stats), key=lambda s: -s["ms"])
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        hd = torch.from_numpy(c.dirty).pin_memory()
+        hdl = torch.from_numpy(c.delta).pin_memory()
+        hx = torch.zeros(c.dirty.shape, dtype=torch.float32).pin_memory()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            hx.zero_()
+            step(hx, hd, hdl)
+        torch.cuda.synchronize()
+        barrier()
+        es = max_over_ranks(time.perf_counter() - t0, dev)
+        nbytes = c.dirty.nbytes
+        e2e = {"value": job_value(vox * args.iters * args.e2e_steps, world, es),
+               "unit": UNIT, "h2d_bytes_per_step": 3 * nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_obj(oracle_sample(args.workload))
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic", "config": workload_config(args),
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches, "clocks": clocks,
+               "theta": list(theta), "kernels": kernels,
+               "iter_ms": ms / args.steps / args.iters}
+        print(json.dumps(out), flush=True)
+    plan.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -200,6 +200,26 @@ MUFFIN_API muffin_status muffin_op_synthesis(muffin_plan plan, const float *u, f
 MUFFIN_API muffin_status muffin_op_dct(muffin_plan plan, const float *x, float *v,
                             int32_t inverse);
 
+/* ---- per-kernel profile --------------------------------------------------
+ * With profiling on, every kernel the plan launches is bracketed by CUDA
+ * events on the plan's stream; stats accumulate per kernel kind until the
+ * next muffin_profile_enable(plan, 1).  bytes/flops are the algorithmic
+ * (minimum) traffic and arithmetic of one launch. */
+typedef struct {
+  char name[40];
+  int64_t launches;
+  double total_ms;
+  double bytes_per_launch;
+  double flops_per_launch;
+} muffin_kernel_stat;
+
+/* on = 1 enables and clears the stats, 0 disables. */
+MUFFIN_API muffin_status muffin_profile_enable(muffin_plan plan, int32_t on);
+/* Copies up to capacity stats; *count = number of kernel kinds recorded. */
+MUFFIN_API muffin_status muffin_profile_read(muffin_plan plan,
+                                             muffin_kernel_stat *out,
+                                             int32_t capacity, int32_t *count);
+
 /* ---- host-only tables (no GPU needed) -----------------------------------
  * The FP64 tables the kernels are built from, for inspection and tests. */
 /* h[0 .. 2p-1]: db<p> scaling filter by spectral factorisation, 1 <= p <= 8. */

@@ -153,6 +153,19 @@ class Plan:
                  for r in rec[: info.records]]
         return (th[0], th[1]), trace, info
 
+    # -- profile
+    def profile(self, on: bool = True) -> None:
+        native.check(self._lib.muffin_profile_enable(self._h, int(on)))
+
+    def profile_stats(self) -> list:
+        cnt = ctypes.c_int32()
+        native.check(self._lib.muffin_profile_read(self._h, None, 0, ctypes.byref(cnt)))
+        arr = (native.KernelStat * max(1, cnt.value))()
+        native.check(self._lib.muffin_profile_read(self._h, arr, cnt.value, ctypes.byref(cnt)))
+        return [dict(name=a.name.decode(), launches=int(a.launches), total_ms=a.total_ms,
+                     bytes_per_launch=a.bytes_per_launch, flops_per_launch=a.flops_per_launch)
+                for a in arr[: cnt.value]]
+
     # -- checkpoints
     def state_export(self) -> bytes:
         sz = ctypes.c_size_t()

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
 }
 
 template <int CH, int MODE, int PT>
-cudaError_t launch_dct(const DctKArgs &a, cudaStream_t st) {
+cudaError_t launch_dct(const DctKArgs &a, cudaStream_t st, Prof *prof) {
   const size_t sm = (size_t)2 * CH * a.Lp * (PT + 8) * sizeof(float);
   static bool attr = false;
   if (!attr) {
@@ -203,16 +203,20 @@ cudaError_t launch_dct(const DctKArgs &a, cudaStream_t st) {
     attr = true;
   }
   const size_t N = (size_t)a.n * a.n;
+  const double vox = (double)N * a.L;
+  ProfScope ps(prof, MODE == WAVE_ITERATE ? "spectral_dual" : "spectral_op",
+               MODE == WAVE_ITERATE ? CH * vox * 20.0 : vox * 8.0,
+               (MODE == WAVE_ITERATE ? 2.0 : 1.0) * CH * 2.0 * a.L * vox, st);
   k_dct<CH, MODE, PT><<<(unsigned)((N + PT - 1) / PT), DT, sm, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int CH, int MODE>
-cudaError_t launch_dct_pt(const DctKArgs &a, cudaStream_t st) {
+cudaError_t launch_dct_pt(const DctKArgs &a, cudaStream_t st, Prof *prof) {
   // largest pixel tile whose two [CH][Lp][PT+8] buffers fit in ~160 KB
   const size_t per32 = (size_t)2 * CH * a.Lp * 40 * sizeof(float);
-  if (per32 <= 160 * 1024) return launch_dct<CH, MODE, 32>(a, st);
-  return launch_dct<CH, MODE, 16>(a, st);
+  if (per32 <= 160 * 1024) return launch_dct<CH, MODE, 32>(a, st, prof);
+  return launch_dct<CH, MODE, 16>(a, st, prof);
 }
 
 }  // namespace
@@ -223,8 +227,8 @@ cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st) {
   a.a1hi = d.chi; a.a1lo = d.clo; a.a2hi = d.cthi; a.a2lo = d.ctlo;
   a.alpha = d.alpha; a.sc = d.sc;
   a.xt = gr.xt; a.x = gr.x; a.v = gr.v; a.t = gr.t;
-  if (gr.C == 3) return launch_dct_pt<3, WAVE_ITERATE>(a, st);
-  return launch_dct_pt<1, WAVE_ITERATE>(a, st);
+  if (gr.C == 3) return launch_dct_pt<3, WAVE_ITERATE>(a, st, d.prof);
+  return launch_dct_pt<1, WAVE_ITERATE>(a, st, d.prof);
 }
 
 cudaError_t dct_op(const DctArgs &d, const float *in, float *out, int inverse,
@@ -234,7 +238,7 @@ cudaError_t dct_op(const DctArgs &d, const float *in, float *out, int inverse,
   a.a1hi = inverse ? d.cthi : d.chi;
   a.a1lo = inverse ? d.ctlo : d.clo;
   a.in = in; a.out = out;
-  return launch_dct_pt<1, WAVE_TRANSFORM>(a, st);
+  return launch_dct_pt<1, WAVE_TRANSFORM>(a, st, d.prof);
 }
 
 }  // namespace muffin

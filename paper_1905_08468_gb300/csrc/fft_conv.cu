@@ -191,7 +191,7 @@ inline int grid_for(size_t count) {
 
 cudaError_t launch_gradient(const float *x, float *g, const float *b,
                             float2 *S, const float *kspec, const float2 *tw,
-                            int n, int L, int C, cudaStream_t st) {
+                            int n, int L, int C, cudaStream_t st, Prof *prof) {
   const int nimg = C * L;
   const int RB = n < kRowBlock ? n : kRowBlock;
   const int nh = (n >> 1) + 1;
@@ -204,10 +204,25 @@ cudaError_t launch_gradient(const float *x, float *g, const float *b,
     cudaFuncSetAttribute(k_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  k_rows_fwd<<<dim3(n / RB, nimg), kThreads, smr, st>>>(x, S, n, RB, tw);
-  k_cols<<<dim3((nh + kColBlock - 1) / kColBlock, nimg), kThreads, smc, st>>>(
-      S, kspec, n, L, kColBlock, tw);
-  k_rows_inv<<<dim3(n / RB, nimg), kThreads, smr, st>>>(S, g, b, n, L, RB, tw);
+  const double img = (double)n * n, spec = (double)nh * n * 8.0;
+  const double fft = 5.0 * n * ilog2(n);   // flops of one length-n complex FFT
+  {
+    ProfScope ps(prof, "grad_rows_fwd", nimg * (img * 4.0 + spec),
+                 nimg * (n / 2.0) * fft, st);
+    k_rows_fwd<<<dim3(n / RB, nimg), kThreads, smr, st>>>(x, S, n, RB, tw);
+  }
+  {
+    ProfScope ps(prof, "grad_cols", nimg * 2.0 * spec + (double)L * nh * n * 4.0,
+                 nimg * (double)nh * 2.0 * fft, st);
+    k_cols<<<dim3((nh + kColBlock - 1) / kColBlock, nimg), kThreads, smc, st>>>(
+        S, kspec, n, L, kColBlock, tw);
+  }
+  {
+    ProfScope ps(prof, "grad_rows_inv",
+                 nimg * (spec + img * 4.0) + (b ? (double)L * img * 4.0 : 0.0),
+                 nimg * (n / 2.0) * fft, st);
+    k_rows_inv<<<dim3(n / RB, nimg), kThreads, smr, st>>>(S, g, b, n, L, RB, tw);
+  }
   return cudaGetLastError();
 }
 

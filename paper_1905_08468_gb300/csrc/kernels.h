@@ -5,9 +5,84 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
 #include "common.cuh"
 
 namespace muffin {
+
+// Per-kernel timing with CUDA events on the launching stream.  Launchers
+// call begin()/end() around every kernel when a profiler is attached; the
+// plan resolves the event pairs at the end of each API call.
+struct Prof {
+  struct Stat {
+    std::string name;
+    long long launches = 0;
+    double total_ms = 0, bytes = 0, flops = 0;   // bytes/flops per launch
+  };
+  struct Pending { int id; cudaEvent_t a, b; };
+  std::vector<Stat> stats;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t cur_a = nullptr;
+  int cur_id = -1;
+
+  int find(const char *name, double bytes, double flops) {
+    for (size_t i = 0; i < stats.size(); ++i)
+      if (stats[i].name == name && stats[i].bytes == bytes) return (int)i;
+    Stat s;
+    s.name = name; s.bytes = bytes; s.flops = flops;
+    stats.push_back(s);
+    return (int)stats.size() - 1;
+  }
+  cudaEvent_t take() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(const char *name, double bytes, double flops, cudaStream_t st) {
+    if (pending.size() >= 2048) resolve();
+    cur_id = find(name, bytes, flops);
+    cur_a = take();
+    cudaEventRecord(cur_a, st);
+  }
+  void end(cudaStream_t st) {
+    cudaEvent_t b = take();
+    cudaEventRecord(b, st);
+    pending.push_back({cur_id, cur_a, b});
+  }
+  void resolve() {
+    if (pending.empty()) return;
+    cudaEventSynchronize(pending.back().b);
+    for (const Pending &p : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        stats[p.id].total_ms += ms;
+        stats[p.id].launches += 1;
+      }
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.clear();
+    cudaGetLastError();
+  }
+  void reset() { resolve(); stats.clear(); }
+  ~Prof() {
+    resolve();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+// RAII bracket used by the launchers
+struct ProfScope {
+  Prof *p;
+  cudaStream_t st;
+  ProfScope(Prof *p_, const char *name, double bytes, double flops, cudaStream_t s)
+      : p(p_), st(s) { if (p) p->begin(name, bytes, flops, st); }
+  ~ProfScope() { if (p) p->end(st); }
+};
 
 // ------------------------------------------------------------ FFT (fft_conv.cu)
 // FP32 gradient pipeline: g[c][l] = H_l^T H_l x[c][l] - (c == 0 && b ? b[l] : 0)
@@ -15,7 +90,8 @@ namespace muffin {
 // kspec: [L][n/2+1][n] = |h_hat_l(ky, kx)|^2 / n^2 (kx-major).
 cudaError_t launch_gradient(const float *x, float *g, const float *b,
                             float2 *S, const float *kspec, const float2 *tw,
-                            int n, int L, int C, cudaStream_t st);
+                            int n, int L, int C, cudaStream_t st,
+                            Prof *prof = nullptr);
 
 // FP64 helpers used when a plan or a call is set up.
 // In-place 2D DFT of nimg complex n x n images; inverse is unnormalised.
@@ -92,6 +168,7 @@ struct WaveArgs {
   float *scratch;          // LL scratch: level j (1 <= j < J) holds
                            // [C][L][K][n>>j][n>>j] at scratch + lvl_off[j]
   size_t lvl_off[16];
+  Prof *prof;              // optional per-kernel timing
 };
 
 // Synthesis + primal prox (Alg. 2 eqs. adjointspat2, stpm, stpx and the
@@ -115,6 +192,7 @@ struct DctArgs {
   const float *cthi, *ctlo;// [Lp][Lp] C^T split
   const float *alpha;      // [n*n] pixel weights
   const DevScalars *sc;
+  Prof *prof;              // optional per-kernel timing
 };
 // Spectral dual update and back-projection (Alg. 2 eqs. vt, v, upt and the
 // derivative forms of Algs. 3/4): reads gr.xt, gr.x, gr.v -> gr.v, gr.t.

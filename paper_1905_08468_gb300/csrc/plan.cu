@@ -104,6 +104,10 @@ struct muffin_plan_s {
   // operator buffers (allocated on first use)
   float *op_in = nullptr, *op_out = nullptr, *op_b = nullptr;
 
+  Prof prof;
+  bool profiling = false;
+  Prof *pp() { return profiling ? &prof : nullptr; }
+
   double lipschitz = 0, Asum = 0, Bsum = 0, Amax2 = 0, Bmax2 = 0;
   double psure_const = 0;
   bool have_b = false, have_state = false, have_sure_state = false;
@@ -137,6 +141,7 @@ struct muffin_plan_s {
     w.n = n; w.L = L; w.K = K; w.J = J; w.C = Cmax;
     w.beta = beta; w.sc = sc; w.scratch = llscr;
     for (int j = 0; j < 16; ++j) w.lvl_off[j] = lvl_off[j];
+    w.prof = profiling ? const_cast<Prof *>(&prof) : nullptr;
     return w;
   }
   DctArgs dct() const {
@@ -144,6 +149,7 @@ struct muffin_plan_s {
     d.n = n; d.L = L; d.Lp = Lp; d.C = Cmax;
     d.chi = chi; d.clo = clo; d.cthi = cthi; d.ctlo = ctlo;
     d.alpha = alpha; d.sc = sc;
+    d.prof = profiling ? const_cast<Prof *>(&prof) : nullptr;
     return d;
   }
 };
@@ -209,7 +215,8 @@ muffin_status set_scalars(muffin_plan P, double mu, double gamma) {
 }
 
 muffin_status iterate_group(muffin_plan P, Group &g) {
-  CK(launch_gradient(g.x, g.g, g.b, P->S, P->kspec, P->tw32, P->n, P->L, g.C, P->st));
+  CK(launch_gradient(g.x, g.g, g.b, P->S, P->kspec, P->tw32, P->n, P->L, g.C, P->st,
+                     P->pp()));
   WaveArgs w = P->wave();
   w.C = g.C;
   CK(wavelet_synthesis_prox(w, g, P->p.positivity, P->st));
@@ -505,6 +512,7 @@ muffin_status muffin_solve(muffin_plan P, const float *dirty, float *x,
   s = store(P, g.x, x, P->NL);
   if (s != MUFFIN_OK) return s;
   CK(cudaStreamSynchronize(P->st));
+  P->prof.resolve();
   if (info) {
     info->iters_done = iters; info->tau = P->tau_for(mu, gamma); info->sigma = P->p.sigma;
     info->lipschitz = P->lipschitz; info->mu = mu; info->gamma = gamma;
@@ -587,13 +595,17 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
     if (P->k_done % sp->window == 0) {
       Group &g = P->grp[0];
       // gradient of the y-primal at the new x (chain 0 only)
-      CK(launch_gradient(g.x, g.g, g.b, P->S, P->kspec, P->tw32, P->n, P->L, 1, P->st));
+      CK(launch_gradient(g.x, g.g, g.b, P->S, P->kspec, P->tw32, P->n, P->L, 1, P->st,
+                         P->pp()));
       SureStatsArgs sa{};
       sa.grad = g.g; sa.x = g.x; sa.xb = P->grp[1].x; sa.b = P->b; sa.htd = P->htd;
       sa.wband = P->wband; sa.n = P->n; sa.L = P->L;
       int nb = 0;
       double *part = P->dred + kRedSure + 65 * (size_t)P->L;
-      CK(sure_stats(sa, part, &nb, P->st));
+      {
+        ProfScope ps(P->pp(), "sure_stats", 9.0 * NL * 4.0, 12.0 * NL, P->st);
+        CK(sure_stats(sa, part, &nb, P->st));
+      }
       ThetaUpdateArgs ta{};
       ta.sc = P->sc; ta.partials = part; ta.nblocks = nb;
       ta.record = P->records + 7 * nrec;
@@ -602,7 +614,10 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
       ta.psure_const = P->psure_const;
       ta.safety = P->p.tau_safety; ta.lipschitz = P->lipschitz; ta.K = P->K;
       ta.Bsum = rule_B; ta.Asum = rule_A;
-      CK(theta_update(ta, P->st));
+      {
+        ProfScope ps(P->pp(), "theta_update", 6.0 * 8.0 * nb, 0.0, P->st);
+        CK(theta_update(ta, P->st));
+      }
       ++nrec;
       if (sp->reset_each_window) {
         s = reset_derivs(P, P->grp[0]);
@@ -621,6 +636,7 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
     CK(cudaMemcpyAsync(rec.data(), P->records, (size_t)7 * nrec * sizeof(double),
                        cudaMemcpyDeviceToHost, P->st));
   CK(cudaStreamSynchronize(P->st));
+  P->prof.resolve();
   theta[0] = hs.mu; theta[1] = hs.gamma;
   P->cur_mu = hs.mu; P->cur_gamma = hs.gamma;
   if (trace)
@@ -634,6 +650,32 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
     info->iters_done = sp->iters; info->tau = hs.tau; info->sigma = P->p.sigma;
     info->lipschitz = P->lipschitz; info->mu = hs.mu; info->gamma = hs.gamma;
     info->records = nrec;
+  }
+  return MUFFIN_OK;
+}
+
+// ---------------------------------------------------------------- profile
+muffin_status muffin_profile_enable(muffin_plan P, int32_t on) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  P->prof.resolve();
+  if (on) P->prof.stats.clear();
+  P->profiling = on != 0;
+  return MUFFIN_OK;
+}
+
+muffin_status muffin_profile_read(muffin_plan P, muffin_kernel_stat *out,
+                                  int32_t capacity, int32_t *count) {
+  if (!P || !count) return fail(MUFFIN_EINVAL, "NULL argument");
+  P->prof.resolve();
+  *count = (int32_t)P->prof.stats.size();
+  for (int32_t i = 0; i < *count && i < capacity && out; ++i) {
+    const Prof::Stat &st = P->prof.stats[i];
+    std::memset(out[i].name, 0, sizeof(out[i].name));
+    std::strncpy(out[i].name, st.name.c_str(), sizeof(out[i].name) - 1);
+    out[i].launches = st.launches;
+    out[i].total_ms = st.total_ms;
+    out[i].bytes_per_launch = st.bytes;
+    out[i].flops_per_launch = st.flops;
   }
   return MUFFIN_OK;
 }

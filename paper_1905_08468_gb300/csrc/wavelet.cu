@@ -541,8 +541,20 @@ __global__ void k_ana0(AnaArgs a) {
 // ------------------------------------------------------------ launch helpers
 inline int tiles(int h) { return ((h + TX - 1) / TX) * ((h + TY - 1) / TY); }
 
+// algorithmic bytes and flops of one level launch (FP32)
+inline double level_flops(int CH, int L, int K, int h) {
+  return (double)CH * L * 32.0 * (K * (K + 1) / 2) * (double)h * h;
+}
+
 template <int CH, int MODE, bool L1>
-cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st) {
+cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st, Prof *prof) {
+  const double h = a.M >> 1, rw = MODE == WAVE_ITERATE ? 2.0 : 1.0;
+  const double in = L1 ? (double)CH * a.L * a.M * a.M * (MODE == WAVE_ITERATE ? 8.0 : 4.0)
+                       : (double)CH * a.L * a.K * a.M * a.M * 4.0;
+  const double det = (double)CH * a.L * a.K * 3.0 * h * h * 4.0 * rw;
+  const double ll = (double)CH * a.L * a.K * h * h * 4.0 * (a.last ? rw : 1.0);
+  ProfScope ps(prof, L1 ? "ana_level1_dual" : "ana_level_dual", in + det + ll,
+               level_flops(CH, a.L, L1 ? a.K : a.K, (int)h), st);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_ana<CH, MODE, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -554,7 +566,13 @@ cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st) {
 }
 
 template <int CH, int MODE, bool L1>
-cudaError_t launch_syn(const SynArgs &a, int nblk_y, cudaStream_t st) {
+cudaError_t launch_syn(const SynArgs &a, int nblk_y, cudaStream_t st, Prof *prof) {
+  const double h = a.M >> 1;
+  const double det = (double)CH * a.L * a.K * 4.0 * h * h * 4.0;   // 3 details + LL
+  const double out = L1 ? (double)CH * a.L * a.M * a.M * (MODE == WAVE_ITERATE ? 16.0 : 4.0)
+                        : (double)CH * a.L * a.K * a.M * a.M * 4.0;
+  ProfScope ps(prof, L1 ? "syn_level1_prox" : "syn_level", det + out,
+               level_flops(CH, a.L, a.K, (int)h), st);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_syn<CH, MODE, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -575,6 +593,7 @@ cudaError_t synthesis_all(const WaveArgs &w, const SynArgs &base, cudaStream_t s
   SynArgs a = base;
   if (w.J == 0) {
     a.M = w.n;
+    ProfScope ps(w.prof, "syn_identity_prox", (double)CH * w.L * w.n * w.n * 4.0 * (w.K + 4), 0.0, st);
     k_syn0<CH, MODE><<<grid_elem((size_t)w.L * w.n * w.n), 256, 0, st>>>(a);
     return cudaGetLastError();
   }
@@ -584,14 +603,14 @@ cudaError_t synthesis_all(const WaveArgs &w, const SynArgs &base, cudaStream_t s
     a.top = (j == w.J);
     a.ll_in = a.top ? nullptr : w.scratch + w.lvl_off[j];
     a.ll_out = w.scratch + w.lvl_off[j - 1];
-    e = launch_syn<CH, MODE, false>(a, w.L * w.K, st);
+    e = launch_syn<CH, MODE, false>(a, w.L * w.K, st, w.prof);
     if (e != cudaSuccess) return e;
   }
   a.M = w.n;
   a.top = (w.J == 1);
   a.ll_in = a.top ? nullptr : w.scratch + w.lvl_off[1];
   a.ll_out = nullptr;
-  return launch_syn<CH, MODE, true>(a, w.L, st);
+  return launch_syn<CH, MODE, true>(a, w.L, st, w.prof);
 }
 
 template <int CH, int MODE>
@@ -599,19 +618,20 @@ cudaError_t analysis_all(const WaveArgs &w, const AnaArgs &base, cudaStream_t st
   AnaArgs a = base;
   if (w.J == 0) {
     a.M = w.n;
+    ProfScope ps(w.prof, "ana_identity_dual", (double)CH * w.L * w.n * w.n * 4.0 * (2 * w.K + 2), 0.0, st);
     k_ana0<CH, MODE><<<grid_elem((size_t)w.L * w.n * w.n), 256, 0, st>>>(a);
     return cudaGetLastError();
   }
   a.M = w.n;
   a.last = (w.J == 1);
   a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[1];
-  cudaError_t e = launch_ana<CH, MODE, true>(a, w.L, st);
+  cudaError_t e = launch_ana<CH, MODE, true>(a, w.L, st, w.prof);
   for (int j = 2; j <= w.J && e == cudaSuccess; ++j) {
     a.M = w.n >> (j - 1);
     a.in = w.scratch + w.lvl_off[j - 1];
     a.last = (j == w.J);
     a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[j];
-    e = launch_ana<CH, MODE, false>(a, w.L * w.K, st);
+    e = launch_ana<CH, MODE, false>(a, w.L * w.K, st, w.prof);
   }
   return e;
 }

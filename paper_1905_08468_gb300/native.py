@@ -37,6 +37,12 @@ class SureRecord(ctypes.Structure):
                 ("psure", c_double), ("tau", c_double)]
 
 
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64),
+                ("total_ms", c_double), ("bytes_per_launch", c_double),
+                ("flops_per_launch", c_double)]
+
+
 STATUS = {0: "MUFFIN_OK", 1: "MUFFIN_EINVAL", 2: "MUFFIN_ENOMEM", 3: "MUFFIN_ECUDA",
           4: "MUFFIN_ETIMEOUT", 5: "MUFFIN_ENUMERIC", 6: "MUFFIN_ESTATE"}
 MUFFIN_WARM = 1
@@ -63,6 +69,9 @@ SIGNATURES = {
     "muffin_op_analysis": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "muffin_op_synthesis": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "muffin_op_dct": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
+    "muffin_profile_enable": (c_int32, [c_void_p, c_int32]),
+    "muffin_profile_read": (c_int32, [c_void_p, ctypes.POINTER(KernelStat), c_int32,
+                                      ctypes.POINTER(c_int32)]),
     "muffin_filter_taps": (c_int32, [c_int32, ctypes.POINTER(c_double)]),
     "muffin_dct_table": (c_int32, [c_int32, ctypes.POINTER(c_double)]),
     "muffin_last_error": (ctypes.c_char_p, []),

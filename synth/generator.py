@@ -40,6 +40,8 @@ WORKLOADS = {
     "c3_1024x1024x64": (1024, 64, 2000, 100, 200000, 3),
     "c5_2048x2048x256": (2048, 256, 8000, 400, 1000000, 5),
     "c5crop_256x256x16": (256, 16, 125, 6, 15625, 5),
+    # a mid-size cube for profiler captures (state ~2 GB, inputs > L2)
+    "prof_512x512x32": (512, 32, 500, 25, 50000, 6),
 }
 
 
