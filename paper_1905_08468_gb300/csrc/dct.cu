@@ -193,6 +193,145 @@ __global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
   }
 }
 
+// Iteration kernel for L <= 64 (one 16-row m-tile per warp): the input
+// tile is loaded with 16-byte loads, both chains' products of the first GEMM
+// stay in registers, and the updated duals overwrite the input tile in
+// shared memory, so a CTA needs a single [CH][Lp][PT+8] buffer (higher
+// occupancy for this HBM-bound step).
+template <int CH, int PT>
+__global__ void __launch_bounds__(DT, 5) k_dct_small(DctKArgs a) {
+  extern __shared__ float sm[];
+  constexpr int PP = PT + 8;
+  const int Lp = a.Lp, L = a.L;
+  float *zb = sm;                        // [CH][Lp][PP]
+  const size_t N = (size_t)a.n * a.n;
+  const size_t CS = (size_t)L * N;
+  const size_t n0 = (size_t)blockIdx.x * PT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const float gamma = (float)a.sc->gamma;
+  const float sigma = (float)a.sc->sigma;
+  const bool full = n0 + PT <= N;
+  for (int it = threadIdx.x; it < Lp * (PT / 4); it += DT) {
+    const int l = it / (PT / 4), p4 = (it - l * (PT / 4)) * 4;
+    float z[CH][4];
+    if (l < L && full) {
+      const size_t j = (size_t)l * N + n0 + p4;
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const float4 xt = *reinterpret_cast<const float4 *>(a.xt + c * CS + j);
+        const float4 xx = *reinterpret_cast<const float4 *>(a.x + c * CS + j);
+        z[c][0] = 2.f * xt.x - xx.x; z[c][1] = 2.f * xt.y - xx.y;
+        z[c][2] = 2.f * xt.z - xx.z; z[c][3] = 2.f * xt.w - xx.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const size_t pix = n0 + p4 + e;
+          const size_t j = (size_t)l * N + pix;
+          z[c][e] = (l < L && pix < N) ? 2.f * a.xt[c * CS + j] - a.x[c * CS + j] : 0.f;
+        }
+    }
+    if (CH == 3)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) z[2][e] = fmaf(gamma, z[2][e], z[0][e]);  // Algorithm 4
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) zb[(c * Lp + l) * PP + p4 + e] = z[c][e];
+  }
+  __syncthreads();
+  const int mt = warp;
+  const bool has = mt * 16 < Lp;
+  float acc[CH][PT / 8][4];
+  if (has) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+      tile_gemm<PT>(a.a1hi, a.a1lo, Lp, mt * 16, zb + c * Lp * PP, PP, acc[c]);
+  }
+  __syncthreads();
+  if (has) {
+#pragma unroll
+    for (int nt = 0; nt < PT / 8; ++nt) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k = mt * 16 + g + (e >= 2 ? 8 : 0);
+        const int p = nt * 8 + 2 * t + (e & 1);
+        const size_t pix = n0 + p;
+        const bool valid = k < L && pix < N;
+        const size_t j = (size_t)k * N + pix;
+        float al = 0.f, vc[CH];
+        if (valid) {
+          al = a.alpha[pix];
+#pragma unroll
+          for (int c = 0; c < CH; ++c) vc[c] = a.v[c * CS + j];
+        }
+        bool keep = false;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          float vn = 0.f;
+          if (valid) {
+            const float s1 = (c == 2) ? sigma * al : sigma * gamma * al;
+            const float vt = fmaf(s1, acc[c][nt][e], vc[c]);
+            if (c == 0) { vn = satf(vt); keep = fabsf(vt) <= 1.f; }
+            else vn = keep ? vt : 0.f;
+            a.v[c * CS + j] = vn;
+          }
+          zb[(c * Lp + k) * PP + p] = vn;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (CH == 3) {
+    for (int it = threadIdx.x; it < Lp * PT; it += DT) {
+      const int l = it / PT, p = it - l * PT;
+      float *d = zb + (2 * Lp + l) * PP + p;
+      *d = fmaf(gamma, *d, zb[l * PP + p]);     // gamma v'_gamma + v
+    }
+    __syncthreads();
+  }
+  if (has) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      float acc2[PT / 8][4];
+      tile_gemm<PT>(a.a2hi, a.a2lo, Lp, mt * 16, zb + c * Lp * PP, PP, acc2);
+#pragma unroll
+      for (int nt = 0; nt < PT / 8; ++nt) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int l = mt * 16 + g + (e >= 2 ? 8 : 0);
+          const int p = nt * 8 + 2 * t + (e & 1);
+          const size_t pix = n0 + p;
+          if (l < L && pix < N) {
+            const float al = a.alpha[pix];
+            const float s2 = (c == 2) ? al : gamma * al;
+            a.t[c * CS + (size_t)l * N + pix] = s2 * acc2[nt][e];
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int CH>
+cudaError_t launch_dct_small(const DctKArgs &a, cudaStream_t st, Prof *prof) {
+  constexpr int PT = 32;
+  const size_t sm = (size_t)CH * a.Lp * (PT + 8) * sizeof(float);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_dct_small<CH, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    attr = true;
+  }
+  const size_t N = (size_t)a.n * a.n;
+  const double vox = (double)N * a.L;
+  ProfScope ps(prof, "spectral_dual", CH * vox * 20.0, 2.0 * CH * 2.0 * a.L * vox, st);
+  k_dct_small<CH, PT><<<(unsigned)((N + PT - 1) / PT), DT, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int CH, int MODE, int PT>
 cudaError_t launch_dct(const DctKArgs &a, cudaStream_t st, Prof *prof) {
   const size_t sm = (size_t)2 * CH * a.Lp * (PT + 8) * sizeof(float);
@@ -227,6 +366,10 @@ cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st) {
   a.a1hi = d.chi; a.a1lo = d.clo; a.a2hi = d.cthi; a.a2lo = d.ctlo;
   a.alpha = d.alpha; a.sc = d.sc;
   a.xt = gr.xt; a.x = gr.x; a.v = gr.v; a.t = gr.t;
+  if (d.Lp <= 64) {
+    if (gr.C == 3) return launch_dct_small<3>(a, st, d.prof);
+    return launch_dct_small<1>(a, st, d.prof);
+  }
   if (gr.C == 3) return launch_dct_pt<3, WAVE_ITERATE>(a, st, d.prof);
   return launch_dct_pt<1, WAVE_ITERATE>(a, st, d.prof);
 }

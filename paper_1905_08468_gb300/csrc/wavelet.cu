@@ -49,10 +49,10 @@ constexpr int S_LP = S_CP;                           // column-pass output pitch
 constexpr int QXP = 4, QYP = 2;                      // coefficient pairs per thread
 
 constexpr size_t ana_smem(int ch) {
-  return (size_t)ch * (A_RH * A_IP + 2 * A_RH * A_LP) * sizeof(float);
+  return ((size_t)ch * A_RH * A_IP + 2 * A_RH * A_LP) * sizeof(float);
 }
-constexpr size_t syn_smem(int ch) {
-  return (size_t)ch * (4 * S_CH * S_CP + 2 * (2 * TY) * S_LP) * sizeof(float);
+constexpr size_t syn_smem(int) {
+  return (size_t)(8 * S_CH * S_CP + 2 * (2 * TY) * S_LP) * sizeof(float);
 }
 
 struct AnaArgs {
@@ -100,26 +100,54 @@ __device__ __forceinline__ void ana_emit(const AnaArgs &a, int l, int bb,
   }
 }
 
-template <int P, int CH, int MODE>
-__device__ __forceinline__ void ana_basis(const AnaArgs &a, const float *in_s,
-                                          float *lo_s, float *hi_s, int l,
-                                          int bb, int kx0, int ky0,
-                                          const float (&q)[CH]) {
+// One (basis, chain) step of an analysis level: rows of the resident input
+// tile -> lo/hi, then the thread's own column item (TY/QY x TX items ==
+// NT threads): four subbands of QY coefficients, fused with the dual update.
+// The U values the item updates are loaded before the row pass so their
+// latency overlaps the filtering.  Channel 0 records the mask Pi(p) of each
+// output in `keep`; derivative channels (c > 0) apply it.
+template <int P, int MODE>
+__device__ __forceinline__ void ana_step(const AnaArgs &a, const float *in_c,
+                                         float *lo_s, float *hi_s, int l, int bb,
+                                         int c, int kx0, int ky0, float q,
+                                         uint32_t &keep) {
   constexpr int RH = 2 * TY + 2 * P - 2;
   constexpr int NSX = TX / QX;
   constexpr int NV = 2 * QX + 2 * P - 2;
+  constexpr int NW = 2 * QY + 2 * P - 2;
+  static_assert((TY / QY) * TX == NT, "one column item per thread");
+  const int h = a.M >> 1;
+  const int kx = threadIdx.x % TX, s = threadIdx.x / TX;
+  const int kxg = kx0 + kx;
+  const size_t NN = (size_t)a.n * a.n;
+  float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * NN;
+  // prefetch: subbands DX (low y, high x), DY (high y, low x), HH, LL
+  float pre[4][QY];
+  size_t off[4][QY];
+  bool act[QY];
+#pragma unroll
+  for (int qq = 0; qq < QY; ++qq) {
+    const int ky = ky0 + QY * s + qq;
+    act[qq] = ky < h && kxg < h;
+    off[0][qq] = (size_t)ky * a.n + h + kxg;
+    off[1][qq] = (size_t)(h + ky) * a.n + kxg;
+    off[2][qq] = (size_t)(h + ky) * a.n + h + kxg;
+    off[3][qq] = (size_t)ky * a.n + kxg;
+#pragma unroll
+    for (int sb = 0; sb < 4; ++sb) pre[sb][qq] = 0.f;
+    if (MODE == WAVE_ITERATE && act[qq]) {
+#pragma unroll
+      for (int sb = 0; sb < 3; ++sb) pre[sb][qq] = up[off[sb][qq]];
+      if (a.last) pre[3][qq] = up[off[3][qq]];
+    }
+  }
   // rows: lo/hi along x
-  for (int it = threadIdx.x; it < CH * RH * NSX; it += NT) {
-    const int r = it % RH;
-    const int rest = it / RH;
-    const int s = rest % NSX;
-    const int c = rest / NSX;
-    const float *src = in_s + (c * A_RH + r) * A_IP + 2 * QX * s;
+  for (int it = threadIdx.x; it < RH * NSX; it += NT) {
+    const int r = it % RH, sx = it / RH;
+    const float *src = in_c + r * A_IP + 2 * QX * sx;
     float v[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] = src[i];
-    float *dl = lo_s + (c * A_RH + r) * A_LP + QX * s;
-    float *dh = hi_s + (c * A_RH + r) * A_LP + QX * s;
 #pragma unroll
     for (int qq = 0; qq < QX; ++qq) {
       float lo = 0.f, hi = 0.f;
@@ -128,93 +156,86 @@ __device__ __forceinline__ void ana_basis(const AnaArgs &a, const float *in_s,
         lo = fmaf(c_h[P - 1][i], v[2 * qq + i], lo);
         hi = fmaf(c_g[P - 1][i], v[2 * qq + i], hi);
       }
-      dl[qq] = lo;
-      dh[qq] = hi;
+      lo_s[r * A_LP + QX * sx + qq] = lo;
+      hi_s[r * A_LP + QX * sx + qq] = hi;
     }
   }
   __syncthreads();
-  // columns: four subbands, then the update
-  constexpr int NSY = TY / QY;
-  constexpr int NW = 2 * QY + 2 * P - 2;
-  const int h = a.M >> 1;
-  for (int it = threadIdx.x; it < NSY * TX; it += NT) {
-    const int kx = it % TX, s = it / TX;
-    float cLL[CH][QY], cDY[CH][QY], cDX[CH][QY], cHH[CH][QY];
+  // columns: the thread's item
+  float cf[4][QY];
+  {
+    const float *pl = lo_s + (2 * QY * s) * A_LP + kx;
+    const float *ph = hi_s + (2 * QY * s) * A_LP + kx;
+    float vl[NW], vh[NW];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const float *pl = lo_s + (c * A_RH + 2 * QY * s) * A_LP + kx;
-      const float *ph = hi_s + (c * A_RH + 2 * QY * s) * A_LP + kx;
-      float vl[NW], vh[NW];
+    for (int i = 0; i < NW; ++i) { vl[i] = pl[i * A_LP]; vh[i] = ph[i * A_LP]; }
 #pragma unroll
-      for (int i = 0; i < NW; ++i) { vl[i] = pl[i * A_LP]; vh[i] = ph[i * A_LP]; }
+    for (int qq = 0; qq < QY; ++qq) {
+      float ll = 0.f, dy = 0.f, dx = 0.f, hh = 0.f;
 #pragma unroll
-      for (int qq = 0; qq < QY; ++qq) {
-        float ll = 0.f, dy = 0.f, dx = 0.f, hh = 0.f;
-#pragma unroll
-        for (int i = 0; i < 2 * P; ++i) {
-          ll = fmaf(c_h[P - 1][i], vl[2 * qq + i], ll);
-          dy = fmaf(c_g[P - 1][i], vl[2 * qq + i], dy);
-          dx = fmaf(c_h[P - 1][i], vh[2 * qq + i], dx);
-          hh = fmaf(c_g[P - 1][i], vh[2 * qq + i], hh);
-        }
-        cLL[c][qq] = ll; cDY[c][qq] = dy; cDX[c][qq] = dx; cHH[c][qq] = hh;
+      for (int i = 0; i < 2 * P; ++i) {
+        ll = fmaf(c_h[P - 1][i], vl[2 * qq + i], ll);
+        dy = fmaf(c_g[P - 1][i], vl[2 * qq + i], dy);
+        dx = fmaf(c_h[P - 1][i], vh[2 * qq + i], dx);
+        hh = fmaf(c_g[P - 1][i], vh[2 * qq + i], hh);
       }
+      cf[0][qq] = dx; cf[1][qq] = dy; cf[2][qq] = hh; cf[3][qq] = ll;
     }
-    const int kxg = kx0 + kx;
-    if (kxg < h) {
+  }
+  if (c == 0) keep = 0;
 #pragma unroll
-      for (int qq = 0; qq < QY; ++qq) {
-        const int ky = ky0 + QY * s + qq;
-        if (ky >= h) continue;
-        float t[CH];
+  for (int qq = 0; qq < QY; ++qq) {
+    if (!act[qq]) continue;
+    const int ky = ky0 + QY * s + qq;
+    const int nsb = a.last ? 4 : 3;
 #pragma unroll
-        for (int c = 0; c < CH; ++c) t[c] = cDX[c][qq];
-        ana_emit<CH, MODE>(a, l, bb, ky, h + kxg, t, q);
-#pragma unroll
-        for (int c = 0; c < CH; ++c) t[c] = cDY[c][qq];
-        ana_emit<CH, MODE>(a, l, bb, h + ky, kxg, t, q);
-#pragma unroll
-        for (int c = 0; c < CH; ++c) t[c] = cHH[c][qq];
-        ana_emit<CH, MODE>(a, l, bb, h + ky, h + kxg, t, q);
-#pragma unroll
-        for (int c = 0; c < CH; ++c) t[c] = cLL[c][qq];
-        if (a.last) {
-          ana_emit<CH, MODE>(a, l, bb, ky, kxg, t, q);
+    for (int sb = 0; sb < 4; ++sb) {
+      if (sb >= nsb) break;
+      float val;
+      if (MODE == WAVE_TRANSFORM) {
+        val = cf[sb][qq];
+      } else {
+        const float p = fmaf(q, cf[sb][qq], pre[sb][qq]);
+        const uint32_t bit = 1u << (sb * QY + qq);
+        if (c == 0) {
+          val = satf(p);
+          if (fabsf(p) <= 1.0f) keep |= bit;
         } else {
-#pragma unroll
-          for (int c = 0; c < CH; ++c)
-            a.ll_out[(((size_t)(c * a.L + l) * a.K + bb) * h + ky) * h + kxg] = t[c];
+          val = (keep & bit) ? p : 0.f;
         }
       }
+      up[off[sb][qq]] = val;
     }
+    if (!a.last)
+      a.ll_out[(((size_t)(c * a.L + l) * a.K + bb) * h + ky) * h + kxg] = cf[3][qq];
   }
   __syncthreads();
 }
 
-template <int CH, int MODE>
+template <int MODE>
 __device__ __forceinline__ void ana_dispatch(int p, const AnaArgs &a,
-                                             const float *in_s, float *lo_s,
-                                             float *hi_s, int l, int bb,
-                                             int kx0, int ky0,
-                                             const float (&q)[CH]) {
+                                             const float *in_c, float *lo_s,
+                                             float *hi_s, int l, int bb, int c,
+                                             int kx0, int ky0, float q,
+                                             uint32_t &keep) {
   switch (p) {
-    case 1: ana_basis<1, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
-    case 2: ana_basis<2, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
-    case 3: ana_basis<3, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
-    case 4: ana_basis<4, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
-    case 5: ana_basis<5, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
-    case 6: ana_basis<6, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
-    case 7: ana_basis<7, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
-    default: ana_basis<8, CH, MODE>(a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q); break;
+    case 1: ana_step<1, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
+    case 2: ana_step<2, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
+    case 3: ana_step<3, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
+    case 4: ana_step<4, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
+    case 5: ana_step<5, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
+    case 6: ana_step<6, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
+    case 7: ana_step<7, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
+    default: ana_step<8, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
   }
 }
 
 template <int CH, int MODE, bool LEVEL1>
-__global__ void __launch_bounds__(NT) k_ana(AnaArgs a) {
+__global__ void __launch_bounds__(NT, 3) k_ana(AnaArgs a) {
   extern __shared__ float smem[];
-  float *in_s = smem;
-  float *lo_s = in_s + CH * A_RH * A_IP;
-  float *hi_s = lo_s + CH * A_RH * A_LP;
+  float *in_s = smem;                       // [CH][A_RH][A_IP]
+  float *lo_s = in_s + CH * A_RH * A_IP;    // [A_RH][A_LP]
+  float *hi_s = lo_s + A_RH * A_LP;
   const int h = a.M >> 1;
   const int ntx = (h + TX - 1) / TX;
   const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
@@ -225,16 +246,10 @@ __global__ void __launch_bounds__(NT) k_ana(AnaArgs a) {
   const int Mm = a.M - 1;
   const size_t NN = (size_t)a.n * a.n;
   const size_t CS = (size_t)a.L * NN;   // channel stride of images
-  float mu = 0.f;
-  float q[CH];
+  float mu = 0.f, sbl = 1.f;
   if (MODE == WAVE_ITERATE) {
     mu = (float)a.sc->mu;
-    const float sb = (float)(a.sc->sigma * (double)a.beta[l]);
-    q[0] = sb * mu;
-    if (CH == 3) { q[1] = sb; q[2] = sb * mu; }
-  } else {
-#pragma unroll
-    for (int c = 0; c < CH; ++c) q[c] = 1.f;
+    sbl = (float)(a.sc->sigma * (double)a.beta[l]);
   }
   for (int it = threadIdx.x; it < RH * RW; it += NT) {
     const int r = it / RW, cc = it - r * RW;
@@ -261,11 +276,16 @@ __global__ void __launch_bounds__(NT) k_ana(AnaArgs a) {
     for (int c = 0; c < CH; ++c) in_s[(c * A_RH + r) * A_IP + cc] = w[c];
   }
   __syncthreads();
-  if (LEVEL1) {
-    for (int bb = 0; bb < a.K; ++bb)
-      ana_dispatch<CH, MODE>(bb + 1, a, in_s, lo_s, hi_s, l, bb, kx0, ky0, q);
-  } else {
-    ana_dispatch<CH, MODE>(b + 1, a, in_s, lo_s, hi_s, l, b, kx0, ky0, q);
+  uint32_t keep = 0;
+  const int b0 = LEVEL1 ? 0 : b, b1 = LEVEL1 ? a.K : b + 1;
+  for (int bb = b0; bb < b1; ++bb) {
+#pragma unroll 1
+    for (int c = 0; c < CH; ++c) {
+      // dual step scale: sigma mu_l (primal, d/dgamma), sigma beta_l (d/dmu)
+      const float qc = MODE == WAVE_ITERATE ? (c == 1 ? sbl : sbl * mu) : 1.f;
+      ana_dispatch<MODE>(bb + 1, a, in_s + c * A_RH * A_IP, lo_s, hi_s, l, bb, c,
+                         kx0, ky0, qc, keep);
+    }
   }
 }
 
@@ -273,28 +293,65 @@ __global__ void __launch_bounds__(NT) k_ana(AnaArgs a) {
 // Inverse of one level: lo/hi along y from (LL, DY) and (DX, HH), then the
 // rows.  x[2k+e] = sum_s h[2s+e] a[k-s] + g[2s+e] d[k-s] (transpose of the
 // analysis, indices mod the level size).
-template <int P, int CH>
-__device__ __forceinline__ void syn_basis(const float *cf, float *lo_s,
-                                          float *hi_s, float (&acc)[CH][2 * QXP],
-                                          bool accumulate) {
-  // cf: [4][CH][S_CH][S_CP] subbands LL, DY, DX, HH; row 0 = coefficient ky0-(P-1)
+//
+// A CTA walks (basis, chain) steps; the coefficient tiles of the next step
+// are copied global->shared with cp.async while the current step computes
+// (double buffer).  Steps are pure per chain: by linearity the d/dmu chain's
+// synthesis of (u + mu u'_mu) (Algorithm 3) is accumulated as
+// W^T u + mu W^T u'_mu from the chain-0 and chain-1 steps.
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+constexpr int SUB = S_CH * S_CP;   // one subband tile in shared memory
+
+// issue the copies of the four subband tiles of (basis bb, chain c)
+__device__ __forceinline__ void syn_issue(const SynArgs &a, float *cf, int l,
+                                          int bb, int c, int kx0, int ky0) {
+  const int P = bb + 1;
+  const int h = a.M >> 1, hm = h - 1;
+  const int R = TY + P - 1, W = TX + P - 1;
+  const size_t NN = (size_t)a.n * a.n;
+  const float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * NN;
+  const float *lp = a.top ? nullptr
+                          : a.ll_in + ((size_t)(c * a.L + l) * a.K + bb) * h * h;
+  for (int it = threadIdx.x; it < R * W; it += NT) {
+    const int r = it / W, cc = it - r * W;
+    const int ky = (ky0 - (P - 1) + r) & hm, kx = (kx0 - (P - 1) + cc) & hm;
+    const int o = r * S_CP + cc;
+    cp_async4(cf + o, a.top ? up + (size_t)ky * a.n + kx : lp + (size_t)ky * h + kx);
+    cp_async4(cf + SUB + o, up + (size_t)(h + ky) * a.n + kx);          // DY
+    cp_async4(cf + 2 * SUB + o, up + (size_t)ky * a.n + h + kx);        // DX
+    cp_async4(cf + 3 * SUB + o, up + (size_t)(h + ky) * a.n + h + kx);  // HH
+  }
+}
+
+// one step: column pass into lo/hi, then the thread's row item -> o[8]
+template <int P>
+__device__ __forceinline__ void syn_step(const float *cf, float *lo_s, float *hi_s,
+                                         float (&o)[2 * QXP]) {
   constexpr int NCOL = TX + P - 1;
   constexpr int NSY = TY / QYP;
   constexpr int NWC = QYP + P - 1;
-  const float *cLL = cf, *cDY = cf + CH * S_CH * S_CP, *cDX = cf + 2 * CH * S_CH * S_CP,
-              *cHH = cf + 3 * CH * S_CH * S_CP;
-  for (int it = threadIdx.x; it < CH * NSY * NCOL; it += NT) {
-    const int kc = it % NCOL;
-    const int rest = it / NCOL;
-    const int sy = rest % NSY, c = rest / NSY;
-    const int base = (c * S_CH + QYP * sy) * S_CP + kc;
+  for (int it = threadIdx.x; it < NSY * NCOL; it += NT) {
+    const int kc = it % NCOL, sy = it / NCOL;
+    const int base = (QYP * sy) * S_CP + kc;
     float vLL[NWC], vDY[NWC], vDX[NWC], vHH[NWC];
 #pragma unroll
     for (int i = 0; i < NWC; ++i) {
-      vLL[i] = cLL[base + i * S_CP];
-      vDY[i] = cDY[base + i * S_CP];
-      vDX[i] = cDX[base + i * S_CP];
-      vHH[i] = cHH[base + i * S_CP];
+      vLL[i] = cf[base + i * S_CP];
+      vDY[i] = cf[SUB + base + i * S_CP];
+      vDX[i] = cf[2 * SUB + base + i * S_CP];
+      vHH[i] = cf[3 * SUB + base + i * S_CP];
     }
 #pragma unroll
     for (int qq = 0; qq < QYP; ++qq) {
@@ -310,140 +367,106 @@ __device__ __forceinline__ void syn_basis(const float *cf, float *lo_s,
           hi = fmaf(c_g[P - 1][2 * s + e], vHH[ci], hi);
         }
         const int my = 2 * (QYP * sy + qq) + e;
-        lo_s[(c * 2 * TY + my) * S_LP + kc] = lo;
-        hi_s[(c * 2 * TY + my) * S_LP + kc] = hi;
+        lo_s[my * S_LP + kc] = lo;
+        hi_s[my * S_LP + kc] = hi;
       }
     }
   }
   __syncthreads();
-  // rows: thread owns output row my, pixels 8 sx .. 8 sx + 7
   constexpr int NWR = QXP + P - 1;
-  {
-    const int it = threadIdx.x;
-    const int sx = it % (TX / QXP), my = it / (TX / QXP);
+  const int sx = threadIdx.x % (TX / QXP), my = threadIdx.x / (TX / QXP);
+  const float *pl = lo_s + my * S_LP + QXP * sx;
+  const float *ph = hi_s + my * S_LP + QXP * sx;
+  float vl[NWR], vh[NWR];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const float *pl = lo_s + (c * 2 * TY + my) * S_LP + QXP * sx;
-      const float *ph = hi_s + (c * 2 * TY + my) * S_LP + QXP * sx;
-      float vl[NWR], vh[NWR];
+  for (int i = 0; i < NWR; ++i) { vl[i] = pl[i]; vh[i] = ph[i]; }
 #pragma unroll
-      for (int i = 0; i < NWR; ++i) { vl[i] = pl[i]; vh[i] = ph[i]; }
+  for (int qq = 0; qq < QXP; ++qq) {
 #pragma unroll
-      for (int qq = 0; qq < QXP; ++qq) {
+    for (int e = 0; e < 2; ++e) {
+      float v = 0.f;
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          float o = 0.f;
-#pragma unroll
-          for (int s = 0; s < P; ++s) {
-            const int ci = qq + P - 1 - s;
-            o = fmaf(c_h[P - 1][2 * s + e], vl[ci], o);
-            o = fmaf(c_g[P - 1][2 * s + e], vh[ci], o);
-          }
-          if (accumulate) acc[c][2 * qq + e] += o; else acc[c][2 * qq + e] = o;
-        }
+      for (int s = 0; s < P; ++s) {
+        const int ci = qq + P - 1 - s;
+        v = fmaf(c_h[P - 1][2 * s + e], vl[ci], v);
+        v = fmaf(c_g[P - 1][2 * s + e], vh[ci], v);
       }
+      o[2 * qq + e] = v;
     }
   }
-  __syncthreads();
 }
 
-template <int CH>
 __device__ __forceinline__ void syn_dispatch(int p, const float *cf, float *lo_s,
-                                             float *hi_s, float (&acc)[CH][2 * QXP],
-                                             bool accumulate) {
+                                             float *hi_s, float (&o)[2 * QXP]) {
   switch (p) {
-    case 1: syn_basis<1, CH>(cf, lo_s, hi_s, acc, accumulate); break;
-    case 2: syn_basis<2, CH>(cf, lo_s, hi_s, acc, accumulate); break;
-    case 3: syn_basis<3, CH>(cf, lo_s, hi_s, acc, accumulate); break;
-    case 4: syn_basis<4, CH>(cf, lo_s, hi_s, acc, accumulate); break;
-    case 5: syn_basis<5, CH>(cf, lo_s, hi_s, acc, accumulate); break;
-    case 6: syn_basis<6, CH>(cf, lo_s, hi_s, acc, accumulate); break;
-    case 7: syn_basis<7, CH>(cf, lo_s, hi_s, acc, accumulate); break;
-    default: syn_basis<8, CH>(cf, lo_s, hi_s, acc, accumulate); break;
+    case 1: syn_step<1>(cf, lo_s, hi_s, o); break;
+    case 2: syn_step<2>(cf, lo_s, hi_s, o); break;
+    case 3: syn_step<3>(cf, lo_s, hi_s, o); break;
+    case 4: syn_step<4>(cf, lo_s, hi_s, o); break;
+    case 5: syn_step<5>(cf, lo_s, hi_s, o); break;
+    case 6: syn_step<6>(cf, lo_s, hi_s, o); break;
+    case 7: syn_step<7>(cf, lo_s, hi_s, o); break;
+    default: syn_step<8>(cf, lo_s, hi_s, o); break;
   }
-}
-
-template <int CH, int MODE>
-__device__ __forceinline__ void syn_load(const SynArgs &a, float *cf, int l,
-                                         int bb, int kx0, int ky0, float mu) {
-  const int P = bb + 1;
-  const int h = a.M >> 1, hm = h - 1;
-  const int R = TY + P - 1, W = TX + P - 1;
-  const size_t NN = (size_t)a.n * a.n;
-  const size_t US = (size_t)a.L * a.K * NN;   // channel stride of U
-  const float *u0 = a.u + ((size_t)l * a.K + bb) * NN;
-  for (int it = threadIdx.x; it < R * W; it += NT) {
-    const int r = it / W, cc = it - r * W;
-    const int ky = (ky0 - (P - 1) + r) & hm, kx = (kx0 - (P - 1) + cc) & hm;
-    const size_t oDX = (size_t)ky * a.n + h + kx, oDY = (size_t)(h + ky) * a.n + kx,
-                 oHH = (size_t)(h + ky) * a.n + h + kx, oLL = (size_t)ky * a.n + kx;
-    float vDX[CH], vDY[CH], vHH[CH], vLL[CH];
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const float *uc = u0 + c * US;
-      vDX[c] = uc[oDX]; vDY[c] = uc[oDY]; vHH[c] = uc[oHH];
-      vLL[c] = a.top ? uc[oLL]
-                     : a.ll_in[(((size_t)(c * a.L + l) * a.K + bb) * h + ky) * h + kx];
-    }
-    if (MODE == WAVE_ITERATE && CH == 3) {
-      // Algorithm 3: s' = beta_l W_s^T (u + mu u'_mu); LL from scratch is combined already
-      vDX[1] = fmaf(mu, vDX[1], vDX[0]);
-      vDY[1] = fmaf(mu, vDY[1], vDY[0]);
-      vHH[1] = fmaf(mu, vHH[1], vHH[0]);
-      if (a.top) vLL[1] = fmaf(mu, vLL[1], vLL[0]);
-    }
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int o = (c * S_CH + r) * S_CP + cc;
-      cf[o] = vLL[c];
-      cf[CH * S_CH * S_CP + o] = vDY[c];
-      cf[2 * CH * S_CH * S_CP + o] = vDX[c];
-      cf[3 * CH * S_CH * S_CP + o] = vHH[c];
-    }
-  }
-  __syncthreads();
 }
 
 template <int CH, int MODE, bool LEVEL1>
-__global__ void __launch_bounds__(NT) k_syn(SynArgs a) {
+__global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
   extern __shared__ float smem[];
-  float *cf = smem;
-  float *lo_s = cf + 4 * CH * S_CH * S_CP;
-  float *hi_s = lo_s + CH * 2 * TY * S_LP;
+  float *cf0 = smem;                  // two [4][S_CH][S_CP] buffers
+  float *lo_s = smem + 8 * SUB;       // [2TY][S_LP]
+  float *hi_s = lo_s + 2 * TY * S_LP;
   const int h = a.M >> 1;
   const int ntx = (h + TX - 1) / TX;
   const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
   const int l = LEVEL1 ? blockIdx.y : blockIdx.y / a.K;
   const int b = LEVEL1 ? 0 : blockIdx.y % a.K;
   const float mu = (MODE == WAVE_ITERATE) ? (float)a.sc->mu : 0.f;
+  const int sx = threadIdx.x % (TX / QXP), my = threadIdx.x / (TX / QXP);
+  const int yy = 2 * ky0 + my, xx0 = 2 * kx0 + 2 * QXP * sx;
   float acc[CH][2 * QXP];
 #pragma unroll
   for (int c = 0; c < CH; ++c)
 #pragma unroll
     for (int e = 0; e < 2 * QXP; ++e) acc[c][e] = 0.f;
-  if (LEVEL1) {
-    for (int bb = 0; bb < a.K; ++bb) {
-      syn_load<CH, MODE>(a, cf, l, bb, kx0, ky0, mu);
-      syn_dispatch<CH>(bb + 1, cf, lo_s, hi_s, acc, true);
+  const int nsteps = (LEVEL1 ? a.K : 1) * CH;
+  syn_issue(a, cf0, l, LEVEL1 ? 0 : b, 0, kx0, ky0);
+  cp_commit();
+  for (int i = 0; i < nsteps; ++i) {
+    const int bb = LEVEL1 ? i / CH : b, c = i % CH;
+    float *cf = cf0 + (i & 1) * 4 * SUB;
+    if (i + 1 < nsteps) {
+      const int nb = LEVEL1 ? (i + 1) / CH : b;
+      syn_issue(a, cf0 + ((i + 1) & 1) * 4 * SUB, l, nb, (i + 1) % CH, kx0, ky0);
+      cp_commit();
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
     }
-  } else {
-    syn_load<CH, MODE>(a, cf, l, b, kx0, ky0, mu);
-    syn_dispatch<CH>(b + 1, cf, lo_s, hi_s, acc, false);
-  }
-  const int sx = threadIdx.x % (TX / QXP), my = threadIdx.x / (TX / QXP);
-  const int yy = 2 * ky0 + my, xx0 = 2 * kx0 + 2 * QXP * sx;
-  if (yy >= a.M) return;
-  const size_t NN = (size_t)a.n * a.n;
-  if (!LEVEL1) {
+    __syncthreads();
+    float o[2 * QXP];
+    syn_dispatch(bb + 1, cf, lo_s, hi_s, o);
+    if (LEVEL1) {
 #pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      float *o = a.ll_out + (((size_t)(c * a.L + l) * a.K + b) * a.M + yy) * a.M;
+      for (int e = 0; e < 2 * QXP; ++e) {
+        if (CH == 3) {
+          if (c == 0) { acc[0][e] += o[e]; acc[1][e] += o[e]; }
+          else if (c == 1) acc[1][e] = fmaf(mu, o[e], acc[1][e]);
+          else acc[2][e] += o[e];
+        } else {
+          acc[0][e] += o[e];
+        }
+      }
+    } else if (yy < a.M) {
+      float *dst = a.ll_out + (((size_t)(c * a.L + l) * a.K + b) * a.M + yy) * a.M;
 #pragma unroll
       for (int e = 0; e < 2 * QXP; ++e)
-        if (xx0 + e < a.M) o[xx0 + e] = acc[c][e];
+        if (xx0 + e < a.M) dst[xx0 + e] = o[e];
     }
-    return;
+    __syncthreads();
   }
+  if (!LEVEL1 || yy >= a.M) return;
+  const size_t NN = (size_t)a.n * a.n;
   const size_t row = (size_t)l * NN + (size_t)yy * a.n;
   if (MODE == WAVE_TRANSFORM) {
 #pragma unroll
