@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
 // shared memory, so a CTA needs a single [CH][Lp][PT+8] buffer (higher
 // occupancy for this HBM-bound step).
 template <int CH, int PT>
-__global__ void __launch_bounds__(DT, 5) k_dct_small(DctKArgs a) {
+__global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
   extern __shared__ float sm[];
   constexpr int PP = PT + 8;
   const int Lp = a.Lp, L = a.L;
@@ -244,38 +244,34 @@ __global__ void __launch_bounds__(DT, 5) k_dct_small(DctKArgs a) {
   __syncthreads();
   const int mt = warp;
   const bool has = mt * 16 < Lp;
-  float acc[CH][PT / 8][4];
-  if (has) {
+  // one chain at a time: product, then (after every warp has read the
+  // chain's input tile) the dual update written over that tile
+  uint32_t keep = 0;
+#pragma unroll 1
+  for (int c = 0; c < CH; ++c) {
+    float acc[PT / 8][4];
+    if (has) tile_gemm<PT>(a.a1hi, a.a1lo, Lp, mt * 16, zb + c * Lp * PP, PP, acc);
+    __syncthreads();
+    if (has) {
+      const float sg = c == 2 ? sigma : sigma * gamma;
 #pragma unroll
-    for (int c = 0; c < CH; ++c)
-      tile_gemm<PT>(a.a1hi, a.a1lo, Lp, mt * 16, zb + c * Lp * PP, PP, acc[c]);
-  }
-  __syncthreads();
-  if (has) {
+      for (int nt = 0; nt < PT / 8; ++nt) {
 #pragma unroll
-    for (int nt = 0; nt < PT / 8; ++nt) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int k = mt * 16 + g + (e >= 2 ? 8 : 0);
-        const int p = nt * 8 + 2 * t + (e & 1);
-        const size_t pix = n0 + p;
-        const bool valid = k < L && pix < N;
-        const size_t j = (size_t)k * N + pix;
-        float al = 0.f, vc[CH];
-        if (valid) {
-          al = a.alpha[pix];
-#pragma unroll
-          for (int c = 0; c < CH; ++c) vc[c] = a.v[c * CS + j];
-        }
-        bool keep = false;
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
+        for (int e = 0; e < 4; ++e) {
+          const int k = mt * 16 + g + (e >= 2 ? 8 : 0);
+          const int p = nt * 8 + 2 * t + (e & 1);
+          const size_t pix = n0 + p;
+          const size_t j = (size_t)k * N + pix;
           float vn = 0.f;
-          if (valid) {
-            const float s1 = (c == 2) ? sigma * al : sigma * gamma * al;
-            const float vt = fmaf(s1, acc[c][nt][e], vc[c]);
-            if (c == 0) { vn = satf(vt); keep = fabsf(vt) <= 1.f; }
-            else vn = keep ? vt : 0.f;
+          if (k < L && pix < N) {
+            const float vt = fmaf(sg * a.alpha[pix], acc[nt][e], a.v[c * CS + j]);
+            const uint32_t bit = 1u << (nt * 4 + e);
+            if (c == 0) {
+              vn = satf(vt);
+              if (fabsf(vt) <= 1.f) keep |= bit;
+            } else {
+              vn = (keep & bit) ? vt : 0.f;
+            }
             a.v[c * CS + j] = vn;
           }
           zb[(c * Lp + k) * PP + p] = vn;

@@ -16,35 +16,45 @@
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
+#include "fft32.cuh"
 #include "kernels.h"
 
 namespace muffin {
 
 namespace {
 
-constexpr int kRowBlock = 8;   // rows per CTA in passes 1 and 3 (even)
-constexpr int kColBlock = 4;   // columns per CTA in pass 2
 constexpr int kThreads = 256;
 
+// sequences per CTA so that every thread owns fft_vpt(n) values per stage
+inline int seqs_per_cta(int n) { return kThreads * fft_vpt(n) / n; }
+
+// stage the twiddle tables (tlen entries) into shared memory
+__device__ __forceinline__ void load_tw(float2 *dst, const float2 *__restrict__ src, int tlen) {
+  for (int i = threadIdx.x; i < tlen; i += blockDim.x) dst[i] = src[i];
+}
+
+template <int NN>
 __global__ void __launch_bounds__(kThreads)
 k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S, int n, int RB,
-           const float2 *__restrict__ tw) {
+           const float2 *__restrict__ tw, int tlen) {
   extern __shared__ float2 sm2[];
   const int img = blockIdx.y;
   const int y0 = blockIdx.x * RB;
   const int nq = RB >> 1, nh = (n >> 1) + 1;
-  float2 *a = sm2, *b = sm2 + nq * n;
+  const int pitch = n + (n >> 4);
+  float2 *d = sm2, *tws = sm2 + nq * pitch;
+  load_tw(tws, tw, tlen);
   const float *xi = x + (size_t)img * n * n + (size_t)y0 * n;
   for (int i = threadIdx.x; i < nq * n; i += blockDim.x) {
     const int q = i / n, col = i - q * n;
-    a[i] = make_float2(xi[(2 * q) * n + col], xi[(2 * q + 1) * n + col]);
+    d[q * pitch + fpad(col)] = make_float2(xi[(2 * q) * n + col], xi[(2 * q + 1) * n + col]);
   }
   __syncthreads();
-  const float2 *r = fft_batch<float2, false>(a, b, n, nq, tw);
+  fft_inplace<NN, false>(d, nq, pitch, tws);
   float4 *Si = reinterpret_cast<float4 *>(S + (size_t)img * nh * n);
   for (int i = threadIdx.x; i < nh * nq; i += blockDim.x) {
     const int k = i / nq, q = i - k * nq;
-    const float2 Z = r[q * n + k], Zc = r[q * n + ((n - k) & (n - 1))];
+    const float2 Z = d[q * pitch + fpad(k)], Zc = d[q * pitch + fpad((n - k) & (n - 1))];
     // row 2q: (Z + conj Zc)/2 ; row 2q+1: (Z - conj Zc)/(2i)
     float4 o;
     o.x = 0.5f * (Z.x + Zc.x);
@@ -55,56 +65,81 @@ k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S, int n, int RB,
   }
 }
 
+template <int NN>
 __global__ void __launch_bounds__(kThreads)
 k_cols(float2 *__restrict__ S, const float *__restrict__ kspec, int n, int L,
-       int CB, const float2 *__restrict__ tw) {
+       int CB, const float2 *__restrict__ tw, int tlen) {
   extern __shared__ float2 sm2[];
   const int img = blockIdx.y, band = img % L;
   const int nh = (n >> 1) + 1;
   const int k0 = blockIdx.x * CB;
   const int ncol = min(CB, nh - k0);
-  float2 *a = sm2, *b = sm2 + CB * n;
+  const int pitch = n + (n >> 4);
+  float2 *d = sm2, *tws = sm2 + CB * pitch;
+  load_tw(tws, tw, tlen);
   float2 *Si = S + ((size_t)img * nh + k0) * n;
   const float *Ki = kspec + ((size_t)band * nh + k0) * n;
-  for (int i = threadIdx.x; i < ncol * n; i += blockDim.x) a[i] = Si[i];
-  __syncthreads();
-  float2 *r = fft_batch<float2, false>(a, b, n, ncol, tw);
+  // every thread owns at most KPT multiplier entries: prefetch them now
+  constexpr int KPT = NN < 16 ? NN : 16;
+  float kr[KPT];
+#pragma unroll
+  for (int u = 0; u < KPT; ++u) {
+    const int i = threadIdx.x + u * kThreads;
+    kr[u] = i < ncol * n ? __ldg(Ki + i) : 0.f;
+  }
   for (int i = threadIdx.x; i < ncol * n; i += blockDim.x) {
-    const float kk = __ldg(Ki + i);
-    r[i].x *= kk;
-    r[i].y *= kk;
+    const int c = i / n, y = i - c * n;
+    d[c * pitch + fpad(y)] = Si[i];
   }
   __syncthreads();
-  r = fft_batch<float2, true>(r, r == a ? b : a, n, ncol, tw);
-  for (int i = threadIdx.x; i < ncol * n; i += blockDim.x) Si[i] = r[i];
+  fft_inplace<NN, false>(d, ncol, pitch, tws);
+#pragma unroll
+  for (int u = 0; u < KPT; ++u) {
+    const int i = threadIdx.x + u * kThreads;
+    if (i < ncol * n) {
+      const int c = i / n, y = i - c * n;
+      float2 &z = d[c * pitch + fpad(y)];
+      z.x *= kr[u];
+      z.y *= kr[u];
+    }
+  }
+  __syncthreads();
+  fft_inplace<NN, true>(d, ncol, pitch, tws);
+  for (int i = threadIdx.x; i < ncol * n; i += blockDim.x) {
+    const int c = i / n, y = i - c * n;
+    Si[i] = d[c * pitch + fpad(y)];
+  }
 }
 
+template <int NN>
 __global__ void __launch_bounds__(kThreads)
 k_rows_inv(const float2 *__restrict__ S, float *__restrict__ g,
            const float *__restrict__ bdata, int n, int L, int RB,
-           const float2 *__restrict__ tw) {
+           const float2 *__restrict__ tw, int tlen) {
   extern __shared__ float2 sm2[];
   const int img = blockIdx.y, band = img % L;
   const int y0 = blockIdx.x * RB;
   const int nq = RB >> 1, nh = (n >> 1) + 1, half = n >> 1;
-  float2 *a = sm2, *b = sm2 + nq * n;
+  const int pitch = n + (n >> 4);
+  float2 *d = sm2, *tws = sm2 + nq * pitch;
+  load_tw(tws, tw, tlen);
   const float4 *Si = reinterpret_cast<const float4 *>(S + (size_t)img * nh * n);
   for (int i = threadIdx.x; i < nh * nq; i += blockDim.x) {
     const int k = i / nq, q = i - k * nq;
     float4 v = Si[((size_t)k * n + y0 + 2 * q) >> 1];   // Xa = (x,y), Xb = (z,w)
     if (k == 0 || k == half) { v.y = 0.f; v.w = 0.f; }
-    a[q * n + k] = make_float2(v.x - v.w, v.y + v.z);    // Xa + i Xb
+    d[q * pitch + fpad(k)] = make_float2(v.x - v.w, v.y + v.z);    // Xa + i Xb
     if (k > 0 && k < half)
-      a[q * n + n - k] = make_float2(v.x + v.w, v.z - v.y);  // conj Xa + i conj Xb
+      d[q * pitch + fpad(n - k)] = make_float2(v.x + v.w, v.z - v.y);  // conj Xa + i conj Xb
   }
   __syncthreads();
-  const float2 *r = fft_batch<float2, true>(a, b, n, nq, tw);
+  fft_inplace<NN, true>(d, nq, pitch, tws);
   const bool sub = (bdata != nullptr) && (img < L);
   float *gi = g + (size_t)img * n * n + (size_t)y0 * n;
   const float *bi = sub ? bdata + (size_t)band * n * n + (size_t)y0 * n : nullptr;
   for (int i = threadIdx.x; i < nq * n; i += blockDim.x) {
     const int q = i / n, col = i - q * n;
-    const float2 z = r[i];
+    const float2 z = d[q * pitch + fpad(col)];
     float v0 = z.x, v1 = z.y;
     if (sub) {
       v0 -= __ldg(bi + (2 * q) * n + col);
@@ -187,21 +222,26 @@ inline int grid_for(size_t count) {
   return (int)(g > 152 * 32 ? 152 * 32 : (g ? g : 1));
 }
 
-}  // namespace
 
-cudaError_t launch_gradient(const float *x, float *g, const float *b,
-                            float2 *S, const float *kspec, const float2 *tw,
-                            int n, int L, int C, cudaStream_t st, Prof *prof) {
+template <int NN>
+cudaError_t gradient_n(const float *x, float *g, const float *b, float2 *S,
+                       const float *kspec, const float2 *tw, int L, int C,
+                       cudaStream_t st, Prof *prof) {
+  constexpr int n = NN;
   const int nimg = C * L;
-  const int RB = n < kRowBlock ? n : kRowBlock;
+  const int nb = seqs_per_cta(n);
+  const int RB = 2 * nb < n ? 2 * nb : n;          // real rows per CTA (even)
+  const int CB = nb;                                // columns per CTA
   const int nh = (n >> 1) + 1;
-  const size_t smr = (size_t)RB * n * sizeof(float2);       // 2 buffers of RB/2 rows
-  const size_t smc = (size_t)2 * kColBlock * n * sizeof(float2);
+  const int pitch = n + (n >> 4);
+  const int tlen = fft_table_len(n);
+  const size_t smr = ((size_t)(RB / 2) * pitch + tlen) * sizeof(float2);
+  const size_t smc = ((size_t)CB * pitch + tlen) * sizeof(float2);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_rows_fwd<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_rows_inv<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_cols<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   const double img = (double)n * n, spec = (double)nh * n * 8.0;
@@ -209,22 +249,45 @@ cudaError_t launch_gradient(const float *x, float *g, const float *b,
   {
     ProfScope ps(prof, "grad_rows_fwd", nimg * (img * 4.0 + spec),
                  nimg * (n / 2.0) * fft, st);
-    k_rows_fwd<<<dim3(n / RB, nimg), kThreads, smr, st>>>(x, S, n, RB, tw);
+    k_rows_fwd<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(x, S, n, RB, tw, tlen);
   }
   {
     ProfScope ps(prof, "grad_cols", nimg * 2.0 * spec + (double)L * nh * n * 4.0,
                  nimg * (double)nh * 2.0 * fft, st);
-    k_cols<<<dim3((nh + kColBlock - 1) / kColBlock, nimg), kThreads, smc, st>>>(
-        S, kspec, n, L, kColBlock, tw);
+    k_cols<NN><<<dim3((nh + CB - 1) / CB, nimg), kThreads, smc, st>>>(S, kspec, n, L, CB, tw, tlen);
   }
   {
     ProfScope ps(prof, "grad_rows_inv",
                  nimg * (spec + img * 4.0) + (b ? (double)L * img * 4.0 : 0.0),
                  nimg * (n / 2.0) * fft, st);
-    k_rows_inv<<<dim3(n / RB, nimg), kThreads, smr, st>>>(S, g, b, n, L, RB, tw);
+    k_rows_inv<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(S, g, b, n, L, RB, tw, tlen);
   }
   return cudaGetLastError();
 }
+
+}  // namespace
+
+cudaError_t launch_gradient(const float *x, float *g, const float *b,
+                            float2 *S, const float *kspec, const float2 *tw,
+                            int n, int L, int C, cudaStream_t st, Prof *prof) {
+  switch (n) {
+    case 2: return gradient_n<2>(x, g, b, S, kspec, tw, L, C, st, prof);
+    case 4: return gradient_n<4>(x, g, b, S, kspec, tw, L, C, st, prof);
+    case 8: return gradient_n<8>(x, g, b, S, kspec, tw, L, C, st, prof);
+    case 16: return gradient_n<16>(x, g, b, S, kspec, tw, L, C, st, prof);
+    case 32: return gradient_n<32>(x, g, b, S, kspec, tw, L, C, st, prof);
+    case 64: return gradient_n<64>(x, g, b, S, kspec, tw, L, C, st, prof);
+    case 128: return gradient_n<128>(x, g, b, S, kspec, tw, L, C, st, prof);
+    case 256: return gradient_n<256>(x, g, b, S, kspec, tw, L, C, st, prof);
+    case 512: return gradient_n<512>(x, g, b, S, kspec, tw, L, C, st, prof);
+    case 1024: return gradient_n<1024>(x, g, b, S, kspec, tw, L, C, st, prof);
+    case 2048: return gradient_n<2048>(x, g, b, S, kspec, tw, L, C, st, prof);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int fft32_table_len(int n) { return fft_table_len(n); }
+void fft32_tables(int n, float2 *tab) { fft_tables(n, tab); }
 
 cudaError_t fft2d_c64(double2 *data, double2 *tmp, int n, int nimg,
                       bool inverse, const double2 *tw64, cudaStream_t st) {

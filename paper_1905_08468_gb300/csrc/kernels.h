@@ -93,6 +93,10 @@ cudaError_t launch_gradient(const float *x, float *g, const float *b,
                             int n, int L, int C, cudaStream_t st,
                             Prof *prof = nullptr);
 
+// Stage twiddle tables of the FP32 gradient FFT for side n (host side).
+int fft32_table_len(int n);
+void fft32_tables(int n, float2 *tab);
+
 // FP64 helpers used when a plan or a call is set up.
 // In-place 2D DFT of nimg complex n x n images; inverse is unnormalised.
 cudaError_t fft2d_c64(double2 *data, double2 *tmp, int n, int nimg, bool inverse,

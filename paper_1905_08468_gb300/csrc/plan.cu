@@ -279,7 +279,7 @@ muffin_status plan_init(muffin_plan P, const float *psf, const float *alpha,
   CK(P->alloc(&P->w64a, NL));
   CK(P->alloc(&P->w64b, NL));
   CK(P->alloc(&P->kspec, (size_t)L * nh * n));
-  CK(P->alloc(&P->tw32, (size_t)n));
+  CK(P->alloc(&P->tw32, (size_t)fft32_table_len(n)));
   CK(P->alloc(&P->tw64, (size_t)n));
   const size_t LL2 = (size_t)P->Lp * P->Lp;
   CK(P->alloc(&P->chi, LL2));
@@ -313,16 +313,16 @@ muffin_status plan_init(muffin_plan P, const float *psf, const float *alpha,
   P->grp[0].b = P->b;
   P->grp[1].b = P->bbar;
 
-  // ---- twiddles e^{-2 pi i k / n}
-  std::vector<float2> t32(n);
+  // ---- twiddles: FP64 e^{-2 pi i k / n}; FP32 per-stage tables of the hot FFT
   std::vector<double2> t64(n);
   const double pi = 3.14159265358979323846;
   for (int k = 0; k < n; ++k) {
     const double a = -2.0 * pi * k / n;
     t64[k] = make_double2(std::cos(a), std::sin(a));
-    t32[k] = make_float2((float)t64[k].x, (float)t64[k].y);
   }
-  CK(cudaMemcpyAsync(P->tw32, t32.data(), n * sizeof(float2), cudaMemcpyHostToDevice, P->st));
+  std::vector<float2> t32(fft32_table_len(n));
+  fft32_tables(n, t32.data());
+  CK(cudaMemcpyAsync(P->tw32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice, P->st));
   CK(cudaMemcpyAsync(P->tw64, t64.data(), n * sizeof(double2), cudaMemcpyHostToDevice, P->st));
 
   // ---- filters

@@ -42,10 +42,12 @@ constexpr int A_RH = 2 * TY + 2 * PMAX - 2;          // input rows held
 constexpr int A_IP = (2 * TX + 2 * PMAX - 2) | 1;    // odd pitch: conflict-free rows
 constexpr int A_LP = TX + 1;                         // row-pass output pitch
 constexpr int QX = 4, QY = 2;                        // outputs per thread
-// synthesis tiles
-constexpr int S_CH = TY + PMAX - 1;                  // coefficient rows held
-constexpr int S_CP = (TX + PMAX - 1) | 1;            // coefficient pitch
-constexpr int S_LP = S_CP;                           // column-pass output pitch
+// synthesis tiles: a fixed window of coefficients [k0 - 8, k0 + T) in both
+// directions (covers the p - 1 <= 7 halo of every basis), 16-byte aligned
+constexpr int S_HALO = 8;
+constexpr int S_CH = TY + S_HALO;                    // coefficient rows held
+constexpr int S_CP = TX + S_HALO;                    // coefficient pitch (x4 aligned)
+constexpr int S_LP = (TX + PMAX - 1) | 1;            // column-pass output pitch
 constexpr int QXP = 4, QYP = 2;                      // coefficient pairs per thread
 
 constexpr size_t ana_smem(int ch) {
@@ -314,24 +316,43 @@ __device__ __forceinline__ void cp_wait() {
 
 constexpr int SUB = S_CH * S_CP;   // one subband tile in shared memory
 
-// issue the copies of the four subband tiles of (basis bb, chain c)
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// issue the copies of the four subband tiles of (basis bb, chain c): rows
+// ky0-8 .. ky0+TY-1 and columns kx0-8 .. kx0+TX-1 (mod the level size h).
+// With h >= 8 every aligned group of 4 columns is contiguous in memory (the
+// wrap point is a multiple of 4), so whole groups move with 16-byte copies.
 __device__ __forceinline__ void syn_issue(const SynArgs &a, float *cf, int l,
                                           int bb, int c, int kx0, int ky0) {
-  const int P = bb + 1;
   const int h = a.M >> 1, hm = h - 1;
-  const int R = TY + P - 1, W = TX + P - 1;
   const size_t NN = (size_t)a.n * a.n;
   const float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * NN;
   const float *lp = a.top ? nullptr
                           : a.ll_in + ((size_t)(c * a.L + l) * a.K + bb) * h * h;
-  for (int it = threadIdx.x; it < R * W; it += NT) {
-    const int r = it / W, cc = it - r * W;
-    const int ky = (ky0 - (P - 1) + r) & hm, kx = (kx0 - (P - 1) + cc) & hm;
-    const int o = r * S_CP + cc;
-    cp_async4(cf + o, a.top ? up + (size_t)ky * a.n + kx : lp + (size_t)ky * h + kx);
-    cp_async4(cf + SUB + o, up + (size_t)(h + ky) * a.n + kx);          // DY
-    cp_async4(cf + 2 * SUB + o, up + (size_t)ky * a.n + h + kx);        // DX
-    cp_async4(cf + 3 * SUB + o, up + (size_t)(h + ky) * a.n + h + kx);  // HH
+  if (h >= 8) {
+    constexpr int G4 = S_CP / 4;
+    for (int it = threadIdx.x; it < S_CH * G4; it += NT) {
+      const int r = it / G4, cc = (it - r * G4) * 4;
+      const int ky = (ky0 - S_HALO + r) & hm, kx = (kx0 - S_HALO + cc) & hm;
+      const int o = r * S_CP + cc;
+      cp_async16(cf + o, a.top ? up + (size_t)ky * a.n + kx : lp + (size_t)ky * h + kx);
+      cp_async16(cf + SUB + o, up + (size_t)(h + ky) * a.n + kx);          // DY
+      cp_async16(cf + 2 * SUB + o, up + (size_t)ky * a.n + h + kx);        // DX
+      cp_async16(cf + 3 * SUB + o, up + (size_t)(h + ky) * a.n + h + kx);  // HH
+    }
+  } else {
+    for (int it = threadIdx.x; it < S_CH * S_CP; it += NT) {
+      const int r = it / S_CP, cc = it - r * S_CP;
+      const int ky = (ky0 - S_HALO + r) & hm, kx = (kx0 - S_HALO + cc) & hm;
+      const int o = r * S_CP + cc;
+      cp_async4(cf + o, a.top ? up + (size_t)ky * a.n + kx : lp + (size_t)ky * h + kx);
+      cp_async4(cf + SUB + o, up + (size_t)(h + ky) * a.n + kx);
+      cp_async4(cf + 2 * SUB + o, up + (size_t)ky * a.n + h + kx);
+      cp_async4(cf + 3 * SUB + o, up + (size_t)(h + ky) * a.n + h + kx);
+    }
   }
 }
 
@@ -342,9 +363,10 @@ __device__ __forceinline__ void syn_step(const float *cf, float *lo_s, float *hi
   constexpr int NCOL = TX + P - 1;
   constexpr int NSY = TY / QYP;
   constexpr int NWC = QYP + P - 1;
+  constexpr int OFF = S_HALO - (P - 1);     // window offset of this basis' halo
   for (int it = threadIdx.x; it < NSY * NCOL; it += NT) {
     const int kc = it % NCOL, sy = it / NCOL;
-    const int base = (QYP * sy) * S_CP + kc;
+    const int base = (QYP * sy + OFF) * S_CP + kc + OFF;
     float vLL[NWC], vDY[NWC], vDX[NWC], vHH[NWC];
 #pragma unroll
     for (int i = 0; i < NWC; ++i) {
