@@ -254,6 +254,22 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
     __syncthreads();
     if (has) {
       const float sg = c == 2 ? sigma : sigma * gamma;
+      // all loads of the fragment first (independent), then update and store
+      float vold[PT / 8][4], alw[PT / 8][2];
+#pragma unroll
+      for (int nt = 0; nt < PT / 8; ++nt) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = mt * 16 + g + (e >= 2 ? 8 : 0);
+          const size_t pix = n0 + nt * 8 + 2 * t + (e & 1);
+          vold[nt][e] = (k < L && pix < N) ? a.v[c * CS + (size_t)k * N + pix] : 0.f;
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const size_t pix = n0 + nt * 8 + 2 * t + e;
+          alw[nt][e] = pix < N ? a.alpha[pix] : 0.f;
+        }
+      }
 #pragma unroll
       for (int nt = 0; nt < PT / 8; ++nt) {
 #pragma unroll
@@ -261,10 +277,9 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
           const int k = mt * 16 + g + (e >= 2 ? 8 : 0);
           const int p = nt * 8 + 2 * t + (e & 1);
           const size_t pix = n0 + p;
-          const size_t j = (size_t)k * N + pix;
           float vn = 0.f;
           if (k < L && pix < N) {
-            const float vt = fmaf(sg * a.alpha[pix], acc[nt][e], a.v[c * CS + j]);
+            const float vt = fmaf(sg * alw[nt][e & 1], acc[nt][e], vold[nt][e]);
             const uint32_t bit = 1u << (nt * 4 + e);
             if (c == 0) {
               vn = satf(vt);
@@ -272,7 +287,7 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
             } else {
               vn = (keep & bit) ? vt : 0.f;
             }
-            a.v[c * CS + j] = vn;
+            a.v[c * CS + (size_t)k * N + pix] = vn;
           }
           zb[(c * Lp + k) * PP + p] = vn;
         }
@@ -293,6 +308,14 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
     for (int c = 0; c < CH; ++c) {
       float acc2[PT / 8][4];
       tile_gemm<PT>(a.a2hi, a.a2lo, Lp, mt * 16, zb + c * Lp * PP, PP, acc2);
+      float alw[PT / 8][2];
+#pragma unroll
+      for (int nt = 0; nt < PT / 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const size_t pix = n0 + nt * 8 + 2 * t + e;
+          alw[nt][e] = pix < N ? a.alpha[pix] : 0.f;
+        }
 #pragma unroll
       for (int nt = 0; nt < PT / 8; ++nt) {
 #pragma unroll
@@ -301,8 +324,7 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
           const int p = nt * 8 + 2 * t + (e & 1);
           const size_t pix = n0 + p;
           if (l < L && pix < N) {
-            const float al = a.alpha[pix];
-            const float s2 = (c == 2) ? al : gamma * al;
+            const float s2 = (c == 2) ? alw[nt][e & 1] : gamma * alw[nt][e & 1];
             a.t[c * CS + (size_t)l * N + pix] = s2 * acc2[nt][e];
           }
         }

@@ -498,22 +498,57 @@ __global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
   }
   const float tau = (float)a.sc->tau;
   const float bl = a.beta[l];
-  float sc[CH];
-  sc[0] = bl * mu;
-  if (CH == 3) { sc[1] = bl; sc[2] = bl * mu; }
   const size_t CS = (size_t)a.L * NN;
+  if (xx0 >= a.n) return;
+  // vector path: the thread's 8 pixels are inside the row and 32-byte aligned
+  const bool vec = (a.n & 7) == 0 && xx0 + 2 * QXP <= a.n;
+  // chains in order; each loads its x, grad, t first, then stores x-tilde
+  uint32_t keep = 0;
 #pragma unroll
-  for (int e = 0; e < 2 * QXP; ++e) {
-    if (xx0 + e >= a.n) continue;
-    const size_t i0 = row + xx0 + e;
-    const float m0 = a.x[i0] - tau * (a.g[i0] + sc[0] * acc[0][e] + a.t[i0]);
-    const bool keep = !a.positivity || m0 > 0.f;
-    a.xt[i0] = keep ? m0 : 0.f;
+  for (int c = 0; c < CH; ++c) {
+    const float sc = (CH == 3 && c == 1) ? bl : bl * mu;   // mu_l, beta_l, mu_l
+    const size_t i0 = row + xx0 + c * CS;
+    float xv[2 * QXP], gv[2 * QXP], tv[2 * QXP];
+    if (vec) {
 #pragma unroll
-    for (int c = 1; c < CH; ++c) {
-      const size_t ic = i0 + c * CS;
-      const float mc = a.x[ic] - tau * (a.g[ic] + sc[c] * acc[c][e] + a.t[ic]);
-      a.xt[ic] = keep ? mc : 0.f;
+      for (int h4 = 0; h4 < 2 * QXP; h4 += 4) {
+        const float4 x4 = *reinterpret_cast<const float4 *>(a.x + i0 + h4);
+        const float4 g4 = *reinterpret_cast<const float4 *>(a.g + i0 + h4);
+        const float4 t4 = *reinterpret_cast<const float4 *>(a.t + i0 + h4);
+        xv[h4] = x4.x; xv[h4 + 1] = x4.y; xv[h4 + 2] = x4.z; xv[h4 + 3] = x4.w;
+        gv[h4] = g4.x; gv[h4 + 1] = g4.y; gv[h4 + 2] = g4.z; gv[h4 + 3] = g4.w;
+        tv[h4] = t4.x; tv[h4 + 1] = t4.y; tv[h4 + 2] = t4.z; tv[h4 + 3] = t4.w;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 2 * QXP; ++e) {
+        const bool ok = xx0 + e < a.n;
+        xv[e] = ok ? a.x[i0 + e] : 0.f;
+        gv[e] = ok ? a.g[i0 + e] : 0.f;
+        tv[e] = ok ? a.t[i0 + e] : 0.f;
+      }
+    }
+    float o[2 * QXP];
+#pragma unroll
+    for (int e = 0; e < 2 * QXP; ++e) {
+      const float m = xv[e] - tau * (gv[e] + sc * acc[c][e] + tv[e]);
+      if (c == 0) {
+        const bool k = !a.positivity || m > 0.f;
+        if (k) keep |= 1u << e;
+        o[e] = k ? m : 0.f;
+      } else {
+        o[e] = (keep >> e) & 1u ? m : 0.f;
+      }
+    }
+    if (vec) {
+#pragma unroll
+      for (int h4 = 0; h4 < 2 * QXP; h4 += 4)
+        *reinterpret_cast<float4 *>(a.xt + i0 + h4) =
+            make_float4(o[h4], o[h4 + 1], o[h4 + 2], o[h4 + 3]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 2 * QXP; ++e)
+        if (xx0 + e < a.n) a.xt[i0 + e] = o[e];
     }
   }
 }
