@@ -34,7 +34,14 @@ METRIC = "voxel-iters/s (px x bands x iters) at 1024^2 x 64, ADA-PT'ed MUFFIN"
 UNIT = "voxel-iters/s"
 THETA0 = (1e-2, 1e-2)
 ETA = (1e-12, 1e-12)
-CROP = dict(n=256, L=8, iters=1)      # oracle sample: top-left 256^2 x 8 bands
+CROP = dict(n=256, L=8, iters=3)      # oracle sample: top-left 256^2 x 8 bands
+
+# DRAM bytes (read + write) per chain-voxel of a kernel, from a committed
+# ncu capture (profiles/), valid only while the kernel's source file is the
+# one the counters were taken on (sha256 prefix).
+CAPTURED_TRAFFIC = {
+    "ana_level1_dual": ("paper_1905_08468_gb300/csrc/wavelet.cu", "c7ff470693b88ee5", 61.607),
+}
 
 
 # ------------------------------------------------------------------ ranks
@@ -204,6 +211,18 @@ def workload_config(args, oracle=False) -> dict:
     return cfg
 
 
+def captured_traffic(kernel: str, chain_voxels: float):
+    import hashlib
+    ent = CAPTURED_TRAFFIC.get(kernel)
+    if not ent:
+        return None
+    path, sha, per_voxel = ent
+    with open(os.path.join(ROOT, path), "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest()[:16] != sha:
+            return None
+    return per_voxel * chain_voxels
+
+
 def measured_peak_gbs():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -287,7 +306,8 @@ def main() -> None:
     achieved = dom["bytes_per_launch"] / (avg_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved,
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": captured_traffic(dom["name"], 3.0 * vox),
                 "bytes_per_launch": dom["bytes_per_launch"],
                 "avg_launch_ms": avg_ms, "share": dom["total_ms"] / tot_ms}
     kernels = sorted(({"name": s["name"], "launches": s["launches"],
