@@ -200,6 +200,37 @@ MUFFIN_API muffin_status muffin_op_synthesis(muffin_plan plan, const float *u, f
 MUFFIN_API muffin_status muffin_op_dct(muffin_plan plan, const float *x, float *v,
                             int32_t inverse);
 
+/* ---- allocation-free operator ------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory: a host program that gives the
+ * library a fixed device-memory budget and forbids allocations after
+ * start-up, a latency-critical pipeline that cannot afford the implicit
+ * device-wide synchronisation cudaMalloc/cudaFree may cause, or code running
+ * where the CUDA allocator must not be re-entered (for example inside a
+ * memory-pool callback).
+ *
+ * u = W_s x, exactly what muffin_op_analysis computes, with no plan: x
+ * [nbands][n][n] and u [nbands][n_wavelets][n][n] are device arrays owned by
+ * the caller; the work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ * default stream) and the call returns without synchronising.  Levels 2..J
+ * use a fixed file-scope device scratch of 4 Mi floats (16 MiB), which every
+ * GPU that loads the library keeps until the process exits; a cube needing
+ * more (nbands * n_wavelets * sum_{1<=j<levels} (n>>j)^2 floats) is rejected
+ * with MUFFIN_EINVAL before any work.  The call never allocates (no
+ * cudaMalloc/cudaFree, no library allocation).  The first call on a device
+ * does a one-time set-up with that device current (it looks up the
+ * scratch's device address and uploads the filter taps); make that first
+ * call before any stream capture.  All calls share the one scratch array and
+ * it keeps the previous call's contents (every level writes the LL values it
+ * later reads, so nothing needs clearing); calls whose work overlaps on the
+ * GPU (different streams, or different threads) race on it and must be
+ * ordered by the caller.
+ * Errors: EINVAL (NULL or host arrays, bad shape, scratch too small), ECUDA. */
+MUFFIN_API muffin_status muffin_op_analysis_noalloc(const float *x, float *u,
+                                                    int32_t n, int32_t nbands,
+                                                    int32_t n_wavelets,
+                                                    int32_t levels, void *stream);
+
 /* ---- per-kernel profile --------------------------------------------------
  * With profiling on, every kernel the plan launches is bracketed by CUDA
  * events on the plan's stream; stats accumulate per kernel kind until the

@@ -84,6 +84,9 @@ struct ProfScope {
   ~ProfScope() { if (p) p->end(st); }
 };
 
+// Records msg as the thread's muffin_last_error() text and returns s (plan.cu).
+int set_last_error_code(int s, const char *msg);
+
 // ------------------------------------------------------------ FFT (fft_conv.cu)
 // FP32 gradient pipeline: g[c][l] = H_l^T H_l x[c][l] - (c == 0 && b ? b[l] : 0)
 // for nimg = C*L images.  S: spectrum scratch [nimg][n/2+1][n] float2.

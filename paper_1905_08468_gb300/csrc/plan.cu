@@ -76,6 +76,11 @@ float tf32_round(float f) {
 
 }  // namespace
 
+int muffin::set_last_error_code(int s, const char *msg) {
+  g_err = msg ? msg : "";
+  return s;
+}
+
 struct muffin_plan_s {
   muffin_params p{};
   int n = 0, L = 0, K = 0, J = 0, Lp = 0, Cmax = 1;

@@ -69,6 +69,8 @@ SIGNATURES = {
     "muffin_op_analysis": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "muffin_op_synthesis": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "muffin_op_dct": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
+    "muffin_op_analysis_noalloc": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32,
+                                             c_int32, c_void_p]),
     "muffin_profile_enable": (c_int32, [c_void_p, c_int32]),
     "muffin_profile_read": (c_int32, [c_void_p, ctypes.POINTER(KernelStat), c_int32,
                                       ctypes.POINTER(c_int32)]),
