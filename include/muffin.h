@@ -74,6 +74,10 @@ typedef struct {
   int32_t positivity; /* 1 (default): projection of Eq. projpos; 0 skips it */
   int32_t sure;       /* 1: also allocate the ADA-PT chains (needed by
                          muffin_sure_tune); 0: plain MUFFIN only */
+  int32_t batch;      /* B >= 1 independent cubes of the same shape advanced
+                         by the same launches (default 1); every cube array
+                         argument below then holds B cubes one after the
+                         other: [B][L][n][n] */
 } muffin_params;
 
 /* Fill *p with the defaults above for an n x n x nbands cube. */
@@ -82,11 +86,12 @@ MUFFIN_API void muffin_params_default(muffin_params *p, int32_t n, int32_t nband
 /*
  * Create a plan: validates p, allocates the device state, computes the PSF
  * spectra h_hat_l = F psf_l (FP64), beta = max_l ||H_l||^2 =
- * max_{l,k} |h_hat_l(k)|^2 (the Lipschitz constant of the least-squares
- * gradient, Sec. 2.2), the Daubechies filters and the DCT-II tables.
- *   psf   [L][n][n] float32, host or device; read during the call only.
- *   alpha [n*n] pixel weights alpha_n, or NULL for all ones (Eq. 2regpar).
- *   beta  [L]   band weights beta_l, or NULL for all ones.
+ * max_{l,k} |h_hat_l(k)|^2 per cube (the Lipschitz constant of the
+ * least-squares gradient, Sec. 2.2), the Daubechies filters and the DCT-II
+ * tables.
+ *   psf   [B][L][n][n] float32, host or device; read during the call only.
+ *   alpha [B][n*n] pixel weights alpha_n, or NULL for all ones (Eq. 2regpar).
+ *   beta  [B][L]   band weights beta_l, or NULL for all ones.
  *   stream  a cudaStream_t (NULL = legacy default stream) used for all work.
  * Errors: EINVAL (shape, NULL out, PSF all zero), ENOMEM, ECUDA.
  */
@@ -99,8 +104,13 @@ MUFFIN_API void muffin_plan_destroy(muffin_plan plan);
 /* Device bytes held by the plan (state + scratch). */
 MUFFIN_API size_t muffin_plan_device_bytes(muffin_plan plan);
 
-/* beta = max_l ||H_l||^2 computed at plan creation (FP64). */
+/* beta[b] = max_l ||H_l||^2 of cube b (FP64), b < B. */
 MUFFIN_API muffin_status muffin_plan_lipschitz(muffin_plan plan, double *beta);
+
+/* on = 1 (default): repeated launch sequences (two plain iterations, one
+ * ADA-PT window) are captured once into CUDA graphs and replayed; 0 launches
+ * every kernel directly.  Results are identical either way. */
+MUFFIN_API muffin_status muffin_plan_graphs(muffin_plan plan, int32_t on);
 
 typedef struct {
   int32_t iters_done; /* iterations run by this call */
@@ -115,9 +125,10 @@ typedef struct {
                          on input; dirty may be NULL to keep the last one) */
 
 /*
- * Plain MUFFIN: run `iters` iterations of Algorithm 2 with fixed (mu, gamma).
- *   dirty [L][n][n] dirty cube y (NULL with MUFFIN_WARM: keep the last one).
- *   x     [L][n][n] in: X0 (ignored with MUFFIN_WARM), out: X after iters.
+ * Plain MUFFIN: run `iters` iterations of Algorithm 2 with fixed (mu, gamma)
+ * for every cube of the plan.
+ *   dirty [B][L][n][n] dirty cubes y (NULL with MUFFIN_WARM: keep the last).
+ *   x     [B][L][n][n] in: X0 (ignored with MUFFIN_WARM), out: X after iters.
  *   Without MUFFIN_WARM the duals start at U = V = T = 0.
  *   tau is derived from (mu, gamma) by the plan's step rule.
  *   info  optional (NULL allowed).
@@ -127,6 +138,12 @@ typedef struct {
 MUFFIN_API muffin_status muffin_solve(muffin_plan plan, const float *dirty, float *x,
                            int32_t iters, double mu, double gamma,
                            int32_t flags, muffin_info *info);
+
+/* muffin_solve with per-cube weights: mu[B], gamma[B] (host arrays). */
+MUFFIN_API muffin_status muffin_solve_batch(muffin_plan plan, const float *dirty,
+                                            float *x, int32_t iters,
+                                            const double *mu, const double *gamma,
+                                            int32_t flags, muffin_info *info);
 
 /* ADA-PT settings (Algorithm 5, Eq. adaptgrad). */
 typedef struct {
@@ -158,12 +175,13 @@ typedef struct {
  * after every `window` iterations computes SUGAR, updates
  * theta <- max(theta - eta * SUGAR, theta_min), recomputes tau and restarts
  * the derivative iterates.
- *   dirty     [L][n][n] y.   delta [L][n][n] N(0,1) probe.
- *   noise_var [L] host array, sigma_l^2 of each band.
- *   x         [L][n][n] in: X0 for both primal chains (ignored with
+ *   dirty     [B][L][n][n] y.   delta [B][L][n][n] N(0,1) probe.
+ *   noise_var [B][L] host array, sigma_l^2 of each band.
+ *   x         [B][L][n][n] in: X0 for both primal chains (ignored with
  *             MUFFIN_WARM), out: X of the chain on y.
- *   theta     host double[2] in: (mu, gamma), out: tuned (mu, gamma).
- *   trace     host array of iters/window records, or NULL.
+ *   theta     host double[B][2] in: (mu, gamma) per cube, out: tuned values.
+ *   trace     host array [B][iters/window + 1] of records (cube-major), or
+ *             NULL; info->records says how many per cube were written.
  * The plan must have been created with p.sure = 1.
  * Errors: EINVAL, ESTATE (plan without SURE chains), ECUDA.
  */

@@ -71,15 +71,16 @@ class Plan:
     def __init__(self, n: int, nbands: int, psf, *, n_wavelets: int = 8,
                  levels: int = 3, sigma: float = 10.0, step_rule: int = 0,
                  tau_safety: float = 0.99, positivity: bool = True,
-                 sure: bool = False, alpha=None, beta=None, stream=None):
+                 sure: bool = False, alpha=None, beta=None, stream=None,
+                 batch: int = 1):
         lib = library()
         self._lib = lib
-        self.n, self.L, self.K = n, nbands, n_wavelets
+        self.n, self.L, self.K, self.B = n, nbands, n_wavelets, batch
         p = native.Params()
         lib.muffin_params_default(ctypes.byref(p), n, nbands)
         p.n_wavelets, p.levels, p.sigma = n_wavelets, levels, sigma
         p.step_rule, p.tau_safety = step_rule, tau_safety
-        p.positivity, p.sure = int(positivity), int(sure)
+        p.positivity, p.sure, p.batch = int(positivity), int(sure), int(batch)
         keep = []
         handle = ctypes.c_void_p()
         st = stream if stream is not None else _stream_handle()
@@ -112,33 +113,50 @@ class Plan:
         return int(self._lib.muffin_plan_device_bytes(self._h))
 
     @property
-    def lipschitz(self) -> float:
-        b = ctypes.c_double()
-        native.check(self._lib.muffin_plan_lipschitz(self._h, ctypes.byref(b)))
-        return b.value
+    def lipschitz(self):
+        """beta = max ||H_l||^2 (a list of B values when the plan is batched)."""
+        b = (ctypes.c_double * self.B)()
+        native.check(self._lib.muffin_plan_lipschitz(self._h, b))
+        return b[0] if self.B == 1 else list(b)
+
+    def graphs(self, on: bool = True) -> None:
+        native.check(self._lib.muffin_plan_graphs(self._h, int(on)))
 
     # -- solvers
-    def solve(self, dirty, x, iters: int, mu: float, gamma: float,
-              warm: bool = False) -> native.Info:
+    def solve(self, dirty, x, iters: int, mu, gamma, warm: bool = False) -> native.Info:
+        """mu, gamma: scalars (all cubes) or sequences of B values."""
         keep, info = [], native.Info()
-        native.check(self._lib.muffin_solve(
-            self._h, _ptr(dirty, keep), _ptr(x, keep), int(iters), float(mu),
-            float(gamma), MUFFIN_WARM if warm else 0, ctypes.byref(info)))
+        flags = MUFFIN_WARM if warm else 0
+        if np.ndim(mu) == 0 and np.ndim(gamma) == 0:
+            native.check(self._lib.muffin_solve(
+                self._h, _ptr(dirty, keep), _ptr(x, keep), int(iters), float(mu),
+                float(gamma), flags, ctypes.byref(info)))
+        else:
+            m = (ctypes.c_double * self.B)(*np.broadcast_to(np.asarray(mu, float), self.B))
+            g = (ctypes.c_double * self.B)(*np.broadcast_to(np.asarray(gamma, float), self.B))
+            native.check(self._lib.muffin_solve_batch(
+                self._h, _ptr(dirty, keep), _ptr(x, keep), int(iters), m, g, flags,
+                ctypes.byref(info)))
         return info
 
     def sure_tune(self, dirty, delta, noise_var, x, theta, iters: int, *,
                   window: int = 10, eta=(1e-3, 1e-3), theta_min: float = 1e-8,
                   reset: bool = True, eps: float, warm: bool = False):
-        """Returns (theta, trace, info); trace is a list of dicts per window."""
+        """Returns (theta, trace, info); trace is a list of dicts per window.
+
+        For a batched plan theta is a [B][2] array-like and the returned
+        theta and trace are lists over the B cubes."""
         keep = []
         sp = native.SureParams()
         self._lib.muffin_sure_params_default(ctypes.byref(sp))
         sp.iters, sp.window = int(iters), int(window)
         sp.eta_mu, sp.eta_gamma = float(eta[0]), float(eta[1])
         sp.theta_min, sp.reset_each_window, sp.eps = theta_min, int(reset), float(eps)
-        th = (ctypes.c_double * 2)(float(theta[0]), float(theta[1]))
-        nrec = max(1, int(iters) // int(window) + 1)
-        rec = (SureRecord * nrec)()
+        B = self.B
+        th_in = np.broadcast_to(np.asarray(theta, dtype=np.float64).reshape(-1, 2), (B, 2))
+        th = (ctypes.c_double * (2 * B))(*th_in.ravel())
+        cap = int(iters) // int(window) + 1
+        rec = (SureRecord * (cap * B))()
         nv = None
         if noise_var is not None:
             nv_arr = np.ascontiguousarray(noise_var, dtype=np.float64)
@@ -148,10 +166,14 @@ class Plan:
         native.check(self._lib.muffin_sure_tune(
             self._h, _ptr(dirty, keep), _ptr(delta, keep), nv, ctypes.byref(sp),
             _ptr(x, keep), th, rec, MUFFIN_WARM if warm else 0, ctypes.byref(info)))
-        trace = [dict(k=r.k, mu=r.mu, gamma=r.gamma, sugar_mu=r.sugar_mu,
-                      sugar_gamma=r.sugar_gamma, psure=r.psure, tau=r.tau)
-                 for r in rec[: info.records]]
-        return (th[0], th[1]), trace, info
+        def cube_trace(c):
+            return [dict(k=r.k, mu=r.mu, gamma=r.gamma, sugar_mu=r.sugar_mu,
+                         sugar_gamma=r.sugar_gamma, psure=r.psure, tau=r.tau)
+                    for r in rec[c * cap: c * cap + info.records]]
+        if B == 1:
+            return (th[0], th[1]), cube_trace(0), info
+        return ([(th[2 * c], th[2 * c + 1]) for c in range(B)],
+                [cube_trace(c) for c in range(B)], info)
 
     # -- profile
     def profile(self, on: bool = True) -> None:

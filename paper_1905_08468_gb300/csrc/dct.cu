@@ -43,6 +43,7 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4],
 
 struct DctKArgs {
   int n, L, Lp, inverse;
+  int B;                      // cubes; blockIdx.y selects the cube
   const float *a1hi, *a1lo;   // first product: C (or C^T for the inverse operator)
   const float *a2hi, *a2lo;   // second product: C^T
   const float *alpha;
@@ -98,17 +99,20 @@ __global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
   float *zin = sm;                       // [CH][Lp][PP]
   float *vo = zin + CH * Lp * PP;        // [CH][Lp][PP]
   const size_t N = (size_t)a.n * a.n;
-  const size_t CS = (size_t)L * N;
+  const size_t CS = (size_t)a.B * L * N;     // chain stride
   const size_t n0 = (size_t)blockIdx.x * PT;
+  const int cube = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const float gamma = (MODE == WAVE_ITERATE) ? (float)a.sc->gamma : 0.f;
-  const float sigma = (MODE == WAVE_ITERATE) ? (float)a.sc->sigma : 0.f;
+  const float gamma = (MODE == WAVE_ITERATE) ? (float)a.sc[cube].gamma : 0.f;
+  const float sigma = (MODE == WAVE_ITERATE) ? (float)a.sc[cube].sigma : 0.f;
+  const size_t cb = (size_t)cube * L * N;    // the cube's first band
+  const float *__restrict__ alpha = a.alpha + (size_t)cube * N;
 
   for (int it = threadIdx.x; it < Lp * PT; it += DT) {
     const int l = it / PT, p = it - l * PT;
     const size_t pix = n0 + p;
     const bool ok = l < L && pix < N;
-    const size_t j = (size_t)l * N + pix;
+    const size_t j = cb + (size_t)l * N + pix;
     float z[CH];
     if (MODE == WAVE_TRANSFORM) {
       z[0] = ok ? a.in[j] : 0.f;
@@ -137,14 +141,14 @@ __global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
           const int p = nt * 8 + 2 * t + (e & 1);
           const size_t pix = n0 + p;
           const bool valid = k < L && pix < N;
-          const size_t j = (size_t)k * N + pix;
+          const size_t j = cb + (size_t)k * N + pix;
           if (MODE == WAVE_TRANSFORM) {
             if (valid) a.out[j] = acc[nt][e];
             continue;
           }
           float vn = 0.f;
           if (valid) {
-            const float al = a.alpha[pix];
+            const float al = alpha[pix];
             const float s1 = (c == 2) ? sigma * al : sigma * gamma * al;
             const float vt = fmaf(s1, acc[nt][e], a.v[c * CS + j]);
             if (c == 0) {
@@ -183,9 +187,9 @@ __global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
           const int p = nt * 8 + 2 * t + (e & 1);
           const size_t pix = n0 + p;
           if (l < L && pix < N) {
-            const float al = a.alpha[pix];
+            const float al = alpha[pix];
             const float s2 = (c == 2) ? al : gamma * al;
-            a.t[c * CS + (size_t)l * N + pix] = s2 * acc[nt][e];
+            a.t[c * CS + cb + (size_t)l * N + pix] = s2 * acc[nt][e];
           }
         }
       }
@@ -205,17 +209,20 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
   const int Lp = a.Lp, L = a.L;
   float *zb = sm;                        // [CH][Lp][PP]
   const size_t N = (size_t)a.n * a.n;
-  const size_t CS = (size_t)L * N;
+  const size_t CS = (size_t)a.B * L * N;     // chain stride
   const size_t n0 = (size_t)blockIdx.x * PT;
+  const int cube = blockIdx.y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const float gamma = (float)a.sc->gamma;
-  const float sigma = (float)a.sc->sigma;
+  const float gamma = (float)a.sc[cube].gamma;
+  const float sigma = (float)a.sc[cube].sigma;
+  const size_t cb = (size_t)cube * L * N;    // the cube's first band
+  const float *__restrict__ alpha = a.alpha + (size_t)cube * N;
   const bool full = n0 + PT <= N;
   for (int it = threadIdx.x; it < Lp * (PT / 4); it += DT) {
     const int l = it / (PT / 4), p4 = (it - l * (PT / 4)) * 4;
     float z[CH][4];
     if (l < L && full) {
-      const size_t j = (size_t)l * N + n0 + p4;
+      const size_t j = cb + (size_t)l * N + n0 + p4;
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         const float4 xt = *reinterpret_cast<const float4 *>(a.xt + c * CS + j);
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const size_t pix = n0 + p4 + e;
-          const size_t j = (size_t)l * N + pix;
+          const size_t j = cb + (size_t)l * N + pix;
           z[c][e] = (l < L && pix < N) ? 2.f * a.xt[c * CS + j] - a.x[c * CS + j] : 0.f;
         }
     }
@@ -262,12 +269,12 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
         for (int e = 0; e < 4; ++e) {
           const int k = mt * 16 + g + (e >= 2 ? 8 : 0);
           const size_t pix = n0 + nt * 8 + 2 * t + (e & 1);
-          vold[nt][e] = (k < L && pix < N) ? a.v[c * CS + (size_t)k * N + pix] : 0.f;
+          vold[nt][e] = (k < L && pix < N) ? a.v[c * CS + cb + (size_t)k * N + pix] : 0.f;
         }
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const size_t pix = n0 + nt * 8 + 2 * t + e;
-          alw[nt][e] = pix < N ? a.alpha[pix] : 0.f;
+          alw[nt][e] = pix < N ? alpha[pix] : 0.f;
         }
       }
 #pragma unroll
@@ -287,7 +294,7 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
             } else {
               vn = (keep & bit) ? vt : 0.f;
             }
-            a.v[c * CS + (size_t)k * N + pix] = vn;
+            a.v[c * CS + cb + (size_t)k * N + pix] = vn;
           }
           zb[(c * Lp + k) * PP + p] = vn;
         }
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const size_t pix = n0 + nt * 8 + 2 * t + e;
-          alw[nt][e] = pix < N ? a.alpha[pix] : 0.f;
+          alw[nt][e] = pix < N ? alpha[pix] : 0.f;
         }
 #pragma unroll
       for (int nt = 0; nt < PT / 8; ++nt) {
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
           const size_t pix = n0 + p;
           if (l < L && pix < N) {
             const float s2 = (c == 2) ? alw[nt][e & 1] : gamma * alw[nt][e & 1];
-            a.t[c * CS + (size_t)l * N + pix] = s2 * acc2[nt][e];
+            a.t[c * CS + cb + (size_t)l * N + pix] = s2 * acc2[nt][e];
           }
         }
       }
@@ -344,9 +351,9 @@ cudaError_t launch_dct_small(const DctKArgs &a, cudaStream_t st, Prof *prof) {
     attr = true;
   }
   const size_t N = (size_t)a.n * a.n;
-  const double vox = (double)N * a.L;
+  const double vox = (double)N * a.L * a.B;
   ProfScope ps(prof, "spectral_dual", CH * vox * 20.0, 2.0 * CH * 2.0 * a.L * vox, st);
-  k_dct_small<CH, PT><<<(unsigned)((N + PT - 1) / PT), DT, sm, st>>>(a);
+  k_dct_small<CH, PT><<<dim3((unsigned)((N + PT - 1) / PT), a.B), DT, sm, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -360,11 +367,11 @@ cudaError_t launch_dct(const DctKArgs &a, cudaStream_t st, Prof *prof) {
     attr = true;
   }
   const size_t N = (size_t)a.n * a.n;
-  const double vox = (double)N * a.L;
+  const double vox = (double)N * a.L * a.B;
   ProfScope ps(prof, MODE == WAVE_ITERATE ? "spectral_dual" : "spectral_op",
                MODE == WAVE_ITERATE ? CH * vox * 20.0 : vox * 8.0,
                (MODE == WAVE_ITERATE ? 2.0 : 1.0) * CH * 2.0 * a.L * vox, st);
-  k_dct<CH, MODE, PT><<<(unsigned)((N + PT - 1) / PT), DT, sm, st>>>(a);
+  k_dct<CH, MODE, PT><<<dim3((unsigned)((N + PT - 1) / PT), a.B), DT, sm, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -380,7 +387,7 @@ cudaError_t launch_dct_pt(const DctKArgs &a, cudaStream_t st, Prof *prof) {
 
 cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st) {
   DctKArgs a{};
-  a.n = d.n; a.L = d.L; a.Lp = d.Lp;
+  a.n = d.n; a.L = d.L; a.Lp = d.Lp; a.B = d.B > 0 ? d.B : 1;
   a.a1hi = d.chi; a.a1lo = d.clo; a.a2hi = d.cthi; a.a2lo = d.ctlo;
   a.alpha = d.alpha; a.sc = d.sc;
   a.xt = gr.xt; a.x = gr.x; a.v = gr.v; a.t = gr.t;
@@ -395,7 +402,7 @@ cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st) {
 cudaError_t dct_op(const DctArgs &d, const float *in, float *out, int inverse,
                    cudaStream_t st) {
   DctKArgs a{};
-  a.n = d.n; a.L = d.L; a.Lp = d.Lp; a.inverse = inverse;
+  a.n = d.n; a.L = d.L; a.Lp = d.Lp; a.inverse = inverse; a.B = d.B > 0 ? d.B : 1;
   a.a1hi = inverse ? d.cthi : d.chi;
   a.a1lo = inverse ? d.ctlo : d.clo;
   a.in = in; a.out = out;

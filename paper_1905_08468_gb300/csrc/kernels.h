@@ -144,21 +144,25 @@ struct SureStatsArgs {
   const double *wband;  // [L] 2 sigma_l^2 / eps
   int n, L;
 };
+// nblocks = blocks per band (partials are band-major)
 cudaError_t sure_stats(const SureStatsArgs &a, double *partials, int *nblocks,
                        cudaStream_t st);
 
-// Theta update (Eq. adaptgrad) run by one block on the device.
+// Theta update (Eq. adaptgrad) run on the device, one block per cube, then
+// the record counter is advanced (so the same launches can be replayed).
 struct ThetaUpdateArgs {
-  DevScalars *sc;          // in/out
-  const double *partials;  // [nblocks][6]
-  int nblocks;
-  double *record;          // out: 7 doubles {k, mu, gamma, sugar_mu,
-                           //   sugar_gamma, psure, tau} (pre-update theta)
-  int k;
+  int B;                   // cubes
+  DevScalars *sc;          // [B] in/out
+  const double *partials;  // [B][nb_per_cube][6] (bands of a cube are contiguous)
+  int nb_per_cube;
+  double *record;          // out: cube b of record r at record + (r*B + b)*7:
+  int *rec_count;          //   {0, mu, gamma, sugar_mu, sugar_gamma, psure, tau}
+                           //   (theta before the update); r = *rec_count
   double eta_mu, eta_gamma, theta_min;
-  double psure_const;      // sum_l ||y_l||^2 - N sum_l sigma_l^2
+  // per cube: {sum_l ||y_l||^2 - N sum_l sigma_l^2, beta, Bsum, Asum} with
   // tau = safety / (beta/2 + sigma * (K * mu^2 * Bsum + gamma^2 * Asum))
-  double safety, lipschitz, K, Bsum, Asum;
+  const double *cube_const;
+  double safety, K;
 };
 cudaError_t theta_update(const ThetaUpdateArgs &a, cudaStream_t st);
 
@@ -169,9 +173,10 @@ cudaError_t upload_filters(const double h[8][16]);
 enum WaveMode { WAVE_TRANSFORM = 0, WAVE_ITERATE = 1 };
 
 struct WaveArgs {
-  int n, L, K, J, C;
+  int n, L, K, J, C;       // L = all bands of all cubes of the batch
+  int Lc;                  // bands per cube (0: one cube of L bands)
   const float *beta;       // [L] band weights
-  const DevScalars *sc;    // mu, gamma, tau, sigma
+  const DevScalars *sc;    // [L / Lc] per cube: mu, gamma, tau, sigma
   float *scratch;          // LL scratch: level j (1 <= j < J) holds
                            // [C][L][K][n>>j][n>>j] at scratch + lvl_off[j]
   size_t lvl_off[16];
@@ -194,11 +199,12 @@ cudaError_t wavelet_synthesis_op(const WaveArgs &w, const float *u, float *x,
 
 // ------------------------------------------------------------ DCT (dct.cu)
 struct DctArgs {
-  int n, L, Lp, C;         // Lp = L rounded up to a multiple of 16
+  int n, L, Lp, C;         // L = bands per cube, Lp = L rounded up to 16
+  int B;                   // cubes in the batch (band-major, cube after cube)
   const float *chi, *clo;  // [Lp][Lp] C split in TF32 hi + lo (zero padded)
   const float *cthi, *ctlo;// [Lp][Lp] C^T split
-  const float *alpha;      // [n*n] pixel weights
-  const DevScalars *sc;
+  const float *alpha;      // [B][n*n] pixel weights
+  const DevScalars *sc;    // [B]
   Prof *prof;              // optional per-kernel timing
 };
 // Spectral dual update and back-projection (Alg. 2 eqs. vt, v, upt and the

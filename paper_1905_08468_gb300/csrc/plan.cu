@@ -9,10 +9,12 @@
 //                    each fused with the spatial dual update of U
 //   4. spectral      DCT tile kernel: V, T
 //   5. swap x <-> x~ (pointer swap)
-// ADA-PT runs the group on y and the group on y_bar = y + eps delta per
-// iteration; at the end of every window a gradient of the y-primal, one FP64
-// statistics pass and a one-block theta update run on the device, so the
-// whole loop is launch-only (no host round trip) until the call returns.
+// All B cubes of a plan advance in the same launches.  ADA-PT runs the group
+// on y and the group on y_bar = y + eps delta per iteration; at the end of
+// every window a gradient of the y-primal, one FP64 statistics pass and a
+// per-cube theta update run on the device.  Repeated fixed-shape launch
+// sequences (two plain iterations, one ADA-PT window) are captured once into
+// CUDA graphs on the plan's own stream and replayed.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -20,11 +22,12 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
-#include "../../include/muffin.h"
 #include "host_math.h"
 #include "kernels.h"
+#include "plan_internal.h"
 
 using namespace muffin;
 
@@ -32,36 +35,8 @@ namespace {
 
 thread_local std::string g_err = "no error";
 
-muffin_status fail(muffin_status s, const char *fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  g_err = buf;
-  return s;
-}
-
-#define CK(expr)                                                              \
-  do {                                                                        \
-    cudaError_t e_ = (expr);                                                  \
-    if (e_ != cudaSuccess)                                                    \
-      return fail(e_ == cudaErrorMemoryAllocation ? MUFFIN_ENOMEM : MUFFIN_ECUDA, \
-                  "%s: %s", #expr, cudaGetErrorString(e_));                   \
-  } while (0)
-
-bool is_device_ptr(const void *p) {
-  if (!p) return false;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
-}
-
 // reduction scratch layout (doubles): [0] result, [16, 16+1024) max partials;
-// band sums use [0, 65 L); ADA-PT partials start at kRedSure + 65 L.
+// band sums use [0, 65 Lt); ADA-PT partials start at kRedSure + 65 Lt.
 constexpr size_t kRedSure = 1040;
 
 // round-to-nearest (ties away) to the 10-bit TF32 mantissa
@@ -76,88 +51,47 @@ float tf32_round(float f) {
 
 }  // namespace
 
-int muffin::set_last_error_code(int s, const char *msg) {
+#define CK MUFFIN_CK
+
+namespace muffin {
+
+muffin_status fail(muffin_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+int set_last_error_code(int s, const char *msg) {
   g_err = msg ? msg : "";
   return s;
 }
 
-struct muffin_plan_s {
-  muffin_params p{};
-  int n = 0, L = 0, K = 0, J = 0, Lp = 0, Cmax = 1;
-  size_t N = 0, NL = 0;
-  cudaStream_t st = nullptr;
-  std::vector<void *> allocs;
-  size_t bytes = 0;
-
-  double2 *hhat = nullptr, *w64a = nullptr, *w64b = nullptr;
-  float *kspec = nullptr;
-  float2 *tw32 = nullptr;
-  double2 *tw64 = nullptr;
-  float *chi = nullptr, *clo = nullptr, *cthi = nullptr, *ctlo = nullptr;
-  float *alpha = nullptr, *beta = nullptr;
-  DevScalars *sc = nullptr;
-  double *dred = nullptr;      // reduction scratch
-  double *wband = nullptr;     // [L]
-  double *records = nullptr;   // [max_records][7]
-  int max_records = 0;
-  float2 *S = nullptr;
-  float *llscr = nullptr;
-  size_t lvl_off[16] = {};
-  Group grp[2];
-  float *b = nullptr, *bbar = nullptr, *htd = nullptr;
-  float *stage_a = nullptr, *stage_b = nullptr;   // [L][n][n] staging
-  // operator buffers (allocated on first use)
-  float *op_in = nullptr, *op_out = nullptr, *op_b = nullptr;
-
-  Prof prof;
-  bool profiling = false;
-  Prof *pp() { return profiling ? &prof : nullptr; }
-
-  double lipschitz = 0, Asum = 0, Bsum = 0, Amax2 = 0, Bmax2 = 0;
-  double psure_const = 0;
-  bool have_b = false, have_state = false, have_sure_state = false;
-  long long k_done = 0;   // ADA-PT iterations done in the current run
-  double cur_mu = 0, cur_gamma = 0;
-
-  template <typename T>
-  cudaError_t alloc(T **ptr, size_t count) {
-    void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
-    if (e != cudaSuccess) return e;
-    allocs.push_back(q);
-    bytes += count * sizeof(T) + 16;
-    *ptr = static_cast<T *>(q);
-    return cudaSuccess;
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
   }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
 
-  ~muffin_plan_s() {
-    for (void *q : allocs) cudaFree(q);
-  }
+}  // namespace muffin
 
-  double lnorm2(double mu, double gamma) const {
-    if (p.step_rule == 0) return K * mu * mu * Bsum + gamma * gamma * Asum;
-    return K * mu * mu * Bmax2 + gamma * gamma * Amax2;
+muffin_plan_s::~muffin_plan_s() {
+  for (int i = 0; i < 2; ++i) {
+    if (gplain[i]) cudaGraphExecDestroy(gplain[i]);
+    if (gsure[i]) cudaGraphExecDestroy(gsure[i]);
   }
-  double tau_for(double mu, double gamma) const {
-    return p.tau_safety / (0.5 * lipschitz + p.sigma * lnorm2(mu, gamma));
-  }
-  WaveArgs wave() const {
-    WaveArgs w{};
-    w.n = n; w.L = L; w.K = K; w.J = J; w.C = Cmax;
-    w.beta = beta; w.sc = sc; w.scratch = llscr;
-    for (int j = 0; j < 16; ++j) w.lvl_off[j] = lvl_off[j];
-    w.prof = profiling ? const_cast<Prof *>(&prof) : nullptr;
-    return w;
-  }
-  DctArgs dct() const {
-    DctArgs d{};
-    d.n = n; d.L = L; d.Lp = Lp; d.C = Cmax;
-    d.chi = chi; d.clo = clo; d.cthi = cthi; d.ctlo = ctlo;
-    d.alpha = alpha; d.sc = sc;
-    d.prof = profiling ? const_cast<Prof *>(&prof) : nullptr;
-    return d;
-  }
-};
+  for (void *q : allocs) cudaFree(q);
+  if (ev_in) cudaEventDestroy(ev_in);
+  if (ev_out) cudaEventDestroy(ev_out);
+  if (ws) cudaStreamDestroy(ws);
+}
 
 namespace {
 
@@ -167,6 +101,8 @@ muffin_status validate(const muffin_params *p) {
     return fail(MUFFIN_EINVAL, "n=%d must be a power of two in [2, 2048]", p->n);
   if (p->nbands < 1 || p->nbands > 4096)
     return fail(MUFFIN_EINVAL, "nbands=%d out of range [1, 4096]", p->nbands);
+  if (p->batch < 1 || (long long)p->batch * p->nbands > 65535)
+    return fail(MUFFIN_EINVAL, "batch=%d must be >= 1 with batch * nbands <= 65535", p->batch);
   if (p->n_wavelets < 1 || p->n_wavelets > 8)
     return fail(MUFFIN_EINVAL, "n_wavelets=%d out of range [1, 8]", p->n_wavelets);
   if (p->levels < 0 || p->levels > 15 || (1 << p->levels) > p->n)
@@ -188,69 +124,47 @@ muffin_status validate(const muffin_params *p) {
 muffin_status fetch(muffin_plan P, const float *src, float *dst, size_t count) {
   const cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice
                                               : cudaMemcpyHostToDevice;
-  CK(cudaMemcpyAsync(dst, src, count * sizeof(float), k, P->st));
+  CK(cudaMemcpyAsync(dst, src, count * sizeof(float), k, P->ws));
   return MUFFIN_OK;
 }
 
 muffin_status store(muffin_plan P, const float *src, float *dst, size_t count) {
   const cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice
                                               : cudaMemcpyDeviceToHost;
-  CK(cudaMemcpyAsync(dst, src, count * sizeof(float), k, P->st));
+  CK(cudaMemcpyAsync(dst, src, count * sizeof(float), k, P->ws));
   return MUFFIN_OK;
 }
 
-// out = (float) (H^T y) for a dirty cube y already on the device (FP64 path)
-muffin_status adjoint_fp64(muffin_plan P, const float *y_dev, double2 *w,
-                           double2 *tmp) {
-  const size_t cnt = P->NL;
-  CK(real_to_c64(y_dev, w, cnt, P->st));
-  CK(fft2d_c64(w, tmp, P->n, P->L, false, P->tw64, P->st));
-  CK(mul_conj_c64(w, P->hhat, cnt, P->st));
-  CK(fft2d_c64(w, tmp, P->n, P->L, true, P->tw64, P->st));
-  return MUFFIN_OK;
-}
-
-muffin_status set_scalars(muffin_plan P, double mu, double gamma) {
-  DevScalars h{};
-  h.mu = mu; h.gamma = gamma; h.sigma = P->p.sigma; h.tau = P->tau_for(mu, gamma);
-  CK(cudaMemcpyAsync(P->sc, &h, sizeof(h), cudaMemcpyHostToDevice, P->st));
-  CK(cudaStreamSynchronize(P->st));
-  P->cur_mu = mu; P->cur_gamma = gamma;
+// H^T y (unnormalised, FP64) for `nimg` bands of y already on the device
+muffin_status adjoint_fp64(muffin_plan P, const float *y_dev, const double2 *hh,
+                           int nimg, double2 *w, double2 *tmp) {
+  const size_t cnt = (size_t)nimg * P->N;
+  CK(real_to_c64(y_dev, w, cnt, P->ws));
+  CK(fft2d_c64(w, tmp, P->n, nimg, false, P->tw64, P->ws));
+  CK(mul_conj_c64(w, hh, cnt, P->ws));
+  CK(fft2d_c64(w, tmp, P->n, nimg, true, P->tw64, P->ws));
   return MUFFIN_OK;
 }
 
 muffin_status iterate_group(muffin_plan P, Group &g) {
-  CK(launch_gradient(g.x, g.g, g.b, P->S, P->kspec, P->tw32, P->n, P->L, g.C, P->st,
+  CK(launch_gradient(g.x, g.g, g.b, P->S, P->kspec, P->tw32, P->n, P->Lt, g.C, P->ws,
                      P->pp()));
-  WaveArgs w = P->wave();
-  w.C = g.C;
-  CK(wavelet_synthesis_prox(w, g, P->p.positivity, P->st));
-  CK(wavelet_analysis_dual(w, g, P->st));
-  DctArgs d = P->dct();
-  d.C = g.C;
-  CK(dct_dual(d, g, P->st));
+  WaveArgs w = P->wave(g.C);
+  CK(wavelet_synthesis_prox(w, g, P->p.positivity, P->ws));
+  CK(wavelet_analysis_dual(w, g, P->ws));
+  DctArgs d = P->dct(g.C);
+  CK(dct_dual(d, g, P->ws));
   float *t = g.x; g.x = g.xt; g.xt = t;
-  return MUFFIN_OK;
-}
-
-muffin_status reset_group(muffin_plan P, Group &g, const float *x0_dev) {
-  const size_t cl = (size_t)g.C * P->NL;
-  CK(cudaMemsetAsync(g.x, 0, cl * sizeof(float), P->st));
-  CK(cudaMemsetAsync(g.u, 0, cl * P->K * sizeof(float), P->st));
-  CK(cudaMemsetAsync(g.v, 0, cl * sizeof(float), P->st));
-  CK(cudaMemsetAsync(g.t, 0, cl * sizeof(float), P->st));
-  if (x0_dev)
-    CK(cudaMemcpyAsync(g.x, x0_dev, P->NL * sizeof(float), cudaMemcpyDeviceToDevice, P->st));
   return MUFFIN_OK;
 }
 
 // zero the derivative chains (1, 2) of a C = 3 group
 muffin_status reset_derivs(muffin_plan P, Group &g) {
   const size_t d = 2 * P->NL;
-  CK(cudaMemsetAsync(g.x + P->NL, 0, d * sizeof(float), P->st));
-  CK(cudaMemsetAsync(g.u + P->NL * P->K, 0, d * P->K * sizeof(float), P->st));
-  CK(cudaMemsetAsync(g.v + P->NL, 0, d * sizeof(float), P->st));
-  CK(cudaMemsetAsync(g.t + P->NL, 0, d * sizeof(float), P->st));
+  CK(cudaMemsetAsync(g.x + P->NL, 0, d * sizeof(float), P->ws));
+  CK(cudaMemsetAsync(g.u + P->NL * P->K, 0, d * P->K * sizeof(float), P->ws));
+  CK(cudaMemsetAsync(g.v + P->NL, 0, d * sizeof(float), P->ws));
+  CK(cudaMemsetAsync(g.t + P->NL, 0, d * sizeof(float), P->ws));
   return MUFFIN_OK;
 }
 
@@ -274,16 +188,31 @@ muffin_status ensure_op_buffers(muffin_plan P) {
   return MUFFIN_OK;
 }
 
-muffin_status plan_init(muffin_plan P, const float *psf, const float *alpha,
-                        const float *beta) {
-  const int n = P->n, L = P->L;
+muffin_status upload_cube_const(muffin_plan P) {
+  std::vector<double> cc(4 * (size_t)P->B);
+  for (int c = 0; c < P->B; ++c) {
+    cc[4 * c] = P->psc[c];
+    cc[4 * c + 1] = P->lips[c];
+    cc[4 * c + 2] = P->p.step_rule == 0 ? P->Bsum[c] : P->Bmax2[c];
+    cc[4 * c + 3] = P->p.step_rule == 0 ? P->Asum[c] : P->Amax2[c];
+  }
+  CK(cudaMemcpyAsync(P->cube_const, cc.data(), cc.size() * sizeof(double),
+                     cudaMemcpyHostToDevice, P->ws));
+  CK(cudaStreamSynchronize(P->ws));
+  return MUFFIN_OK;
+}
+
+muffin_status plan_alloc_init(muffin_plan P, const float *alpha, const float *beta) {
+  const int n = P->n, L = P->L, Lt = P->Lt, B = P->B;
   const size_t N = P->N, NL = P->NL;
   const int nh = n / 2 + 1;
-  // ---- buffers
+  CK(cudaStreamCreateWithFlags(&P->ws, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
   CK(P->alloc(&P->hhat, NL));
   CK(P->alloc(&P->w64a, NL));
   CK(P->alloc(&P->w64b, NL));
-  CK(P->alloc(&P->kspec, (size_t)L * nh * n));
+  CK(P->alloc(&P->kspec, (size_t)Lt * nh * n));
   CK(P->alloc(&P->tw32, (size_t)fft32_table_len(n)));
   CK(P->alloc(&P->tw64, (size_t)n));
   const size_t LL2 = (size_t)P->Lp * P->Lp;
@@ -291,17 +220,19 @@ muffin_status plan_init(muffin_plan P, const float *psf, const float *alpha,
   CK(P->alloc(&P->clo, LL2));
   CK(P->alloc(&P->cthi, LL2));
   CK(P->alloc(&P->ctlo, LL2));
-  CK(P->alloc(&P->alpha, N));
-  CK(P->alloc(&P->beta, (size_t)L));
-  CK(P->alloc(&P->sc, 1));
-  CK(P->alloc(&P->dred, (size_t)kRedSure + 65 * (size_t)L + 6 * 4096));
-  CK(P->alloc(&P->wband, (size_t)L));
-  CK(P->alloc(&P->S, (size_t)P->Cmax * L * nh * n));
+  CK(P->alloc(&P->alpha, (size_t)B * N));
+  CK(P->alloc(&P->beta, (size_t)Lt));
+  CK(P->alloc(&P->sc, (size_t)B));
+  CK(P->alloc(&P->cube_const, (size_t)4 * B));
+  CK(P->alloc(&P->rec_count, 1));
+  CK(P->alloc(&P->dred, kRedSure + 65 * (size_t)Lt + 6 * (size_t)(Lt > 4096 ? Lt : 4096)));
+  CK(P->alloc(&P->wband, (size_t)Lt));
+  CK(P->alloc(&P->S, (size_t)P->Cmax * Lt * nh * n));
   size_t off = 0;
   for (int j = 1; j < P->J; ++j) {
     P->lvl_off[j] = off;
     const size_t h = (size_t)(n >> j);
-    off += (size_t)P->Cmax * L * P->K * h * h;
+    off += (size_t)P->Cmax * Lt * P->K * h * h;
   }
   CK(P->alloc(&P->llscr, off ? off : 1));
   CK(P->alloc(&P->b, NL));
@@ -317,6 +248,8 @@ muffin_status plan_init(muffin_plan P, const float *psf, const float *alpha,
   }
   P->grp[0].b = P->b;
   P->grp[1].b = P->bbar;
+  P->grp_x0[0] = P->grp[0].x;
+  P->grp_x0[1] = P->grp[1].x;
 
   // ---- twiddles: FP64 e^{-2 pi i k / n}; FP32 per-stage tables of the hot FFT
   std::vector<double2> t64(n);
@@ -327,8 +260,8 @@ muffin_status plan_init(muffin_plan P, const float *psf, const float *alpha,
   }
   std::vector<float2> t32(fft32_table_len(n));
   fft32_tables(n, t32.data());
-  CK(cudaMemcpyAsync(P->tw32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice, P->st));
-  CK(cudaMemcpyAsync(P->tw64, t64.data(), n * sizeof(double2), cudaMemcpyHostToDevice, P->st));
+  CK(cudaMemcpyAsync(P->tw32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice, P->ws));
+  CK(cudaMemcpyAsync(P->tw64, t64.data(), n * sizeof(double2), cudaMemcpyHostToDevice, P->ws));
 
   // ---- filters
   double taps[8][16];
@@ -348,74 +281,265 @@ muffin_status plan_init(muffin_plan P, const float *psf, const float *alpha,
       hi[(size_t)k * Lp + l] = h; lo[(size_t)k * Lp + l] = r;
       thi[(size_t)l * Lp + k] = h; tlo[(size_t)l * Lp + k] = r;
     }
-  CK(cudaMemcpyAsync(P->chi, hi.data(), LL2 * 4, cudaMemcpyHostToDevice, P->st));
-  CK(cudaMemcpyAsync(P->clo, lo.data(), LL2 * 4, cudaMemcpyHostToDevice, P->st));
-  CK(cudaMemcpyAsync(P->cthi, thi.data(), LL2 * 4, cudaMemcpyHostToDevice, P->st));
-  CK(cudaMemcpyAsync(P->ctlo, tlo.data(), LL2 * 4, cudaMemcpyHostToDevice, P->st));
-  CK(cudaStreamSynchronize(P->st));
+  CK(cudaMemcpyAsync(P->chi, hi.data(), LL2 * 4, cudaMemcpyHostToDevice, P->ws));
+  CK(cudaMemcpyAsync(P->clo, lo.data(), LL2 * 4, cudaMemcpyHostToDevice, P->ws));
+  CK(cudaMemcpyAsync(P->cthi, thi.data(), LL2 * 4, cudaMemcpyHostToDevice, P->ws));
+  CK(cudaMemcpyAsync(P->ctlo, tlo.data(), LL2 * 4, cudaMemcpyHostToDevice, P->ws));
+  CK(cudaStreamSynchronize(P->ws));
 
-  // ---- weights (Eq. 2regpar)
-  std::vector<float> a(N, 1.f), bw(L, 1.f);
+  // ---- weights (Eq. 2regpar), per cube
+  std::vector<float> a((size_t)B * N, 1.f), bw((size_t)Lt, 1.f);
   if (alpha) {
-    if (is_device_ptr(alpha)) CK(cudaMemcpy(a.data(), alpha, N * 4, cudaMemcpyDeviceToHost));
-    else std::memcpy(a.data(), alpha, N * 4);
+    if (is_device_ptr(alpha)) CK(cudaMemcpy(a.data(), alpha, a.size() * 4, cudaMemcpyDeviceToHost));
+    else std::memcpy(a.data(), alpha, a.size() * 4);
   }
   if (beta) {
-    if (is_device_ptr(beta)) CK(cudaMemcpy(bw.data(), beta, L * 4, cudaMemcpyDeviceToHost));
-    else std::memcpy(bw.data(), beta, L * 4);
+    if (is_device_ptr(beta)) CK(cudaMemcpy(bw.data(), beta, bw.size() * 4, cudaMemcpyDeviceToHost));
+    else std::memcpy(bw.data(), beta, bw.size() * 4);
   }
-  P->Asum = P->Bsum = P->Amax2 = P->Bmax2 = 0;
-  for (size_t i = 0; i < N; ++i) {
-    const double v = a[i];
-    if (!(v >= 0) || !std::isfinite(v)) return fail(MUFFIN_EINVAL, "alpha must be finite and >= 0");
-    P->Asum += v * v; P->Amax2 = std::fmax(P->Amax2, v * v);
+  P->Asum.assign(B, 0); P->Amax2.assign(B, 0); P->Bsum.assign(B, 0); P->Bmax2.assign(B, 0);
+  P->lips.assign(B, 0); P->psc.assign(B, 0); P->mu.assign(B, 0); P->gamma.assign(B, 0);
+  for (int c = 0; c < B; ++c) {
+    for (size_t i = 0; i < N; ++i) {
+      const double v = a[(size_t)c * N + i];
+      if (!(v >= 0) || !std::isfinite(v)) return fail(MUFFIN_EINVAL, "alpha must be finite and >= 0");
+      P->Asum[c] += v * v; P->Amax2[c] = std::fmax(P->Amax2[c], v * v);
+    }
+    for (int l = 0; l < L; ++l) {
+      const double v = bw[(size_t)c * L + l];
+      if (!(v >= 0) || !std::isfinite(v)) return fail(MUFFIN_EINVAL, "beta must be finite and >= 0");
+      P->Bsum[c] += v * v; P->Bmax2[c] = std::fmax(P->Bmax2[c], v * v);
+    }
   }
-  for (int l = 0; l < L; ++l) {
-    const double v = bw[l];
-    if (!(v >= 0) || !std::isfinite(v)) return fail(MUFFIN_EINVAL, "beta must be finite and >= 0");
-    P->Bsum += v * v; P->Bmax2 = std::fmax(P->Bmax2, v * v);
-  }
-  CK(cudaMemcpyAsync(P->alpha, a.data(), N * 4, cudaMemcpyHostToDevice, P->st));
-  CK(cudaMemcpyAsync(P->beta, bw.data(), L * 4, cudaMemcpyHostToDevice, P->st));
-
-  // ---- PSF spectra (FP64), |h_hat|^2 / n^2 for the FP32 gradient, beta
-  s = fetch(P, psf, P->stage_a, NL);
-  if (s != MUFFIN_OK) return s;
-  CK(real_to_c64(P->stage_a, P->hhat, NL, P->st));
-  CK(fft2d_c64(P->hhat, P->w64a, n, L, false, P->tw64, P->st));
-  CK(make_kspec(P->hhat, P->kspec, 1.0 / ((double)n * n), n, L, P->st));
-  CK(max_abs2_c64(P->hhat, NL, P->dred + 16, P->dred, P->st));
-  CK(cudaMemcpyAsync(&P->lipschitz, P->dred, sizeof(double), cudaMemcpyDeviceToHost, P->st));
-  CK(cudaStreamSynchronize(P->st));
-  if (!(P->lipschitz > 0) || !std::isfinite(P->lipschitz))
-    return fail(MUFFIN_EINVAL, "PSF spectrum is zero or not finite (beta=%g)", P->lipschitz);
+  CK(cudaMemcpyAsync(P->alpha, a.data(), a.size() * 4, cudaMemcpyHostToDevice, P->ws));
+  CK(cudaMemcpyAsync(P->beta, bw.data(), bw.size() * 4, cudaMemcpyHostToDevice, P->ws));
+  CK(cudaMemsetAsync(P->sc, 0, (size_t)B * sizeof(DevScalars), P->ws));
+  CK(cudaStreamSynchronize(P->ws));
   return MUFFIN_OK;
 }
 
-muffin_status set_dirty(muffin_plan P, const float *dirty) {
-  muffin_status s = fetch(P, dirty, P->stage_a, P->NL);
-  if (s != MUFFIN_OK) return s;
-  s = adjoint_fp64(P, P->stage_a, P->w64a, P->w64b);
-  if (s != MUFFIN_OK) return s;
-  CK(c64_real_to_f32(P->w64a, P->b, 1.0 / ((double)P->n * P->n), P->NL, P->st));
-  P->have_b = true;
+// capture `body` on the work stream into an executable graph
+template <typename F>
+muffin_status capture(muffin_plan P, cudaGraphExec_t *exec, F body) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(P->ws, cudaStreamCaptureModeThreadLocal));
+  muffin_status s = body();
+  cudaError_t e = cudaStreamEndCapture(P->ws, &g);
+  if (s != MUFFIN_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(MUFFIN_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(MUFFIN_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return MUFFIN_OK;
+}
+
+// one ADA-PT window end: SUGAR/PSURE statistics, theta update, derivative reset
+muffin_status window_end(muffin_plan P, const muffin_sure_params *sp) {
+  Group &g = P->grp[0];
+  Group g0 = g;
+  g0.C = 1;
+  CK(launch_gradient(g0.x, g0.g, g0.b, P->S, P->kspec, P->tw32, P->n, P->Lt, 1, P->ws,
+                     P->pp()));
+  SureStatsArgs sa{};
+  sa.grad = g.g; sa.x = g.x; sa.xb = P->grp[1].x; sa.b = P->b; sa.htd = P->htd;
+  sa.wband = P->wband; sa.n = P->n; sa.L = P->Lt;
+  int bpb = 0;
+  double *part = P->dred + kRedSure + 65 * (size_t)P->Lt;
+  {
+    ProfScope ps(P->pp(), "sure_stats", 9.0 * P->NL * 4.0, 12.0 * P->NL, P->ws);
+    CK(sure_stats(sa, part, &bpb, P->ws));
+  }
+  ThetaUpdateArgs ta{};
+  ta.B = P->B; ta.sc = P->sc; ta.partials = part; ta.nb_per_cube = bpb * P->L;
+  ta.record = P->records; ta.rec_count = P->rec_count;
+  ta.eta_mu = sp->eta_mu; ta.eta_gamma = sp->eta_gamma; ta.theta_min = sp->theta_min;
+  ta.cube_const = P->cube_const; ta.safety = P->p.tau_safety; ta.K = P->K;
+  {
+    ProfScope ps(P->pp(), "theta_update", 6.0 * 8.0 * bpb * P->Lt, 0.0, P->ws);
+    CK(theta_update(ta, P->ws));
+  }
+  if (sp->reset_each_window) {
+    muffin_status s = reset_derivs(P, P->grp[0]);
+    if (s != MUFFIN_OK) return s;
+    s = reset_derivs(P, P->grp[1]);
+    if (s != MUFFIN_OK) return s;
+  }
   return MUFFIN_OK;
 }
 
 }  // namespace
 
+// ---------------------------------------------------------------- internal API
+namespace muffin {
+namespace pi {
+
+muffin_status enter(muffin_plan P) {
+  CK(cudaEventRecord(P->ev_in, P->st));
+  CK(cudaStreamWaitEvent(P->ws, P->ev_in, 0));
+  return MUFFIN_OK;
+}
+
+muffin_status leave(muffin_plan P, bool sync) {
+  CK(cudaEventRecord(P->ev_out, P->ws));
+  CK(cudaStreamWaitEvent(P->st, P->ev_out, 0));
+  if (sync) CK(cudaStreamSynchronize(P->ws));
+  P->prof.resolve();
+  return MUFFIN_OK;
+}
+
+muffin_status load_psf(muffin_plan P, int b0, int b1, const float *psf) {
+  const size_t cnt = (size_t)(b1 - b0) * P->NLc;
+  const size_t off = (size_t)b0 * P->NLc;
+  const int nimg = (b1 - b0) * P->L;
+  muffin_status s = fetch(P, psf, P->stage_a + off, cnt);
+  if (s != MUFFIN_OK) return s;
+  double2 *hh = P->hhat + off;
+  CK(real_to_c64(P->stage_a + off, hh, cnt, P->ws));
+  CK(fft2d_c64(hh, P->w64a + off, P->n, nimg, false, P->tw64, P->ws));
+  const int nh = P->n / 2 + 1;
+  CK(make_kspec(hh, P->kspec + (size_t)b0 * P->L * nh * P->n, 1.0 / ((double)P->n * P->n),
+                P->n, nimg, P->ws));
+  for (int c = b0; c < b1; ++c) {
+    CK(max_abs2_c64(P->hhat + (size_t)c * P->NLc, P->NLc, P->dred + 16, P->dred, P->ws));
+    double lip = 0;
+    CK(cudaMemcpyAsync(&lip, P->dred, sizeof(double), cudaMemcpyDeviceToHost, P->ws));
+    CK(cudaStreamSynchronize(P->ws));
+    if (!(lip > 0) || !std::isfinite(lip))
+      return fail(MUFFIN_EINVAL, "PSF spectrum of cube %d is zero or not finite (beta=%g)", c, lip);
+    P->lips[c] = lip;
+  }
+  return MUFFIN_OK;
+}
+
+muffin_status load_dirty(muffin_plan P, int b0, int b1, const float *dirty) {
+  const size_t cnt = (size_t)(b1 - b0) * P->NLc;
+  const size_t off = (size_t)b0 * P->NLc;
+  muffin_status s = fetch(P, dirty, P->stage_a + off, cnt);
+  if (s != MUFFIN_OK) return s;
+  s = adjoint_fp64(P, P->stage_a + off, P->hhat + off, (b1 - b0) * P->L, P->w64a + off,
+                   P->w64b + off);
+  if (s != MUFFIN_OK) return s;
+  CK(c64_real_to_f32(P->w64a + off, P->b + off, 1.0 / ((double)P->n * P->n), cnt, P->ws));
+  return MUFFIN_OK;
+}
+
+muffin_status reset_cubes(muffin_plan P, int gi, int b0, int b1, const float *x0_dev) {
+  Group &g = P->grp[gi];
+  const size_t cnt = (size_t)(b1 - b0) * P->NLc, off = (size_t)b0 * P->NLc;
+  for (int c = 0; c < g.C; ++c) {
+    const size_t co = (size_t)c * P->NL + off;
+    CK(cudaMemsetAsync(g.x + co, 0, cnt * sizeof(float), P->ws));
+    CK(cudaMemsetAsync(g.u + co * P->K, 0, cnt * P->K * sizeof(float), P->ws));
+    CK(cudaMemsetAsync(g.v + co, 0, cnt * sizeof(float), P->ws));
+    CK(cudaMemsetAsync(g.t + co, 0, cnt * sizeof(float), P->ws));
+  }
+  if (x0_dev)
+    CK(cudaMemcpyAsync(g.x + off, x0_dev, cnt * sizeof(float), cudaMemcpyDeviceToDevice, P->ws));
+  return MUFFIN_OK;
+}
+
+muffin_status set_theta(muffin_plan P, int b0, int b1, const double *mu, const double *gamma) {
+  std::vector<DevScalars> h(b1 - b0);
+  for (int c = b0; c < b1; ++c) {
+    DevScalars &d = h[c - b0];
+    d.mu = mu[c - b0]; d.gamma = gamma[c - b0]; d.sigma = P->p.sigma;
+    d.tau = P->tau_for(c, d.mu, d.gamma);
+    P->mu[c] = d.mu; P->gamma[c] = d.gamma;
+  }
+  CK(cudaMemcpyAsync(P->sc + b0, h.data(), h.size() * sizeof(DevScalars),
+                     cudaMemcpyHostToDevice, P->ws));
+  CK(cudaStreamSynchronize(P->ws));
+  return MUFFIN_OK;
+}
+
+muffin_status run_plain(muffin_plan P, int iters) {
+  Group &g = P->grp[0];
+  Group plain = g;
+  plain.C = 1;
+  muffin_status s = MUFFIN_OK;
+  const bool graphs = P->use_graphs && !P->profiling;
+  int k = 0;
+  while (k < iters) {
+    const int par = plain.x == P->grp_x0[0] ? 0 : 1;
+    if (graphs && iters - k >= 2 && P->gplain[par] == nullptr && k > 0) {
+      Group cap = plain;
+      s = capture(P, &P->gplain[par], [&]() -> muffin_status {
+        muffin_status r = iterate_group(P, cap);
+        if (r == MUFFIN_OK) r = iterate_group(P, cap);
+        return r;
+      });
+      if (s != MUFFIN_OK) return s;
+    }
+    if (graphs && iters - k >= 2 && P->gplain[par] != nullptr) {
+      CK(cudaGraphLaunch(P->gplain[par], P->ws));
+      k += 2;      // two swaps: pointers unchanged
+    } else {
+      s = iterate_group(P, plain);
+      if (s != MUFFIN_OK) return s;
+      ++k;
+    }
+  }
+  g.x = plain.x; g.xt = plain.xt;
+  return MUFFIN_OK;
+}
+
+muffin_status fetch_x(muffin_plan P, int b0, int b1, float *dst) {
+  return store(P, P->grp[0].x + (size_t)b0 * P->NLc, dst, (size_t)(b1 - b0) * P->NLc);
+}
+
+muffin_status create(const muffin_params *p, const float *psf, const float *alpha,
+                     const float *beta, void *stream, muffin_plan *out) {
+  if (!out) return fail(MUFFIN_EINVAL, "out is NULL");
+  *out = nullptr;
+  muffin_status s = validate(p);
+  if (s != MUFFIN_OK) return s;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(MUFFIN_ECUDA, "no CUDA device available");
+  }
+  muffin_plan P = new (std::nothrow) muffin_plan_s();
+  if (!P) return fail(MUFFIN_ENOMEM, "host allocation failed");
+  P->p = *p;
+  P->n = p->n; P->L = p->nbands; P->K = p->n_wavelets; P->J = p->levels;
+  P->B = p->batch; P->Lt = P->B * P->L;
+  P->Lp = (P->L + 15) / 16 * 16;
+  P->Cmax = p->sure ? 3 : 1;
+  P->N = (size_t)P->n * P->n;
+  P->NLc = P->N * P->L;
+  P->NL = P->N * P->Lt;
+  P->st = static_cast<cudaStream_t>(stream);
+  s = plan_alloc_init(P, alpha, beta);
+  if (s == MUFFIN_OK && psf) s = load_psf(P, 0, P->B, psf);
+  if (s == MUFFIN_OK) s = upload_cube_const(P);
+  if (s != MUFFIN_OK) {
+    if (P->ws) cudaStreamSynchronize(P->ws);
+    delete P;
+    return s;
+  }
+  *out = P;
+  return MUFFIN_OK;
+}
+
+}  // namespace pi
+}  // namespace muffin
+
+// ---------------------------------------------------------------- C ABI
 extern "C" {
 
 const char *muffin_last_error(void) { return g_err.c_str(); }
 
-const char *muffin_version(void) { return "muffin-gb300 0.1 (sm_103a)"; }
+const char *muffin_version(void) { return "muffin-gb300 0.2 (sm_103a)"; }
 
 void muffin_params_default(muffin_params *p, int32_t n, int32_t nbands) {
   if (!p) return;
   std::memset(p, 0, sizeof(*p));
   p->n = n; p->nbands = nbands; p->n_wavelets = 8; p->levels = 3;
   p->sigma = 10.0; p->step_rule = 0; p->tau_safety = 0.99; p->positivity = 1;
-  p->sure = 0;
+  p->sure = 0; p->batch = 1;
 }
 
 void muffin_sure_params_default(muffin_sure_params *s) {
@@ -440,37 +564,16 @@ muffin_status muffin_dct_table(int32_t L, double *C) {
 muffin_status muffin_plan_create(const muffin_params *p, const float *psf,
                                  const float *alpha, const float *beta,
                                  void *stream, muffin_plan *out) {
-  if (!out) return fail(MUFFIN_EINVAL, "out is NULL");
-  *out = nullptr;
-  muffin_status s = validate(p);
-  if (s != MUFFIN_OK) return s;
-  if (!psf) return fail(MUFFIN_EINVAL, "psf is NULL");
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
-    cudaGetLastError();
-    return fail(MUFFIN_ECUDA, "no CUDA device available");
+  if (!psf) {
+    if (out) *out = nullptr;
+    return fail(MUFFIN_EINVAL, "psf is NULL");
   }
-  muffin_plan P = new (std::nothrow) muffin_plan_s();
-  if (!P) return fail(MUFFIN_ENOMEM, "host allocation failed");
-  P->p = *p;
-  P->n = p->n; P->L = p->nbands; P->K = p->n_wavelets; P->J = p->levels;
-  P->Lp = (P->L + 15) / 16 * 16;
-  P->Cmax = p->sure ? 3 : 1;
-  P->N = (size_t)P->n * P->n;
-  P->NL = P->N * P->L;
-  P->st = static_cast<cudaStream_t>(stream);
-  s = plan_init(P, psf, alpha, beta);
-  if (s != MUFFIN_OK) {
-    delete P;
-    return s;
-  }
-  *out = P;
-  return MUFFIN_OK;
+  return pi::create(p, psf, alpha, beta, stream, out);
 }
 
 void muffin_plan_destroy(muffin_plan P) {
   if (!P) return;
-  cudaStreamSynchronize(P->st);
+  cudaStreamSynchronize(P->ws);
   delete P;
 }
 
@@ -478,7 +581,55 @@ size_t muffin_plan_device_bytes(muffin_plan P) { return P ? P->bytes : 0; }
 
 muffin_status muffin_plan_lipschitz(muffin_plan P, double *beta) {
   if (!P || !beta) return fail(MUFFIN_EINVAL, "NULL argument");
-  *beta = P->lipschitz;
+  for (int c = 0; c < P->B; ++c) beta[c] = P->lips[c];
+  return MUFFIN_OK;
+}
+
+muffin_status muffin_plan_graphs(muffin_plan P, int32_t on) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  P->use_graphs = on != 0;
+  return MUFFIN_OK;
+}
+
+muffin_status muffin_solve_batch(muffin_plan P, const float *dirty, float *x,
+                                 int32_t iters, const double *mu, const double *gamma,
+                                 int32_t flags, muffin_info *info) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  if (!x || !mu || !gamma) return fail(MUFFIN_EINVAL, "x, mu and gamma must be non-NULL");
+  if (iters < 0) return fail(MUFFIN_EINVAL, "iters must be >= 0");
+  for (int c = 0; c < P->B; ++c)
+    if (!(mu[c] >= 0) || !(gamma[c] >= 0) || !std::isfinite(mu[c]) || !std::isfinite(gamma[c]))
+      return fail(MUFFIN_EINVAL, "mu and gamma must be finite and >= 0");
+  const bool warm = flags & MUFFIN_WARM;
+  if (warm && !P->have_state) return fail(MUFFIN_ESTATE, "no state to continue from");
+  if (!dirty && !(warm && P->have_b)) return fail(MUFFIN_EINVAL, "dirty is NULL");
+  muffin_status s = pi::enter(P);
+  if (s != MUFFIN_OK) return s;
+  if (dirty) {
+    s = pi::load_dirty(P, 0, P->B, dirty);
+    if (s != MUFFIN_OK) return s;
+    P->have_b = true;
+  }
+  if (!warm) {
+    s = fetch(P, x, P->stage_b, P->NL);
+    if (s == MUFFIN_OK) s = pi::reset_cubes(P, 0, 0, P->B, P->stage_b);
+    if (s != MUFFIN_OK) return s;
+  }
+  s = pi::set_theta(P, 0, P->B, mu, gamma);
+  if (s != MUFFIN_OK) return s;
+  P->have_state = true;
+  P->have_sure_state = false;
+  s = pi::run_plain(P, iters);
+  if (s != MUFFIN_OK) return s;
+  s = pi::fetch_x(P, 0, P->B, x);
+  if (s != MUFFIN_OK) return s;
+  s = pi::leave(P, true);
+  if (s != MUFFIN_OK) return s;
+  if (info) {
+    info->iters_done = iters; info->tau = P->tau_for(0, mu[0], gamma[0]);
+    info->sigma = P->p.sigma; info->lipschitz = P->lips[0];
+    info->mu = mu[0]; info->gamma = gamma[0]; info->records = 0;
+  }
   return MUFFIN_OK;
 }
 
@@ -486,44 +637,8 @@ muffin_status muffin_solve(muffin_plan P, const float *dirty, float *x,
                            int32_t iters, double mu, double gamma,
                            int32_t flags, muffin_info *info) {
   if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
-  if (!x) return fail(MUFFIN_EINVAL, "x is NULL");
-  if (iters < 0) return fail(MUFFIN_EINVAL, "iters must be >= 0");
-  if (!(mu >= 0) || !(gamma >= 0) || !std::isfinite(mu) || !std::isfinite(gamma))
-    return fail(MUFFIN_EINVAL, "mu and gamma must be finite and >= 0");
-  const bool warm = flags & MUFFIN_WARM;
-  if (warm && !P->have_state) return fail(MUFFIN_ESTATE, "no state to continue from");
-  if (!dirty && !(warm && P->have_b)) return fail(MUFFIN_EINVAL, "dirty is NULL");
-  muffin_status s;
-  if (dirty) { s = set_dirty(P, dirty); if (s != MUFFIN_OK) return s; }
-  Group &g = P->grp[0];
-  Group plain = g;
-  plain.C = 1;
-  if (!warm) {
-    s = fetch(P, x, P->stage_b, P->NL);
-    if (s != MUFFIN_OK) return s;
-    s = reset_group(P, plain, P->stage_b);
-    if (s != MUFFIN_OK) return s;
-  }
-  s = set_scalars(P, mu, gamma);
-  if (s != MUFFIN_OK) return s;
-  P->have_state = true;
-  P->have_sure_state = false;
-  for (int k = 0; k < iters; ++k) {
-    s = iterate_group(P, plain);
-    if (s != MUFFIN_OK) return s;
-  }
-  // keep the swapped pointers (x <-> x~) in the plan's group
-  g.x = plain.x; g.xt = plain.xt;
-  s = store(P, g.x, x, P->NL);
-  if (s != MUFFIN_OK) return s;
-  CK(cudaStreamSynchronize(P->st));
-  P->prof.resolve();
-  if (info) {
-    info->iters_done = iters; info->tau = P->tau_for(mu, gamma); info->sigma = P->p.sigma;
-    info->lipschitz = P->lipschitz; info->mu = mu; info->gamma = gamma;
-    info->records = 0;
-  }
-  return MUFFIN_OK;
+  std::vector<double> m(P->B, mu), g(P->B, gamma);
+  return muffin_solve_batch(P, dirty, x, iters, m.data(), g.data(), flags, info);
 }
 
 muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
@@ -540,120 +655,143 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
   if (warm && !P->have_sure_state) return fail(MUFFIN_ESTATE, "no ADA-PT state to continue from");
   if (!warm && (!dirty || !delta || !noise_var))
     return fail(MUFFIN_EINVAL, "dirty, delta and noise_var are required");
-  if (!warm && (!(theta[0] >= 0) || !(theta[1] >= 0)))
-    return fail(MUFFIN_EINVAL, "theta must be >= 0");
-  muffin_status s;
+  const int B = P->B;
+  if (!warm)
+    for (int c = 0; c < B; ++c)
+      if (!(theta[2 * c] >= 0) || !(theta[2 * c + 1] >= 0))
+        return fail(MUFFIN_EINVAL, "theta must be >= 0");
+  muffin_status s = pi::enter(P);
+  if (s != MUFFIN_OK) return s;
   const size_t NL = P->NL;
   const double scale = 1.0 / ((double)P->n * P->n);
   if (!warm) {
-    // H^T y and H^T delta in FP64; b_bar = H^T (y + eps delta)
-    s = set_dirty(P, dirty);
+    // H^T y and H^T delta in FP64; b_bar = H^T y + eps H^T delta
+    s = pi::load_dirty(P, 0, B, dirty);
     if (s != MUFFIN_OK) return s;
+    P->have_b = true;
     s = fetch(P, delta, P->stage_b, NL);
     if (s != MUFFIN_OK) return s;
-    s = adjoint_fp64(P, P->stage_b, P->w64b, P->w64a);
+    s = adjoint_fp64(P, P->stage_b, P->hhat, P->Lt, P->w64b, P->w64a);
     if (s != MUFFIN_OK) return s;
-    CK(c64_real_to_f32(P->w64b, P->htd, scale, NL, P->st));
-    CK(axpy_f32(P->b, P->htd, (float)sp->eps, P->bbar, NL, P->st));
+    CK(c64_real_to_f32(P->w64b, P->htd, scale, NL, P->ws));
+    CK(axpy_f32(P->b, P->htd, (float)sp->eps, P->bbar, NL, P->ws));
     // per-band energies and weights
-    std::vector<double> ysq(P->L);
-    CK(band_sumsq(P->stage_a, P->L, P->N, P->dred, P->st));
-    CK(cudaMemcpyAsync(ysq.data(), P->dred, P->L * sizeof(double), cudaMemcpyDeviceToHost, P->st));
-    CK(cudaStreamSynchronize(P->st));
-    std::vector<double> w(P->L);
-    double c = 0;
-    for (int l = 0; l < P->L; ++l) {
-      if (!(noise_var[l] >= 0)) return fail(MUFFIN_EINVAL, "noise_var must be >= 0");
-      c += ysq[l] - (double)P->N * noise_var[l];
-      w[l] = 2.0 * noise_var[l] / sp->eps;
+    std::vector<double> ysq(P->Lt);
+    CK(band_sumsq(P->stage_a, P->Lt, P->N, P->dred, P->ws));
+    CK(cudaMemcpyAsync(ysq.data(), P->dred, P->Lt * sizeof(double), cudaMemcpyDeviceToHost, P->ws));
+    CK(cudaStreamSynchronize(P->ws));
+    std::vector<double> w(P->Lt);
+    for (int c = 0; c < B; ++c) {
+      double cst = 0;
+      for (int l = c * P->L; l < (c + 1) * P->L; ++l) {
+        if (!(noise_var[l] >= 0)) return fail(MUFFIN_EINVAL, "noise_var must be >= 0");
+        cst += ysq[l] - (double)P->N * noise_var[l];
+        w[l] = 2.0 * noise_var[l] / sp->eps;
+      }
+      P->psc[c] = cst;
     }
-    P->psure_const = c;
-    CK(cudaMemcpyAsync(P->wband, w.data(), P->L * sizeof(double), cudaMemcpyHostToDevice, P->st));
+    CK(cudaMemcpyAsync(P->wband, w.data(), P->Lt * sizeof(double), cudaMemcpyHostToDevice, P->ws));
+    s = upload_cube_const(P);
+    if (s != MUFFIN_OK) return s;
     s = fetch(P, x, P->stage_b, NL);
+    if (s == MUFFIN_OK) s = pi::reset_cubes(P, 0, 0, B, P->stage_b);
+    if (s == MUFFIN_OK) s = pi::reset_cubes(P, 1, 0, B, P->stage_b);
     if (s != MUFFIN_OK) return s;
-    s = reset_group(P, P->grp[0], P->stage_b);
-    if (s != MUFFIN_OK) return s;
-    s = reset_group(P, P->grp[1], P->stage_b);
-    if (s != MUFFIN_OK) return s;
-    s = set_scalars(P, theta[0], theta[1]);
+    std::vector<double> m(B), g(B);
+    for (int c = 0; c < B; ++c) { m[c] = theta[2 * c]; g[c] = theta[2 * c + 1]; }
+    s = pi::set_theta(P, 0, B, m.data(), g.data());
     if (s != MUFFIN_OK) return s;
     P->k_done = 0;
     P->have_state = false;
     P->have_sure_state = true;
   }
-  const int nrec_max = sp->iters / sp->window + 1;
-  if (nrec_max > P->max_records) {
+  const int cap = sp->iters / sp->window + 1;
+  if (cap > P->max_records) {
     double *r = nullptr;
-    CK(P->alloc(&r, (size_t)7 * nrec_max));
+    CK(P->alloc(&r, (size_t)7 * B * cap));
     P->records = r;
-    P->max_records = nrec_max;
+    P->max_records = cap;
+    for (int i = 0; i < 2; ++i)   // graphs hold the old record pointer
+      if (P->gsure[i]) { cudaGraphExecDestroy(P->gsure[i]); P->gsure[i] = nullptr; }
   }
-  const double rule_B = P->p.step_rule == 0 ? P->Bsum : P->Bmax2;
-  const double rule_A = P->p.step_rule == 0 ? P->Asum : P->Amax2;
-  int nrec = 0;
-  for (int it = 0; it < sp->iters; ++it) {
+  CK(cudaMemsetAsync(P->rec_count, 0, sizeof(int), P->ws));
+  // cached window graphs depend on the window length and the update settings
+  if (P->gsure_window != sp->window || P->gsure_reset != sp->reset_each_window ||
+      P->gsure_eta[0] != sp->eta_mu || P->gsure_eta[1] != sp->eta_gamma ||
+      P->gsure_tmin != sp->theta_min) {
+    for (int i = 0; i < 2; ++i)
+      if (P->gsure[i]) { cudaGraphExecDestroy(P->gsure[i]); P->gsure[i] = nullptr; }
+    P->gsure_window = sp->window; P->gsure_reset = sp->reset_each_window;
+    P->gsure_eta[0] = sp->eta_mu; P->gsure_eta[1] = sp->eta_gamma; P->gsure_tmin = sp->theta_min;
+  }
+  const bool graphs = P->use_graphs && !P->profiling;
+  std::vector<long long> rec_k;
+  int it = 0;
+  while (it < sp->iters) {
+    const bool at_boundary = P->k_done % sp->window == 0;
+    const int par = P->grp[0].x == P->grp_x0[0] ? 0 : 1;
+    if (graphs && at_boundary && sp->iters - it >= sp->window && it > 0) {
+      if (!P->gsure[par]) {
+        const Group c0 = P->grp[0], c1 = P->grp[1];
+        s = capture(P, &P->gsure[par], [&]() -> muffin_status {
+          for (int q = 0; q < sp->window; ++q) {
+            muffin_status r = iterate_group(P, P->grp[0]);
+            if (r == MUFFIN_OK) r = iterate_group(P, P->grp[1]);
+            if (r != MUFFIN_OK) return r;
+          }
+          return window_end(P, sp);
+        });
+        // capture only records the launches: restore the pointers
+        P->grp[0] = c0; P->grp[1] = c1;
+        if (s != MUFFIN_OK) return s;
+      }
+      CK(cudaGraphLaunch(P->gsure[par], P->ws));
+      if (sp->window & 1) {
+        std::swap(P->grp[0].x, P->grp[0].xt);
+        std::swap(P->grp[1].x, P->grp[1].xt);
+      }
+      it += sp->window;
+      P->k_done += sp->window;
+      rec_k.push_back(P->k_done);
+      continue;
+    }
     s = iterate_group(P, P->grp[0]);
+    if (s == MUFFIN_OK) s = iterate_group(P, P->grp[1]);
     if (s != MUFFIN_OK) return s;
-    s = iterate_group(P, P->grp[1]);
-    if (s != MUFFIN_OK) return s;
+    ++it;
     P->k_done++;
     if (P->k_done % sp->window == 0) {
-      Group &g = P->grp[0];
-      // gradient of the y-primal at the new x (chain 0 only)
-      CK(launch_gradient(g.x, g.g, g.b, P->S, P->kspec, P->tw32, P->n, P->L, 1, P->st,
-                         P->pp()));
-      SureStatsArgs sa{};
-      sa.grad = g.g; sa.x = g.x; sa.xb = P->grp[1].x; sa.b = P->b; sa.htd = P->htd;
-      sa.wband = P->wband; sa.n = P->n; sa.L = P->L;
-      int nb = 0;
-      double *part = P->dred + kRedSure + 65 * (size_t)P->L;
-      {
-        ProfScope ps(P->pp(), "sure_stats", 9.0 * NL * 4.0, 12.0 * NL, P->st);
-        CK(sure_stats(sa, part, &nb, P->st));
-      }
-      ThetaUpdateArgs ta{};
-      ta.sc = P->sc; ta.partials = part; ta.nblocks = nb;
-      ta.record = P->records + 7 * nrec;
-      ta.k = (int)P->k_done;
-      ta.eta_mu = sp->eta_mu; ta.eta_gamma = sp->eta_gamma; ta.theta_min = sp->theta_min;
-      ta.psure_const = P->psure_const;
-      ta.safety = P->p.tau_safety; ta.lipschitz = P->lipschitz; ta.K = P->K;
-      ta.Bsum = rule_B; ta.Asum = rule_A;
-      {
-        ProfScope ps(P->pp(), "theta_update", 6.0 * 8.0 * nb, 0.0, P->st);
-        CK(theta_update(ta, P->st));
-      }
-      ++nrec;
-      if (sp->reset_each_window) {
-        s = reset_derivs(P, P->grp[0]);
-        if (s != MUFFIN_OK) return s;
-        s = reset_derivs(P, P->grp[1]);
-        if (s != MUFFIN_OK) return s;
-      }
+      s = window_end(P, sp);
+      if (s != MUFFIN_OK) return s;
+      rec_k.push_back(P->k_done);
     }
   }
-  s = store(P, P->grp[0].x, x, NL);
+  const int nrec = (int)rec_k.size();
+  s = pi::fetch_x(P, 0, B, x);
   if (s != MUFFIN_OK) return s;
-  DevScalars hs{};
-  CK(cudaMemcpyAsync(&hs, P->sc, sizeof(hs), cudaMemcpyDeviceToHost, P->st));
-  std::vector<double> rec((size_t)7 * (nrec ? nrec : 1));
+  std::vector<DevScalars> hs(B);
+  CK(cudaMemcpyAsync(hs.data(), P->sc, B * sizeof(DevScalars), cudaMemcpyDeviceToHost, P->ws));
+  std::vector<double> rec((size_t)7 * B * (nrec ? nrec : 1));
   if (nrec)
-    CK(cudaMemcpyAsync(rec.data(), P->records, (size_t)7 * nrec * sizeof(double),
-                       cudaMemcpyDeviceToHost, P->st));
-  CK(cudaStreamSynchronize(P->st));
-  P->prof.resolve();
-  theta[0] = hs.mu; theta[1] = hs.gamma;
-  P->cur_mu = hs.mu; P->cur_gamma = hs.gamma;
+    CK(cudaMemcpyAsync(rec.data(), P->records, (size_t)7 * B * nrec * sizeof(double),
+                       cudaMemcpyDeviceToHost, P->ws));
+  s = pi::leave(P, true);
+  if (s != MUFFIN_OK) return s;
+  for (int c = 0; c < B; ++c) {
+    theta[2 * c] = hs[c].mu; theta[2 * c + 1] = hs[c].gamma;
+    P->mu[c] = hs[c].mu; P->gamma[c] = hs[c].gamma;
+  }
   if (trace)
-    for (int q = 0; q < nrec; ++q) {
-      const double *r = &rec[(size_t)7 * q];
-      trace[q].k = (int32_t)r[0]; trace[q].mu = r[1]; trace[q].gamma = r[2];
-      trace[q].sugar_mu = r[3]; trace[q].sugar_gamma = r[4]; trace[q].psure = r[5];
-      trace[q].tau = r[6];
-    }
+    for (int q = 0; q < nrec; ++q)
+      for (int c = 0; c < B; ++c) {
+        const double *r = &rec[((size_t)q * B + c) * 7];
+        muffin_sure_record &t = trace[(size_t)c * cap + q];
+        t.k = (int32_t)rec_k[q]; t.mu = r[1]; t.gamma = r[2];
+        t.sugar_mu = r[3]; t.sugar_gamma = r[4]; t.psure = r[5]; t.tau = r[6];
+      }
   if (info) {
-    info->iters_done = sp->iters; info->tau = hs.tau; info->sigma = P->p.sigma;
-    info->lipschitz = P->lipschitz; info->mu = hs.mu; info->gamma = hs.gamma;
+    info->iters_done = sp->iters; info->tau = hs[0].tau; info->sigma = P->p.sigma;
+    info->lipschitz = P->lips[0]; info->mu = hs[0].mu; info->gamma = hs[0].gamma;
     info->records = nrec;
   }
   return MUFFIN_OK;
@@ -685,19 +823,20 @@ muffin_status muffin_profile_read(muffin_plan P, muffin_kernel_stat *out,
   return MUFFIN_OK;
 }
 
+}  // extern "C"
+
 // ---------------------------------------------------------------- checkpoints
 namespace {
 struct BlobHeader {
   char magic[8];
-  int32_t n, L, K, J, sure, pad;
+  int32_t n, L, K, J, sure, B;
   long long k_done;
-  double psure_const, cur_mu, cur_gamma;
-  int32_t have_b, have_state, have_sure_state, pad2;
+  int32_t have_b, have_state, have_sure_state, pad;
 };
 
 struct Seg {
-  float *p;
-  size_t count;
+  void *p;
+  size_t bytes;
 };
 
 std::vector<Seg> segments(muffin_plan P) {
@@ -705,25 +844,29 @@ std::vector<Seg> segments(muffin_plan P) {
   const int ng = P->p.sure ? 2 : 1;
   for (int i = 0; i < ng; ++i) {
     Group &g = P->grp[i];
-    const size_t cl = (size_t)g.C * P->NL;
+    const size_t cl = (size_t)g.C * P->NL * sizeof(float);
     v.push_back({g.x, cl});
     v.push_back({g.u, cl * P->K});
     v.push_back({g.v, cl});
     v.push_back({g.t, cl});
   }
-  v.push_back({P->b, P->NL});
+  v.push_back({P->b, P->NL * sizeof(float)});
   if (P->p.sure) {
-    v.push_back({P->bbar, P->NL});
-    v.push_back({P->htd, P->NL});
+    v.push_back({P->bbar, P->NL * sizeof(float)});
+    v.push_back({P->htd, P->NL * sizeof(float)});
   }
+  v.push_back({P->sc, P->B * sizeof(DevScalars)});
+  v.push_back({P->wband, P->Lt * sizeof(double)});
   return v;
 }
 }  // namespace
 
+extern "C" {
+
 muffin_status muffin_state_size(muffin_plan P, size_t *bytes) {
   if (!P || !bytes) return fail(MUFFIN_EINVAL, "NULL argument");
-  size_t t = sizeof(BlobHeader) + sizeof(DevScalars) + P->L * sizeof(double);
-  for (const Seg &s : segments(P)) t += s.count * sizeof(float);
+  size_t t = sizeof(BlobHeader) + 3 * P->B * sizeof(double);
+  for (const Seg &s : segments(P)) t += s.bytes;
   *bytes = t;
   return MUFFIN_OK;
 }
@@ -735,23 +878,24 @@ muffin_status muffin_state_export(muffin_plan P, void *host_buf, size_t bytes) {
   if (!host_buf || bytes < need) return fail(MUFFIN_EINVAL, "buffer too small (%zu < %zu)", bytes, need);
   char *o = static_cast<char *>(host_buf);
   BlobHeader h{};
-  std::memcpy(h.magic, "MUFFIN1", 8);
-  h.n = P->n; h.L = P->L; h.K = P->K; h.J = P->J; h.sure = P->p.sure;
-  h.k_done = P->k_done; h.psure_const = P->psure_const;
-  h.cur_mu = P->cur_mu; h.cur_gamma = P->cur_gamma;
+  std::memcpy(h.magic, "MUFFIN2", 8);
+  h.n = P->n; h.L = P->L; h.K = P->K; h.J = P->J; h.sure = P->p.sure; h.B = P->B;
+  h.k_done = P->k_done;
   h.have_b = P->have_b; h.have_state = P->have_state; h.have_sure_state = P->have_sure_state;
   std::memcpy(o, &h, sizeof(h));
   o += sizeof(h);
-  CK(cudaMemcpyAsync(o, P->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, P->st));
-  o += sizeof(DevScalars);
-  CK(cudaMemcpyAsync(o, P->wband, P->L * sizeof(double), cudaMemcpyDeviceToHost, P->st));
-  o += P->L * sizeof(double);
-  for (const Seg &sg : segments(P)) {
-    CK(cudaMemcpyAsync(o, sg.p, sg.count * sizeof(float), cudaMemcpyDeviceToHost, P->st));
-    o += sg.count * sizeof(float);
+  for (int c = 0; c < P->B; ++c) {
+    const double v[3] = {P->psc[c], P->mu[c], P->gamma[c]};
+    std::memcpy(o, v, sizeof(v));
+    o += sizeof(v);
   }
-  CK(cudaStreamSynchronize(P->st));
-  return MUFFIN_OK;
+  s = pi::enter(P);
+  if (s != MUFFIN_OK) return s;
+  for (const Seg &sg : segments(P)) {
+    CK(cudaMemcpyAsync(o, sg.p, sg.bytes, cudaMemcpyDeviceToHost, P->ws));
+    o += sg.bytes;
+  }
+  return pi::leave(P, true);
 }
 
 muffin_status muffin_state_import(muffin_plan P, const void *host_buf, size_t bytes) {
@@ -762,21 +906,27 @@ muffin_status muffin_state_import(muffin_plan P, const void *host_buf, size_t by
   const char *o = static_cast<const char *>(host_buf);
   BlobHeader h;
   std::memcpy(&h, o, sizeof(h));
-  if (std::memcmp(h.magic, "MUFFIN1", 8) != 0 || h.n != P->n || h.L != P->L ||
-      h.K != P->K || h.J != P->J || h.sure != P->p.sure)
+  if (std::memcmp(h.magic, "MUFFIN2", 8) != 0 || h.n != P->n || h.L != P->L ||
+      h.K != P->K || h.J != P->J || h.sure != P->p.sure || h.B != P->B)
     return fail(MUFFIN_EINVAL, "state blob does not match this plan");
   o += sizeof(h);
-  CK(cudaMemcpyAsync(P->sc, o, sizeof(DevScalars), cudaMemcpyHostToDevice, P->st));
-  o += sizeof(DevScalars);
-  CK(cudaMemcpyAsync(P->wband, o, P->L * sizeof(double), cudaMemcpyHostToDevice, P->st));
-  o += P->L * sizeof(double);
-  for (const Seg &sg : segments(P)) {
-    CK(cudaMemcpyAsync(sg.p, o, sg.count * sizeof(float), cudaMemcpyHostToDevice, P->st));
-    o += sg.count * sizeof(float);
+  for (int c = 0; c < P->B; ++c) {
+    double v[3];
+    std::memcpy(v, o, sizeof(v));
+    o += sizeof(v);
+    P->psc[c] = v[0]; P->mu[c] = v[1]; P->gamma[c] = v[2];
   }
-  CK(cudaStreamSynchronize(P->st));
-  P->k_done = h.k_done; P->psure_const = h.psure_const;
-  P->cur_mu = h.cur_mu; P->cur_gamma = h.cur_gamma;
+  s = pi::enter(P);
+  if (s != MUFFIN_OK) return s;
+  for (const Seg &sg : segments(P)) {
+    CK(cudaMemcpyAsync(sg.p, o, sg.bytes, cudaMemcpyHostToDevice, P->ws));
+    o += sg.bytes;
+  }
+  s = pi::leave(P, true);
+  if (s != MUFFIN_OK) return s;
+  s = upload_cube_const(P);
+  if (s != MUFFIN_OK) return s;
+  P->k_done = h.k_done;
   P->have_b = h.have_b; P->have_state = h.have_state; P->have_sure_state = h.have_sure_state;
   return MUFFIN_OK;
 }
@@ -785,68 +935,58 @@ muffin_status muffin_state_import(muffin_plan P, const void *host_buf, size_t by
 muffin_status muffin_op_gradient(muffin_plan P, const float *x, const float *dirty, float *g) {
   if (!P || !x || !g) return fail(MUFFIN_EINVAL, "NULL argument");
   muffin_status s = ensure_op_buffers(P);
+  if (s == MUFFIN_OK) s = pi::enter(P);
   if (s != MUFFIN_OK) return s;
   const float *bb = nullptr;
   if (dirty) {
     s = fetch(P, dirty, P->stage_a, P->NL);
+    if (s == MUFFIN_OK) s = adjoint_fp64(P, P->stage_a, P->hhat, P->Lt, P->w64a, P->w64b);
     if (s != MUFFIN_OK) return s;
-    s = adjoint_fp64(P, P->stage_a, P->w64a, P->w64b);
-    if (s != MUFFIN_OK) return s;
-    CK(c64_real_to_f32(P->w64a, P->op_b, 1.0 / ((double)P->n * P->n), P->NL, P->st));
+    CK(c64_real_to_f32(P->w64a, P->op_b, 1.0 / ((double)P->n * P->n), P->NL, P->ws));
     bb = P->op_b;
   }
   s = fetch(P, x, P->op_in, P->NL);
   if (s != MUFFIN_OK) return s;
-  CK(launch_gradient(P->op_in, P->op_out, bb, P->S, P->kspec, P->tw32, P->n, P->L, 1, P->st));
+  CK(launch_gradient(P->op_in, P->op_out, bb, P->S, P->kspec, P->tw32, P->n, P->Lt, 1, P->ws));
   s = store(P, P->op_out, g, P->NL);
   if (s != MUFFIN_OK) return s;
-  CK(cudaStreamSynchronize(P->st));
-  return MUFFIN_OK;
+  return pi::leave(P, true);
 }
 
 muffin_status muffin_op_analysis(muffin_plan P, const float *x, float *u) {
   if (!P || !x || !u) return fail(MUFFIN_EINVAL, "NULL argument");
   muffin_status s = ensure_op_buffers(P);
+  if (s == MUFFIN_OK) s = pi::enter(P);
+  if (s == MUFFIN_OK) s = fetch(P, x, P->op_in, P->NL);
   if (s != MUFFIN_OK) return s;
-  s = fetch(P, x, P->op_in, P->NL);
-  if (s != MUFFIN_OK) return s;
-  WaveArgs w = P->wave();
-  w.C = 1;
-  CK(wavelet_analysis_op(w, P->op_in, P->op_out, P->st));
+  CK(wavelet_analysis_op(P->wave(1), P->op_in, P->op_out, P->ws));
   s = store(P, P->op_out, u, P->NL * P->K);
   if (s != MUFFIN_OK) return s;
-  CK(cudaStreamSynchronize(P->st));
-  return MUFFIN_OK;
+  return pi::leave(P, true);
 }
 
 muffin_status muffin_op_synthesis(muffin_plan P, const float *u, float *x) {
   if (!P || !x || !u) return fail(MUFFIN_EINVAL, "NULL argument");
   muffin_status s = ensure_op_buffers(P);
+  if (s == MUFFIN_OK) s = pi::enter(P);
+  if (s == MUFFIN_OK) s = fetch(P, u, P->op_in, P->NL * P->K);
   if (s != MUFFIN_OK) return s;
-  s = fetch(P, u, P->op_in, P->NL * P->K);
-  if (s != MUFFIN_OK) return s;
-  WaveArgs w = P->wave();
-  w.C = 1;
-  CK(wavelet_synthesis_op(w, P->op_in, P->op_out, P->st));
+  CK(wavelet_synthesis_op(P->wave(1), P->op_in, P->op_out, P->ws));
   s = store(P, P->op_out, x, P->NL);
   if (s != MUFFIN_OK) return s;
-  CK(cudaStreamSynchronize(P->st));
-  return MUFFIN_OK;
+  return pi::leave(P, true);
 }
 
 muffin_status muffin_op_dct(muffin_plan P, const float *x, float *v, int32_t inverse) {
   if (!P || !x || !v) return fail(MUFFIN_EINVAL, "NULL argument");
   muffin_status s = ensure_op_buffers(P);
+  if (s == MUFFIN_OK) s = pi::enter(P);
+  if (s == MUFFIN_OK) s = fetch(P, x, P->op_in, P->NL);
   if (s != MUFFIN_OK) return s;
-  s = fetch(P, x, P->op_in, P->NL);
-  if (s != MUFFIN_OK) return s;
-  DctArgs d = P->dct();
-  d.C = 1;
-  CK(dct_op(d, P->op_in, P->op_out, inverse, P->st));
+  CK(dct_op(P->dct(1), P->op_in, P->op_out, inverse, P->ws));
   s = store(P, P->op_out, v, P->NL);
   if (s != MUFFIN_OK) return s;
-  CK(cudaStreamSynchronize(P->st));
-  return MUFFIN_OK;
+  return pi::leave(P, true);
 }
 
 }  // extern "C"

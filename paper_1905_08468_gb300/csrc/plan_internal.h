@@ -1,0 +1,142 @@
+// Plan object shared by the C ABI (plan.cu) and the request server (serve.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/muffin.h"
+#include "kernels.h"
+
+namespace muffin {
+
+muffin_status fail(muffin_status s, const char *fmt, ...);
+
+#define MUFFIN_CK(expr)                                                          \
+  do {                                                                           \
+    cudaError_t e_ = (expr);                                                     \
+    if (e_ != cudaSuccess)                                                       \
+      return ::muffin::fail(                                                     \
+          e_ == cudaErrorMemoryAllocation ? MUFFIN_ENOMEM : MUFFIN_ECUDA,        \
+          "%s: %s", #expr, cudaGetErrorString(e_));                              \
+  } while (0)
+
+bool is_device_ptr(const void *p);
+
+}  // namespace muffin
+
+// A plan holds B cubes ("slots") of L bands of n x n pixels, stored one
+// after the other along the band axis (Lt = B L bands in all), so every
+// spatial kernel runs over all of them in one launch and the spectral
+// kernel runs one pixel tile of one cube per CTA.
+struct muffin_plan_s {
+  muffin_params p{};
+  int n = 0, L = 0, K = 0, J = 0, Lp = 0, Cmax = 1, B = 1, Lt = 0;
+  size_t N = 0;      // pixels per band
+  size_t NLc = 0;    // voxels per cube
+  size_t NL = 0;     // voxels of all cubes
+  cudaStream_t st = nullptr;   // caller's stream
+  cudaStream_t ws = nullptr;   // plan's own work stream (graph capture)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<void *> allocs;
+  size_t bytes = 0;
+
+  double2 *hhat = nullptr, *w64a = nullptr, *w64b = nullptr;
+  float *kspec = nullptr;
+  float2 *tw32 = nullptr;
+  double2 *tw64 = nullptr;
+  float *chi = nullptr, *clo = nullptr, *cthi = nullptr, *ctlo = nullptr;
+  float *alpha = nullptr, *beta = nullptr;
+  muffin::DevScalars *sc = nullptr;   // [B]
+  double *cube_const = nullptr;       // [B][4] for the theta update
+  int *rec_count = nullptr;           // device counter of trace records
+  double *dred = nullptr;             // reduction scratch
+  double *wband = nullptr;            // [Lt]
+  double *records = nullptr;          // [max_records][B][7]
+  int max_records = 0;
+  float2 *S = nullptr;
+  float *llscr = nullptr;
+  size_t lvl_off[16] = {};
+  muffin::Group grp[2];
+  float *grp_x0[2] = {nullptr, nullptr};   // x buffer at allocation (graph parity)
+  float *b = nullptr, *bbar = nullptr, *htd = nullptr;
+  float *stage_a = nullptr, *stage_b = nullptr;
+  float *op_in = nullptr, *op_out = nullptr, *op_b = nullptr;
+
+  muffin::Prof prof;
+  bool profiling = false;
+  bool use_graphs = true;
+  cudaGraphExec_t gplain[2] = {nullptr, nullptr};
+  cudaGraphExec_t gsure[2] = {nullptr, nullptr};
+  int gsure_window = 0, gsure_reset = -1;
+  double gsure_eta[2] = {0, 0}, gsure_tmin = 0;
+
+  std::vector<double> lips, Asum, Amax2, Bsum, Bmax2, psc, mu, gamma;
+  bool have_b = false, have_state = false, have_sure_state = false;
+  long long k_done = 0;
+
+  muffin::Prof *pp() { return profiling ? &prof : nullptr; }
+
+  template <typename T>
+  cudaError_t alloc(T **ptr, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+    if (e != cudaSuccess) return e;
+    allocs.push_back(q);
+    bytes += count * sizeof(T) + 16;
+    *ptr = static_cast<T *>(q);
+    return cudaSuccess;
+  }
+
+  ~muffin_plan_s();
+
+  double lnorm2(int c, double m, double g) const {
+    if (p.step_rule == 0) return K * m * m * Bsum[c] + g * g * Asum[c];
+    return K * m * m * Bmax2[c] + g * g * Amax2[c];
+  }
+  double tau_for(int c, double m, double g) const {
+    return p.tau_safety / (0.5 * lips[c] + p.sigma * lnorm2(c, m, g));
+  }
+  muffin::WaveArgs wave(int C) {
+    muffin::WaveArgs w{};
+    w.n = n; w.L = Lt; w.Lc = L; w.K = K; w.J = J; w.C = C;
+    w.beta = beta; w.sc = sc; w.scratch = llscr;
+    for (int j = 0; j < 16; ++j) w.lvl_off[j] = lvl_off[j];
+    w.prof = pp();
+    return w;
+  }
+  muffin::DctArgs dct(int C) {
+    muffin::DctArgs d{};
+    d.n = n; d.L = L; d.Lp = Lp; d.C = C; d.B = B;
+    d.chi = chi; d.clo = clo; d.cthi = cthi; d.ctlo = ctlo;
+    d.alpha = alpha; d.sc = sc;
+    d.prof = pp();
+    return d;
+  }
+};
+
+namespace muffin {
+namespace pi {
+
+// creation; psf may be NULL (slots loaded later with load_psf)
+muffin_status create(const muffin_params *p, const float *psf, const float *alpha,
+                     const float *beta, void *stream, muffin_plan *out);
+// PSF spectra, |h_hat|^2 / n^2 and beta of cubes [b0, b1); psf holds b1-b0 cubes
+muffin_status load_psf(muffin_plan P, int b0, int b1, const float *psf);
+// b = H^T y for cubes [b0, b1) (FP64); dirty holds b1-b0 cubes
+muffin_status load_dirty(muffin_plan P, int b0, int b1, const float *dirty);
+// group g: cubes [b0, b1) restart from X0 (device, b1-b0 cubes; NULL = 0), U = V = T = 0
+muffin_status reset_cubes(muffin_plan P, int g, int b0, int b1, const float *x0_dev);
+// (mu, gamma) of cubes [b0, b1) and their tau (host arrays of b1-b0 values)
+muffin_status set_theta(muffin_plan P, int b0, int b1, const double *mu, const double *gamma);
+// `iters` plain iterations of group 0 (all cubes), on the work stream
+muffin_status run_plain(muffin_plan P, int iters);
+// copy X of cubes [b0, b1) of group 0 to dst (host or device)
+muffin_status fetch_x(muffin_plan P, int b0, int b1, float *dst);
+// order the work stream after the caller's stream / the caller's after it
+muffin_status enter(muffin_plan P);
+muffin_status leave(muffin_plan P, bool sync);
+
+}  // namespace pi
+}  // namespace muffin

@@ -145,33 +145,39 @@ __global__ void k_sure_stats(SureStatsArgs a, double *__restrict__ part) {
   }
 }
 
+// one block per cube: cube b's partials are bands [b L, (b+1) L) x bpb
 __global__ void k_theta_update(ThetaUpdateArgs a) {
+  const int b = blockIdx.x;
+  const double *part = a.partials + (size_t)b * a.nb_per_cube * 6;
   double v[6] = {0, 0, 0, 0, 0, 0};
-  for (int i = threadIdx.x; i < a.nblocks; i += blockDim.x)
-    for (int q = 0; q < 6; ++q) v[q] += a.partials[6 * (size_t)i + q];
+  for (int i = threadIdx.x; i < a.nb_per_cube; i += blockDim.x)
+    for (int q = 0; q < 6; ++q) v[q] += part[6 * (size_t)i + q];
   __shared__ double sh[32 * 6];
   block_sum<6>(v, sh);
   if (threadIdx.x == 0) {
-    DevScalars *sc = a.sc;
+    DevScalars *sc = a.sc + b;
+    const double *cc = a.cube_const + 4 * b;   // psure_const, lipschitz, Bsum, Asum
+    double *rec = a.record + ((size_t)(*a.rec_count) * a.B + b) * 7;
     const double mu = sc->mu, gamma = sc->gamma;
     const double sug_mu = 2.0 * v[0] + v[2];
     const double sug_ga = 2.0 * v[1] + v[3];
-    const double psure = a.psure_const + v[4] + v[5];
-    a.record[0] = (double)a.k;
-    a.record[1] = mu;
-    a.record[2] = gamma;
-    a.record[3] = sug_mu;
-    a.record[4] = sug_ga;
-    a.record[5] = psure;
-    a.record[6] = sc->tau;
+    const double psure = cc[0] + v[4] + v[5];
+    rec[0] = 0.0;
+    rec[1] = mu;
+    rec[2] = gamma;
+    rec[3] = sug_mu;
+    rec[4] = sug_ga;
+    rec[5] = psure;
+    rec[6] = sc->tau;
     const double nmu = fmax(mu - a.eta_mu * sug_mu, a.theta_min);
     const double nga = fmax(gamma - a.eta_gamma * sug_ga, a.theta_min);
     sc->mu = nmu;
     sc->gamma = nga;
-    sc->tau = a.safety / (0.5 * a.lipschitz +
-                          sc->sigma * (a.K * nmu * nmu * a.Bsum + nga * nga * a.Asum));
+    sc->tau = a.safety / (0.5 * cc[1] + sc->sigma * (a.K * nmu * nmu * cc[2] + nga * nga * cc[3]));
   }
 }
+
+__global__ void k_bump(int *counter) { *counter += 1; }
 
 }  // namespace
 
@@ -211,12 +217,13 @@ cudaError_t sure_stats(const SureStatsArgs &a, double *partials, int *nblocks,
   // keep total partial count bounded: L * bpb <= 4096
   while (bpb > 1 && (size_t)a.L * bpb > 4096) bpb >>= 1;
   k_sure_stats<<<dim3(bpb, a.L), kRedThreads, 0, st>>>(a, partials);
-  *nblocks = bpb * a.L;
+  *nblocks = bpb;
   return cudaGetLastError();
 }
 
 cudaError_t theta_update(const ThetaUpdateArgs &a, cudaStream_t st) {
-  k_theta_update<<<1, kRedThreads, 0, st>>>(a);
+  k_theta_update<<<a.B, kRedThreads, 0, st>>>(a);
+  k_bump<<<1, 1, 0, st>>>(a.rec_count);
   return cudaGetLastError();
 }
 

@@ -59,6 +59,7 @@ constexpr size_t syn_smem(int) {
 
 struct AnaArgs {
   int n, M, L, K, last;
+  int Lc;                       // bands per cube (per-cube scalars sc[l / Lc])
   const float *in;              // level >= 2: LL_{j-1}; level-1 operator: x
   const float *xt, *x;          // level-1 iteration inputs
   float *ll_out;                // LL_j scratch when !last
@@ -69,6 +70,7 @@ struct AnaArgs {
 
 struct SynArgs {
   int n, M, L, K, top, positivity;   // M: output side of this level
+  int Lc;                            // bands per cube (per-cube scalars sc[l / Lc])
   const float *ll_in;                // LL_j scratch when !top
   const float *u;
   float *ll_out;                     // LL_{j-1} scratch (levels >= 2)
@@ -250,8 +252,9 @@ __global__ void __launch_bounds__(NT, 3) k_ana(AnaArgs a) {
   const size_t CS = (size_t)a.L * NN;   // channel stride of images
   float mu = 0.f, sbl = 1.f;
   if (MODE == WAVE_ITERATE) {
-    mu = (float)a.sc->mu;
-    sbl = (float)(a.sc->sigma * (double)a.beta[l]);
+    const DevScalars &S = a.sc[l / a.Lc];
+    mu = (float)S.mu;
+    sbl = (float)(S.sigma * (double)a.beta[l]);
   }
   for (int it = threadIdx.x; it < RH * RW; it += NT) {
     const int r = it / RW, cc = it - r * RW;
@@ -443,7 +446,7 @@ __global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
   const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
   const int l = LEVEL1 ? blockIdx.y : blockIdx.y / a.K;
   const int b = LEVEL1 ? 0 : blockIdx.y % a.K;
-  const float mu = (MODE == WAVE_ITERATE) ? (float)a.sc->mu : 0.f;
+  const float mu = (MODE == WAVE_ITERATE) ? (float)a.sc[l / a.Lc].mu : 0.f;
   const int sx = threadIdx.x % (TX / QXP), my = threadIdx.x / (TX / QXP);
   const int yy = 2 * ky0 + my, xx0 = 2 * kx0 + 2 * QXP * sx;
   float acc[CH][2 * QXP];
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
       if (xx0 + e < a.n) a.out[row + xx0 + e] = acc[0][e];
     return;
   }
-  const float tau = (float)a.sc->tau;
+  const float tau = (float)a.sc[l / a.Lc].tau;
   const float bl = a.beta[l];
   const size_t CS = (size_t)a.L * NN;
   if (xx0 >= a.n) return;
@@ -566,7 +569,7 @@ __global__ void k_syn0(SynArgs a) {
     float acc[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) acc[c] = 0.f;
-    const float mu = (MODE == WAVE_ITERATE) ? (float)a.sc->mu : 0.f;
+    const float mu = (MODE == WAVE_ITERATE) ? (float)a.sc[l / a.Lc].mu : 0.f;
     for (int bb = 0; bb < a.K; ++bb) {
       const float *u0 = a.u + ((size_t)l * a.K + bb) * NN + pix;
       float v[CH];
@@ -577,7 +580,7 @@ __global__ void k_syn0(SynArgs a) {
       for (int c = 0; c < CH; ++c) acc[c] += v[c];
     }
     if (MODE == WAVE_TRANSFORM) { a.out[i] = acc[0]; continue; }
-    const float tau = (float)a.sc->tau, bl = a.beta[l];
+    const float tau = (float)a.sc[l / a.Lc].tau, bl = a.beta[l];
     float sc[CH];
     sc[0] = bl * mu;
     if (CH == 3) { sc[1] = bl; sc[2] = bl * mu; }
@@ -605,8 +608,8 @@ __global__ void k_ana0(AnaArgs a) {
     if (MODE == WAVE_TRANSFORM) {
       w[0] = a.in[i]; q[0] = 1.f;
     } else {
-      const float mu = (float)a.sc->mu;
-      const float sb = (float)(a.sc->sigma * (double)a.beta[l]);
+      const float mu = (float)a.sc[l / a.Lc].mu;
+      const float sb = (float)(a.sc[l / a.Lc].sigma * (double)a.beta[l]);
       float z[CH];
 #pragma unroll
       for (int c = 0; c < CH; ++c) z[c] = 2.f * a.xt[i + c * CS] - a.x[i + c * CS];
@@ -734,6 +737,7 @@ cudaError_t wavelet_synthesis_prox(const WaveArgs &w, const Group &gr,
                                    int positivity, cudaStream_t st) {
   SynArgs a{};
   a.n = w.n; a.L = w.L; a.K = w.K; a.positivity = positivity;
+  a.Lc = w.Lc > 0 ? w.Lc : w.L;
   a.u = gr.u; a.x = gr.x; a.g = gr.g; a.t = gr.t; a.xt = gr.xt;
   a.beta = w.beta; a.sc = w.sc;
   if (gr.C == 3) return synthesis_all<3, WAVE_ITERATE>(w, a, st);
@@ -744,6 +748,7 @@ cudaError_t wavelet_analysis_dual(const WaveArgs &w, const Group &gr,
                                   cudaStream_t st) {
   AnaArgs a{};
   a.n = w.n; a.L = w.L; a.K = w.K;
+  a.Lc = w.Lc > 0 ? w.Lc : w.L;
   a.xt = gr.xt; a.x = gr.x; a.u = gr.u; a.beta = w.beta; a.sc = w.sc;
   if (gr.C == 3) return analysis_all<3, WAVE_ITERATE>(w, a, st);
   return analysis_all<1, WAVE_ITERATE>(w, a, st);
@@ -752,14 +757,14 @@ cudaError_t wavelet_analysis_dual(const WaveArgs &w, const Group &gr,
 cudaError_t wavelet_analysis_op(const WaveArgs &w, const float *x, float *u,
                                 cudaStream_t st) {
   AnaArgs a{};
-  a.n = w.n; a.L = w.L; a.K = w.K; a.in = x; a.u = u;
+  a.n = w.n; a.L = w.L; a.K = w.K; a.Lc = w.L; a.in = x; a.u = u;
   return analysis_all<1, WAVE_TRANSFORM>(w, a, st);
 }
 
 cudaError_t wavelet_synthesis_op(const WaveArgs &w, const float *u, float *x,
                                  cudaStream_t st) {
   SynArgs a{};
-  a.n = w.n; a.L = w.L; a.K = w.K; a.u = u; a.out = x;
+  a.n = w.n; a.L = w.L; a.K = w.K; a.Lc = w.L; a.u = u; a.out = x;
   return synthesis_all<1, WAVE_TRANSFORM>(w, a, st);
 }
 

@@ -16,7 +16,8 @@ c_size_t = ctypes.c_size_t
 class Params(ctypes.Structure):
     _fields_ = [("n", c_int32), ("nbands", c_int32), ("n_wavelets", c_int32),
                 ("levels", c_int32), ("sigma", c_double), ("step_rule", c_int32),
-                ("tau_safety", c_double), ("positivity", c_int32), ("sure", c_int32)]
+                ("tau_safety", c_double), ("positivity", c_int32), ("sure", c_int32),
+                ("batch", c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -57,6 +58,10 @@ SIGNATURES = {
     "muffin_plan_lipschitz": (c_int32, [c_void_p, ctypes.POINTER(c_double)]),
     "muffin_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_double,
                                c_double, c_int32, ctypes.POINTER(Info)]),
+    "muffin_solve_batch": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32,
+                                     ctypes.POINTER(c_double), ctypes.POINTER(c_double),
+                                     c_int32, ctypes.POINTER(Info)]),
+    "muffin_plan_graphs": (c_int32, [c_void_p, c_int32]),
     "muffin_sure_params_default": (None, [ctypes.POINTER(SureParams)]),
     "muffin_sure_tune": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p,
                                    ctypes.POINTER(SureParams), c_void_p,
