@@ -223,6 +223,107 @@ def captured_traffic(kernel: str, chain_voxels: float):
     return per_voxel * chain_voxels
 
 
+# ------------------------------------------------------------------ serving
+def nearest_rank(vals, q):
+    v = sorted(vals)
+    return v[max(0, math.ceil(q * len(v)) - 1)]
+
+
+def serve_cube(n, L, seed):
+    from synth import make_cube
+    r = (n / 256.0) ** 2      # densities per pixel of the 256^2 x 32 workload
+    return make_cube(n, L, max(1, round(200 * r)), max(1, round(20 * r)),
+                     max(100, round(20000 * r)), seed, with_delta=False)
+
+
+def run_serve(args) -> None:
+    """Served Poisson stream: continuous batching (muffin_server) against the
+    same stream served one cube per launch, first come first served, no
+    graphs.  Latency = result ready - arrival."""
+    import numpy as np
+    import torch
+    from synth import serve_stream
+    import paper_1905_08468_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    stream = serve_stream(seed=4)[: args.serve_requests]
+    if args.serve_rate != 4.0:          # same draws, arrivals rescaled (0: one burst)
+        k = 0.0 if args.serve_rate <= 0 else 4.0 / args.serve_rate
+        stream = [(t * k, n, L, sd) for t, n, L, sd in stream]
+    cubes = [serve_cube(n, L, seed) for _, n, L, seed in stream]
+    iters, mu = args.serve_iters, 1e-2
+
+    def replay(run_one):
+        lat, t0 = [], time.perf_counter()
+        run_one(t0, lat)
+        make = time.perf_counter() - t0
+        vox = sum(c.voxels for c in cubes) * iters
+        return lat, make, vox / make
+
+    outs_b = {}
+
+    def batched(t0, lat):
+        with pkg.Server(max_batch=args.serve_batch, chunk=10) as srv:
+            nxt, tick, arr = 0, {}, {}
+            while len(lat) < len(stream):
+                now = time.perf_counter() - t0
+                while nxt < len(stream) and stream[nxt][0] <= now:
+                    c = cubes[nxt]
+                    t = srv.submit(c.psf, c.dirty, mu, mu, iters)
+                    tick[t], arr[t] = nxt, stream[nxt][0]
+                    nxt += 1
+                active, queued = srv.step()
+                for t in list(tick):
+                    c = cubes[tick[t]]
+                    out = np.empty((c.L, c.n, c.n), np.float32)
+                    if srv.poll(t, out):
+                        lat.append(time.perf_counter() - t0 - arr[t])
+                        outs_b[tick[t]] = out
+                        del tick[t]
+                if active == 0 and queued == 0 and nxt < len(stream):
+                    time.sleep(max(0.0, stream[nxt][0] - (time.perf_counter() - t0)))
+
+    outs_1 = {}
+
+    def one_by_one(t0, lat):
+        plans = {}
+        for i, (arr, n, L, _) in enumerate(stream):
+            wait = arr - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            c = cubes[i]
+            if (n, L) not in plans:
+                plans[(n, L)] = pkg.Plan(n, L, c.psf)
+                plans[(n, L)].graphs(False)
+            p = plans[(n, L)]
+            p.load_psf(c.psf)
+            x = np.zeros((L, n, n), np.float32)
+            p.solve(c.dirty, x, iters, mu, mu)
+            lat.append(time.perf_counter() - t0 - arr)
+            outs_1[i] = x
+        for p in plans.values():
+            p.close()
+
+    lb, mb, tb = replay(batched)
+    l1, m1, t1 = replay(one_by_one)
+    same = all(np.array_equal(outs_b[i], outs_1[i]) for i in range(len(stream)))
+    rate = "burst" if args.serve_rate <= 0 else f"{args.serve_rate:g}/s"
+    out = {"metric": f"served stream: p50/p99 latency and throughput ({len(stream)} Poisson requests, {rate})",
+           "value": tb, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+           "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+           "config": {"workload": "served Poisson stream, n in {128,256,512}, "
+                                  "L in {16,32,64}", "requests": len(stream),
+                      "iters": iters, "mu": mu, "gamma": mu, "max_batch": args.serve_batch,
+                      "chunk": 10},
+           "batched": {"p50_s": nearest_rank(lb, 0.5), "p99_s": nearest_rank(lb, 0.99),
+                       "makespan_s": mb, "voxel_iters_per_s": tb},
+           "one_cube_per_launch": {"p50_s": nearest_rank(l1, 0.5),
+                                   "p99_s": nearest_rank(l1, 0.99),
+                                   "makespan_s": m1, "voxel_iters_per_s": t1},
+           "results_identical": same}
+    print(json.dumps(out), flush=True)
+
+
 def measured_peak_gbs():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -243,11 +344,21 @@ def main() -> None:
     ap.add_argument("--window", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="served Poisson stream (continuous batching vs one cube per launch)")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-iters", type=int, default=300)
+    ap.add_argument("--serve-batch", type=int, default=8)
+    ap.add_argument("--serve-rate", type=float, default=4.0,
+                    help="mean arrivals per second (0: all requests at once)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.serve:
+        run_serve(args)
         return
 
     import numpy as np

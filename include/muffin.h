@@ -107,6 +107,16 @@ MUFFIN_API size_t muffin_plan_device_bytes(muffin_plan plan);
 /* beta[b] = max_l ||H_l||^2 of cube b (FP64), b < B. */
 MUFFIN_API muffin_status muffin_plan_lipschitz(muffin_plan plan, double *beta);
 
+/* Device bytes muffin_plan_create would allocate for p (the footprint used
+ * for admission by the request server).  Errors: EINVAL for invalid p. */
+MUFFIN_API muffin_status muffin_plan_estimate_bytes(const muffin_params *p,
+                                                    size_t *bytes);
+
+/* Replace the PSFs of cubes [b0, b1): psf [b1-b0][L][n][n] (host or device);
+ * recomputes their spectra and beta (the state is kept). */
+MUFFIN_API muffin_status muffin_plan_load_psf(muffin_plan plan, int32_t b0,
+                                              int32_t b1, const float *psf);
+
 /* on = 1 (default): repeated launch sequences (two plain iterations, one
  * ADA-PT window) are captured once into CUDA graphs and replayed; 0 launches
  * every kernel directly.  Results are identical either way. */
@@ -217,6 +227,59 @@ MUFFIN_API muffin_status muffin_op_synthesis(muffin_plan plan, const float *u, f
  * C the orthonormal DCT-II (3xTF32 tensor-core products). */
 MUFFIN_API muffin_status muffin_op_dct(muffin_plan plan, const float *x, float *v,
                             int32_t inverse);
+
+/* ---- request server (continuous batching) --------------------------------
+ * Deconvolution requests of any shape (n, L) with fixed (mu, gamma) are
+ * queued, admitted in arrival order into free slots of batched plans ("pools",
+ * one per shape) while the active work stays under max_active_voxels and the
+ * pools' device footprint fits the HBM budget, advanced together
+ * in shared launches a few iterations per scheduling step, and retired as
+ * soon as their own iteration count is reached; freed slots take the next
+ * request at the following step.  A request's result does not depend on the
+ * other requests in its pool.  The caller drives the loop (submit as
+ * requests arrive, step, poll).  Not thread-safe: one thread per server. */
+typedef struct muffin_server_s *muffin_server;
+
+typedef struct {
+  size_t hbm_budget_bytes; /* device bytes the pools may hold; 0 = 80 % of the
+                              free device memory at creation */
+  int32_t max_batch;       /* slots per pool (default 8) */
+  int32_t n_wavelets;      /* K (default 8) */
+  int32_t levels;          /* J (default 3) */
+  double sigma;            /* dual step (default 10) */
+  int32_t step_rule;       /* as muffin_params (default 0) */
+  double tau_safety;       /* default 0.99 */
+  int32_t chunk;           /* iterations per scheduling step (default 10) */
+  size_t max_active_voxels;/* admission stops (in arrival order) once the
+                              requests in slots hold this many voxels; one
+                              request is always admitted (default 3 * 2^24) */
+} muffin_server_params;
+
+MUFFIN_API void muffin_server_params_default(muffin_server_params *p);
+/* stream: cudaStream_t the server's work is ordered after (NULL = legacy). */
+MUFFIN_API muffin_status muffin_server_create(const muffin_server_params *p,
+                                              void *stream, muffin_server *out);
+MUFFIN_API void muffin_server_destroy(muffin_server s);
+/* Queue a request: psf and dirty [L][n][n] (host or device, copied now),
+ * Algorithm 2 with fixed (mu, gamma) from X0 = 0 for `iters` iterations.
+ * Errors: EINVAL (shape), ENOMEM (one pool of this shape exceeds the budget). */
+MUFFIN_API muffin_status muffin_serve_submit(muffin_server s, int32_t n,
+                                             int32_t nbands, const float *psf,
+                                             const float *dirty, double mu,
+                                             double gamma, int32_t iters,
+                                             uint64_t *ticket);
+/* One scheduling step: admit, advance every pool by up to `chunk`
+ * iterations, retire finished requests.  Synchronous.  *active / *queued
+ * (nullable) report the requests in slots and still waiting. */
+MUFFIN_API muffin_status muffin_serve_step(muffin_server s, int32_t *active,
+                                           int32_t *queued);
+/* *done = 1 once the request has finished; then, if x_out != NULL, its cube
+ * [L][n][n] is copied to x_out (host or device) and the ticket is released. */
+MUFFIN_API muffin_status muffin_serve_poll(muffin_server s, uint64_t ticket,
+                                           int32_t *done, float *x_out);
+/* Device bytes held by the pools and their number (nullable outputs). */
+MUFFIN_API muffin_status muffin_server_stats(muffin_server s, size_t *device_bytes,
+                                             int32_t *pools);
 
 /* ---- allocation-free operator ------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

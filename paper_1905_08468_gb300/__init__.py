@@ -15,7 +15,8 @@ import numpy as np
 from . import native
 from .native import MUFFIN_WARM, MuffinError, SureRecord
 
-__all__ = ["Plan", "MuffinError", "filter_taps", "dct_table", "library"]
+__all__ = ["Plan", "Server", "MuffinError", "filter_taps", "dct_table", "library",
+           "estimate_bytes"]
 
 
 def library():
@@ -119,6 +120,12 @@ class Plan:
         native.check(self._lib.muffin_plan_lipschitz(self._h, b))
         return b[0] if self.B == 1 else list(b)
 
+    def load_psf(self, psf, b0: int = 0, b1: int = None) -> None:
+        """Replace the PSFs of cubes [b0, b1) (state kept)."""
+        keep = []
+        b1 = self.B if b1 is None else b1
+        native.check(self._lib.muffin_plan_load_psf(self._h, int(b0), int(b1), _ptr(psf, keep)))
+
     def graphs(self, on: bool = True) -> None:
         native.check(self._lib.muffin_plan_graphs(self._h, int(on)))
 
@@ -218,3 +225,77 @@ class Plan:
         keep = []
         native.check(self._lib.muffin_op_dct(self._h, _ptr(x, keep), _ptr(v, keep),
                                              int(inverse)))
+
+
+def estimate_bytes(n: int, nbands: int, *, n_wavelets: int = 8, levels: int = 3,
+                   sure: bool = False, batch: int = 1) -> int:
+    """Device bytes a plan of this shape allocates."""
+    lib = library()
+    p = native.Params()
+    lib.muffin_params_default(ctypes.byref(p), n, nbands)
+    p.n_wavelets, p.levels, p.sure, p.batch = n_wavelets, levels, int(sure), batch
+    out = ctypes.c_size_t()
+    native.check(lib.muffin_plan_estimate_bytes(ctypes.byref(p), ctypes.byref(out)))
+    return int(out.value)
+
+
+class Server:
+    """Continuous-batching request server (see ``muffin_server_create``)."""
+
+    def __init__(self, *, hbm_budget_bytes: int = 0, max_batch: int = 8,
+                 n_wavelets: int = 8, levels: int = 3, sigma: float = 10.0,
+                 chunk: int = 10, max_active_voxels: int = 0, stream=None):
+        lib = library()
+        self._lib = lib
+        p = native.ServerParams()
+        lib.muffin_server_params_default(ctypes.byref(p))
+        p.hbm_budget_bytes, p.max_batch, p.chunk = int(hbm_budget_bytes), int(max_batch), int(chunk)
+        p.n_wavelets, p.levels, p.sigma = n_wavelets, levels, sigma
+        if max_active_voxels:
+            p.max_active_voxels = int(max_active_voxels)
+        h = ctypes.c_void_p()
+        st = stream if stream is not None else _stream_handle()
+        native.check(lib.muffin_server_create(ctypes.byref(p), st, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.muffin_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, psf, dirty, mu: float, gamma: float, iters: int) -> int:
+        keep = []
+        L, n = int(np.shape(dirty)[-3]), int(np.shape(dirty)[-1])
+        t = ctypes.c_uint64()
+        native.check(self._lib.muffin_serve_submit(
+            self._h, n, L, _ptr(psf, keep), _ptr(dirty, keep), float(mu), float(gamma),
+            int(iters), ctypes.byref(t)))
+        return int(t.value)
+
+    def step(self):
+        a, q = ctypes.c_int32(), ctypes.c_int32()
+        native.check(self._lib.muffin_serve_step(self._h, ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, ticket: int, out=None) -> bool:
+        keep, d = [], ctypes.c_int32()
+        native.check(self._lib.muffin_serve_poll(self._h, ctypes.c_uint64(ticket),
+                                                 ctypes.byref(d), _ptr(out, keep)))
+        return bool(d.value)
+
+    def stats(self):
+        b, p = ctypes.c_size_t(), ctypes.c_int32()
+        native.check(self._lib.muffin_server_stats(self._h, ctypes.byref(b), ctypes.byref(p)))
+        return int(b.value), int(p.value)

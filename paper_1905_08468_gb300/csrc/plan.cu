@@ -83,10 +83,9 @@ bool is_device_ptr(const void *p) {
 }  // namespace muffin
 
 muffin_plan_s::~muffin_plan_s() {
-  for (int i = 0; i < 2; ++i) {
-    if (gplain[i]) cudaGraphExecDestroy(gplain[i]);
+  for (auto &kv : gplain) cudaGraphExecDestroy(kv.second);
+  for (int i = 0; i < 2; ++i)
     if (gsure[i]) cudaGraphExecDestroy(gsure[i]);
-  }
   for (void *q : allocs) cudaFree(q);
   if (ev_in) cudaEventDestroy(ev_in);
   if (ev_out) cudaEventDestroy(ev_out);
@@ -146,13 +145,19 @@ muffin_status adjoint_fp64(muffin_plan P, const float *y_dev, const double2 *hh,
   return MUFFIN_OK;
 }
 
-muffin_status iterate_group(muffin_plan P, Group &g) {
-  CK(launch_gradient(g.x, g.g, g.b, P->S, P->kspec, P->tw32, P->n, P->Lt, g.C, P->ws,
+// one iteration of group g; nc < B restricts a plain group (C = 1) to the
+// first nc cubes (the serving pools skip their free slots)
+muffin_status iterate_group(muffin_plan P, Group &g, int nc = -1) {
+  if (nc < 0) nc = P->B;
+  const int Lv = nc * P->L;
+  CK(launch_gradient(g.x, g.g, g.b, P->S, P->kspec, P->tw32, P->n, Lv, g.C, P->ws,
                      P->pp()));
   WaveArgs w = P->wave(g.C);
+  w.L = Lv;
   CK(wavelet_synthesis_prox(w, g, P->p.positivity, P->ws));
   CK(wavelet_analysis_dual(w, g, P->ws));
   DctArgs d = P->dct(g.C);
+  d.B = nc;
   CK(dct_dual(d, g, P->ws));
   float *t = g.x; g.x = g.xt; g.xt = t;
   return MUFFIN_OK;
@@ -455,29 +460,34 @@ muffin_status set_theta(muffin_plan P, int b0, int b1, const double *mu, const d
   return MUFFIN_OK;
 }
 
-muffin_status run_plain(muffin_plan P, int iters) {
+muffin_status run_plain(muffin_plan P, int iters, int ncubes) {
   Group &g = P->grp[0];
   Group plain = g;
   plain.C = 1;
+  const int nc = ncubes < 0 || ncubes > P->B ? P->B : ncubes;
   muffin_status s = MUFFIN_OK;
   const bool graphs = P->use_graphs && !P->profiling;
   int k = 0;
   while (k < iters) {
     const int par = plain.x == P->grp_x0[0] ? 0 : 1;
-    if (graphs && iters - k >= 2 && P->gplain[par] == nullptr && k > 0) {
+    const std::pair<int, int> key(par, nc);
+    auto it = P->gplain.find(key);
+    if (graphs && iters - k >= 2 && it == P->gplain.end() && k > 0) {
       Group cap = plain;
-      s = capture(P, &P->gplain[par], [&]() -> muffin_status {
-        muffin_status r = iterate_group(P, cap);
-        if (r == MUFFIN_OK) r = iterate_group(P, cap);
+      cudaGraphExec_t ex = nullptr;
+      s = capture(P, &ex, [&]() -> muffin_status {
+        muffin_status r = iterate_group(P, cap, nc);
+        if (r == MUFFIN_OK) r = iterate_group(P, cap, nc);
         return r;
       });
       if (s != MUFFIN_OK) return s;
+      it = P->gplain.emplace(key, ex).first;
     }
-    if (graphs && iters - k >= 2 && P->gplain[par] != nullptr) {
-      CK(cudaGraphLaunch(P->gplain[par], P->ws));
+    if (graphs && iters - k >= 2 && it != P->gplain.end()) {
+      CK(cudaGraphLaunch(it->second, P->ws));
       k += 2;      // two swaps: pointers unchanged
     } else {
-      s = iterate_group(P, plain);
+      s = iterate_group(P, plain, nc);
       if (s != MUFFIN_OK) return s;
       ++k;
     }
@@ -488,6 +498,22 @@ muffin_status run_plain(muffin_plan P, int iters) {
 
 muffin_status fetch_x(muffin_plan P, int b0, int b1, float *dst) {
   return store(P, P->grp[0].x + (size_t)b0 * P->NLc, dst, (size_t)(b1 - b0) * P->NLc);
+}
+
+size_t estimate_bytes(const muffin_params *p) {
+  // mirrors plan_alloc_init (each allocation carries 16 bytes of slack)
+  const size_t n = p->n, L = p->nbands, B = p->batch, Lt = B * L, K = p->n_wavelets;
+  const size_t N = n * n, NL = N * Lt, nh = n / 2 + 1, C = p->sure ? 3 : 1;
+  const size_t Lp = (L + 15) / 16 * 16;
+  size_t ll = 0;
+  for (int j = 1; j < p->levels; ++j) ll += C * Lt * K * (n >> j) * (n >> j);
+  size_t b = 3 * NL * 16 + Lt * nh * n * 4 + (size_t)fft32_table_len((int)n) * 8 + n * 16 +
+             4 * Lp * Lp * 4 + B * N * 4 + Lt * 4 + B * sizeof(DevScalars) + B * 32 + 4 +
+             (kRedSure + 65 * Lt + 6 * (Lt > 4096 ? Lt : 4096)) * 8 + Lt * 8 +
+             C * Lt * nh * n * 8 + (ll ? ll : 1) * 4 + 3 * NL * 4 +
+             C * NL * (5 + K) * 4;
+  if (p->sure) b += 3 * NL * (5 + K) * 4 + 2 * NL * 4;
+  return b + (p->sure ? 36 : 28) * 16;   // 16 bytes of slack per allocation
 }
 
 muffin_status create(const muffin_params *p, const float *psf, const float *alpha,
@@ -585,6 +611,24 @@ muffin_status muffin_plan_lipschitz(muffin_plan P, double *beta) {
   return MUFFIN_OK;
 }
 
+muffin_status muffin_plan_estimate_bytes(const muffin_params *p, size_t *bytes) {
+  if (!bytes) return fail(MUFFIN_EINVAL, "bytes is NULL");
+  muffin_status s = validate(p);
+  if (s != MUFFIN_OK) return s;
+  *bytes = pi::estimate_bytes(p);
+  return MUFFIN_OK;
+}
+
+muffin_status muffin_plan_load_psf(muffin_plan P, int32_t b0, int32_t b1, const float *psf) {
+  if (!P || !psf) return fail(MUFFIN_EINVAL, "NULL argument");
+  if (b0 < 0 || b1 > P->B || b0 >= b1) return fail(MUFFIN_EINVAL, "cube range [%d, %d) invalid", b0, b1);
+  muffin_status s = pi::enter(P);
+  if (s == MUFFIN_OK) s = pi::load_psf(P, b0, b1, psf);
+  if (s == MUFFIN_OK) s = upload_cube_const(P);
+  if (s == MUFFIN_OK) s = pi::leave(P, true);
+  return s;
+}
+
 muffin_status muffin_plan_graphs(muffin_plan P, int32_t on) {
   if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
   P->use_graphs = on != 0;
@@ -619,7 +663,7 @@ muffin_status muffin_solve_batch(muffin_plan P, const float *dirty, float *x,
   if (s != MUFFIN_OK) return s;
   P->have_state = true;
   P->have_sure_state = false;
-  s = pi::run_plain(P, iters);
+  s = pi::run_plain(P, iters, P->B);
   if (s != MUFFIN_OK) return s;
   s = pi::fetch_x(P, 0, P->B, x);
   if (s != MUFFIN_OK) return s;

@@ -3,7 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/muffin.h"
@@ -67,7 +69,7 @@ struct muffin_plan_s {
   muffin::Prof prof;
   bool profiling = false;
   bool use_graphs = true;
-  cudaGraphExec_t gplain[2] = {nullptr, nullptr};
+  std::map<std::pair<int, int>, cudaGraphExec_t> gplain;   // (parity, cubes)
   cudaGraphExec_t gsure[2] = {nullptr, nullptr};
   int gsure_window = 0, gsure_reset = -1;
   double gsure_eta[2] = {0, 0}, gsure_tmin = 0;
@@ -119,6 +121,8 @@ struct muffin_plan_s {
 namespace muffin {
 namespace pi {
 
+// device bytes a plan with parameters p allocates (p valid)
+size_t estimate_bytes(const muffin_params *p);
 // creation; psf may be NULL (slots loaded later with load_psf)
 muffin_status create(const muffin_params *p, const float *psf, const float *alpha,
                      const float *beta, void *stream, muffin_plan *out);
@@ -130,8 +134,8 @@ muffin_status load_dirty(muffin_plan P, int b0, int b1, const float *dirty);
 muffin_status reset_cubes(muffin_plan P, int g, int b0, int b1, const float *x0_dev);
 // (mu, gamma) of cubes [b0, b1) and their tau (host arrays of b1-b0 values)
 muffin_status set_theta(muffin_plan P, int b0, int b1, const double *mu, const double *gamma);
-// `iters` plain iterations of group 0 (all cubes), on the work stream
-muffin_status run_plain(muffin_plan P, int iters);
+// `iters` plain iterations of group 0 on the first `ncubes` cubes (work stream)
+muffin_status run_plain(muffin_plan P, int iters, int ncubes);
 // copy X of cubes [b0, b1) of group 0 to dst (host or device)
 muffin_status fetch_x(muffin_plan P, int b0, int b1, float *dst);
 // order the work stream after the caller's stream / the caller's after it

@@ -38,6 +38,13 @@ class SureRecord(ctypes.Structure):
                 ("psure", c_double), ("tau", c_double)]
 
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", c_size_t), ("max_batch", c_int32),
+                ("n_wavelets", c_int32), ("levels", c_int32), ("sigma", c_double),
+                ("step_rule", c_int32), ("tau_safety", c_double), ("chunk", c_int32),
+                ("max_active_voxels", c_size_t)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64),
                 ("total_ms", c_double), ("bytes_per_launch", c_double),
@@ -74,6 +81,20 @@ SIGNATURES = {
     "muffin_op_analysis": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "muffin_op_synthesis": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "muffin_op_dct": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
+    "muffin_plan_estimate_bytes": (c_int32, [ctypes.POINTER(Params), ctypes.POINTER(c_size_t)]),
+    "muffin_plan_load_psf": (c_int32, [c_void_p, c_int32, c_int32, c_void_p]),
+    "muffin_server_params_default": (None, [ctypes.POINTER(ServerParams)]),
+    "muffin_server_create": (c_int32, [ctypes.POINTER(ServerParams), c_void_p,
+                                       ctypes.POINTER(c_void_p)]),
+    "muffin_server_destroy": (None, [c_void_p]),
+    "muffin_serve_submit": (c_int32, [c_void_p, c_int32, c_int32, c_void_p, c_void_p,
+                                      c_double, c_double, c_int32,
+                                      ctypes.POINTER(ctypes.c_uint64)]),
+    "muffin_serve_step": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32)]),
+    "muffin_serve_poll": (c_int32, [c_void_p, ctypes.c_uint64, ctypes.POINTER(c_int32),
+                                    c_void_p]),
+    "muffin_server_stats": (c_int32, [c_void_p, ctypes.POINTER(c_size_t),
+                                      ctypes.POINTER(c_int32)]),
     "muffin_op_analysis_noalloc": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_int32,
                                              c_int32, c_void_p]),
     "muffin_profile_enable": (c_int32, [c_void_p, c_int32]),
