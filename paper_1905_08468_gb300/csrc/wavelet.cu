@@ -11,12 +11,20 @@
 // One level per launch.  A CTA owns a tile of TY x TX coefficients of every
 // subband (2TY x 2TX pixels of the level's input) of one band; level 1 keeps
 // its input tile in shared memory and runs all K bases on it, so x~ and x are
-// read once for the 8 bases; coarser levels run one basis per CTA on the
-// approximation left in an LL scratch by the previous level.  Filters live in
-// constant memory and every pass keeps a sliding window of taps' inputs in
-// registers.  Periodic extension is a wrap of the tile's load indices, which
-// also covers levels smaller than a filter (the transform stays the exact
-// periodised one).
+// read once for the 8 bases; the analysis of coarser levels runs one basis
+// per CTA on the approximation left in an LL scratch by the previous level,
+// and every synthesis CTA walks all K bases of its tile (so its copy
+// pipeline stays full across the bases).  Periodic
+// extension is a wrap of the tile's load indices, which also covers levels
+// smaller than a filter (the transform stays the exact periodised one).
+//
+// The analysis filters run on packed pairs (fma.rn.f32x2): the row pass
+// filters two image rows at once (the tile is stored as row pairs) and the
+// column pass splits each output into its even- and odd-tap halves.  The
+// synthesis keeps scalar FMAs: a packed form needs each coefficient twice in
+// shared memory, and the doubled shared-memory traffic costs more than the
+// halved FMA issue saves.  Filters live in constant memory and every pass
+// keeps a sliding window of taps' inputs in registers.
 //
 // Chains: a launch advances C = 1 (plain) or C = 3 chains {x, dx/dmu,
 // dx/dgamma} of one ADA-PT group.  The derivative channels use the masks of
@@ -31,15 +39,22 @@
 
 namespace muffin {
 
+// filters of db1..db8 (taps beyond 2p are zero): h_i, g_i for the synthesis,
+// pairs (h_i, h_i), (g_i, g_i) and (h_2s, h_2s+1), (g_2s, g_2s+1) for the
+// analysis
 __constant__ float c_h[8][16];
 __constant__ float c_g[8][16];
+__constant__ float2 c_hh[8][16];
+__constant__ float2 c_gg[8][16];
+__constant__ float2 c_hp[8][8];
+__constant__ float2 c_gp[8][8];
 
 namespace {
 
 constexpr int TY = 16, TX = 32, PMAX = 8, NT = 256;
-// analysis tiles
-constexpr int A_RH = 2 * TY + 2 * PMAX - 2;          // input rows held
-constexpr int A_IP = (2 * TX + 2 * PMAX - 2) | 1;    // odd pitch: conflict-free rows
+// analysis tiles, in float2 row pairs (rows 2r, 2r+1 of the input)
+constexpr int A_RP = TY + PMAX - 1;                  // input row pairs held
+constexpr int A_IP = (2 * TX + 2 * PMAX - 2) | 1;    // odd pitch: conflict-free
 constexpr int A_LP = TX + 1;                         // row-pass output pitch
 constexpr int QX = 4, QY = 2;                        // outputs per thread
 // synthesis tiles: a fixed window of coefficients [k0 - 8, k0 + T) in both
@@ -51,10 +66,14 @@ constexpr int S_LP = (TX + PMAX - 1) | 1;            // column-pass output pitch
 constexpr int QXP = 4, QYP = 2;                      // coefficient pairs per thread
 
 constexpr size_t ana_smem(int ch) {
-  return ((size_t)ch * A_RH * A_IP + 2 * A_RH * A_LP) * sizeof(float);
+  return ((size_t)ch * A_RP * A_IP + 2 * A_RP * A_LP) * sizeof(float2);
 }
 constexpr size_t syn_smem(int) {
   return (size_t)(8 * S_CH * S_CP + 2 * (2 * TY) * S_LP) * sizeof(float);
+}
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  return __ffma2_rn(a, b, c);
 }
 
 struct AnaArgs {
@@ -110,87 +129,92 @@ __device__ __forceinline__ void ana_emit(const AnaArgs &a, int l, int bb,
 // The U values the item updates are loaded before the row pass so their
 // latency overlaps the filtering.  Channel 0 records the mask Pi(p) of each
 // output in `keep`; derivative channels (c > 0) apply it.
+//
+// Row pass: item = (row pair, QX outputs); (lo_2r, lo_2r+1) accumulate
+// (h_i, h_i) * (in_2r, in_2r+1), so the result is already the row pair the
+// column pass reads.  Column pass: out = sum_s (h_2s, h_2s+1) . (lo_2(k+s),
+// lo_2(k+s)+1), the even and odd taps summed in the two lanes.
 template <int P, int MODE>
-__device__ __forceinline__ void ana_step(const AnaArgs &a, const float *in_c,
-                                         float *lo_s, float *hi_s, int l, int bb,
+__device__ __forceinline__ void ana_step(const AnaArgs &a, const float2 *in_c,
+                                         float2 *lo_s, float2 *hi_s, int l, int bb,
                                          int c, int kx0, int ky0, float q,
                                          uint32_t &keep) {
-  constexpr int RH = 2 * TY + 2 * P - 2;
+  constexpr int RP = TY + P - 1;
   constexpr int NSX = TX / QX;
   constexpr int NV = 2 * QX + 2 * P - 2;
-  constexpr int NW = 2 * QY + 2 * P - 2;
+  constexpr int NW = QY + P - 1;
   static_assert((TY / QY) * TX == NT, "one column item per thread");
   const int h = a.M >> 1;
   const int kx = threadIdx.x % TX, s = threadIdx.x / TX;
   const int kxg = kx0 + kx;
   const size_t NN = (size_t)a.n * a.n;
   float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * NN;
-  // prefetch: subbands DX (low y, high x), DY (high y, low x), HH, LL
+  // subband offsets from the LL position: DX (low y, high x), DY, HH
+  const int hn = h * a.n;
+  const int sbo[4] = {h, hn, hn + h, 0};
   float pre[4][QY];
-  size_t off[4][QY];
+  int off[QY];
   bool act[QY];
 #pragma unroll
   for (int qq = 0; qq < QY; ++qq) {
     const int ky = ky0 + QY * s + qq;
     act[qq] = ky < h && kxg < h;
-    off[0][qq] = (size_t)ky * a.n + h + kxg;
-    off[1][qq] = (size_t)(h + ky) * a.n + kxg;
-    off[2][qq] = (size_t)(h + ky) * a.n + h + kxg;
-    off[3][qq] = (size_t)ky * a.n + kxg;
+    off[qq] = ky * a.n + kxg;
 #pragma unroll
     for (int sb = 0; sb < 4; ++sb) pre[sb][qq] = 0.f;
     if (MODE == WAVE_ITERATE && act[qq]) {
 #pragma unroll
-      for (int sb = 0; sb < 3; ++sb) pre[sb][qq] = up[off[sb][qq]];
-      if (a.last) pre[3][qq] = up[off[3][qq]];
+      for (int sb = 0; sb < 3; ++sb) pre[sb][qq] = up[off[qq] + sbo[sb]];
+      if (a.last) pre[3][qq] = up[off[qq]];
     }
   }
-  // rows: lo/hi along x
-  for (int it = threadIdx.x; it < RH * NSX; it += NT) {
-    const int r = it % RH, sx = it / RH;
-    const float *src = in_c + r * A_IP + 2 * QX * sx;
-    float v[NV];
+  // rows: lo/hi along x, two rows per item
+  for (int it = threadIdx.x; it < RP * NSX; it += NT) {
+    const int rp = it % RP, sx = it / RP;
+    const float2 *src = in_c + rp * A_IP + 2 * QX * sx;
+    float2 v[NV];
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] = src[i];
 #pragma unroll
     for (int qq = 0; qq < QX; ++qq) {
-      float lo = 0.f, hi = 0.f;
+      float2 lo = make_float2(0.f, 0.f), hi = make_float2(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < 2 * P; ++i) {
-        lo = fmaf(c_h[P - 1][i], v[2 * qq + i], lo);
-        hi = fmaf(c_g[P - 1][i], v[2 * qq + i], hi);
+        lo = ffma2(c_hh[P - 1][i], v[2 * qq + i], lo);
+        hi = ffma2(c_gg[P - 1][i], v[2 * qq + i], hi);
       }
-      lo_s[r * A_LP + QX * sx + qq] = lo;
-      hi_s[r * A_LP + QX * sx + qq] = hi;
+      lo_s[rp * A_LP + QX * sx + qq] = lo;
+      hi_s[rp * A_LP + QX * sx + qq] = hi;
     }
   }
   __syncthreads();
   // columns: the thread's item
   float cf[4][QY];
   {
-    const float *pl = lo_s + (2 * QY * s) * A_LP + kx;
-    const float *ph = hi_s + (2 * QY * s) * A_LP + kx;
-    float vl[NW], vh[NW];
+    const float2 *pl = lo_s + (QY * s) * A_LP + kx;
+    const float2 *ph = hi_s + (QY * s) * A_LP + kx;
+    float2 vl[NW], vh[NW];
 #pragma unroll
     for (int i = 0; i < NW; ++i) { vl[i] = pl[i * A_LP]; vh[i] = ph[i * A_LP]; }
 #pragma unroll
     for (int qq = 0; qq < QY; ++qq) {
-      float ll = 0.f, dy = 0.f, dx = 0.f, hh = 0.f;
+      float2 ll = make_float2(0.f, 0.f), dy = ll, dx = ll, hh = ll;
 #pragma unroll
-      for (int i = 0; i < 2 * P; ++i) {
-        ll = fmaf(c_h[P - 1][i], vl[2 * qq + i], ll);
-        dy = fmaf(c_g[P - 1][i], vl[2 * qq + i], dy);
-        dx = fmaf(c_h[P - 1][i], vh[2 * qq + i], dx);
-        hh = fmaf(c_g[P - 1][i], vh[2 * qq + i], hh);
+      for (int j = 0; j < P; ++j) {
+        ll = ffma2(c_hp[P - 1][j], vl[qq + j], ll);
+        dy = ffma2(c_gp[P - 1][j], vl[qq + j], dy);
+        dx = ffma2(c_hp[P - 1][j], vh[qq + j], dx);
+        hh = ffma2(c_gp[P - 1][j], vh[qq + j], hh);
       }
-      cf[0][qq] = dx; cf[1][qq] = dy; cf[2][qq] = hh; cf[3][qq] = ll;
+      cf[0][qq] = dx.x + dx.y; cf[1][qq] = dy.x + dy.y;
+      cf[2][qq] = hh.x + hh.y; cf[3][qq] = ll.x + ll.y;
     }
   }
   if (c == 0) keep = 0;
+  float *llp = a.last ? nullptr : a.ll_out + ((size_t)(c * a.L + l) * a.K + bb) * h * h;
 #pragma unroll
   for (int qq = 0; qq < QY; ++qq) {
     if (!act[qq]) continue;
-    const int ky = ky0 + QY * s + qq;
     const int nsb = a.last ? 4 : 3;
 #pragma unroll
     for (int sb = 0; sb < 4; ++sb) {
@@ -208,18 +232,17 @@ __device__ __forceinline__ void ana_step(const AnaArgs &a, const float *in_c,
           val = (keep & bit) ? p : 0.f;
         }
       }
-      up[off[sb][qq]] = val;
+      up[off[qq] + sbo[sb]] = val;
     }
-    if (!a.last)
-      a.ll_out[(((size_t)(c * a.L + l) * a.K + bb) * h + ky) * h + kxg] = cf[3][qq];
+    if (!a.last) llp[(ky0 + QY * s + qq) * h + kxg] = cf[3][qq];
   }
   __syncthreads();
 }
 
 template <int MODE>
 __device__ __forceinline__ void ana_dispatch(int p, const AnaArgs &a,
-                                             const float *in_c, float *lo_s,
-                                             float *hi_s, int l, int bb, int c,
+                                             const float2 *in_c, float2 *lo_s,
+                                             float2 *hi_s, int l, int bb, int c,
                                              int kx0, int ky0, float q,
                                              uint32_t &keep) {
   switch (p) {
@@ -236,17 +259,17 @@ __device__ __forceinline__ void ana_dispatch(int p, const AnaArgs &a,
 
 template <int CH, int MODE, bool LEVEL1>
 __global__ void __launch_bounds__(NT, 3) k_ana(AnaArgs a) {
-  extern __shared__ float smem[];
-  float *in_s = smem;                       // [CH][A_RH][A_IP]
-  float *lo_s = in_s + CH * A_RH * A_IP;    // [A_RH][A_LP]
-  float *hi_s = lo_s + A_RH * A_LP;
+  extern __shared__ float2 smem2[];
+  float2 *in_s = smem2;                     // [CH][A_RP][A_IP] row pairs
+  float2 *lo_s = in_s + CH * A_RP * A_IP;   // [A_RP][A_LP]
+  float2 *hi_s = lo_s + A_RP * A_LP;
   const int h = a.M >> 1;
   const int ntx = (h + TX - 1) / TX;
   const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
   const int l = LEVEL1 ? blockIdx.y : blockIdx.y / a.K;
   const int b = LEVEL1 ? 0 : blockIdx.y % a.K;
   const int P = LEVEL1 ? a.K : b + 1;
-  const int RH = 2 * TY + 2 * P - 2, RW = 2 * TX + 2 * P - 2;
+  const int RP = TY + P - 1, RW = 2 * TX + 2 * P - 2;
   const int Mm = a.M - 1;
   const size_t NN = (size_t)a.n * a.n;
   const size_t CS = (size_t)a.L * NN;   // channel stride of images
@@ -256,29 +279,33 @@ __global__ void __launch_bounds__(NT, 3) k_ana(AnaArgs a) {
     mu = (float)S.mu;
     sbl = (float)(S.sigma * (double)a.beta[l]);
   }
-  for (int it = threadIdx.x; it < RH * RW; it += NT) {
-    const int r = it / RW, cc = it - r * RW;
-    const int yy = (2 * ky0 + r) & Mm, xx = (2 * kx0 + cc) & Mm;
-    float w[CH];
-    if (LEVEL1) {
-      const size_t pix = (size_t)l * NN + (size_t)yy * a.n + xx;
-      if (MODE == WAVE_TRANSFORM) {
-        w[0] = a.in[pix];
+  for (int it = threadIdx.x; it < RP * RW; it += NT) {
+    const int rp = it / RW, cc = it - rp * RW;
+    const int xx = (2 * kx0 + cc) & Mm;
+    float w[2][CH];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int yy = (2 * ky0 + 2 * rp + e) & Mm;
+      if (LEVEL1) {
+        const size_t pix = (size_t)l * NN + (size_t)yy * a.n + xx;
+        if (MODE == WAVE_TRANSFORM) {
+          w[e][0] = a.in[pix];
+        } else {
+          float z[CH];
+#pragma unroll
+          for (int c = 0; c < CH; ++c)
+            z[c] = 2.f * a.xt[c * CS + pix] - a.x[c * CS + pix];
+          w[e][0] = z[0];
+          if (CH == 3) { w[e][1] = fmaf(mu, z[1], z[0]); w[e][2] = z[2]; }
+        }
       } else {
-        float z[CH];
 #pragma unroll
         for (int c = 0; c < CH; ++c)
-          z[c] = 2.f * a.xt[c * CS + pix] - a.x[c * CS + pix];
-        w[0] = z[0];
-        if (CH == 3) { w[1] = fmaf(mu, z[1], z[0]); w[2] = z[2]; }
+          w[e][c] = a.in[(((size_t)(c * a.L + l) * a.K + b) * a.M + yy) * a.M + xx];
       }
-    } else {
-#pragma unroll
-      for (int c = 0; c < CH; ++c)
-        w[c] = a.in[(((size_t)(c * a.L + l) * a.K + b) * a.M + yy) * a.M + xx];
     }
 #pragma unroll
-    for (int c = 0; c < CH; ++c) in_s[(c * A_RH + r) * A_IP + cc] = w[c];
+    for (int c = 0; c < CH; ++c) in_s[(c * A_RP + rp) * A_IP + cc] = make_float2(w[0][c], w[1][c]);
   }
   __syncthreads();
   uint32_t keep = 0;
@@ -288,7 +315,7 @@ __global__ void __launch_bounds__(NT, 3) k_ana(AnaArgs a) {
     for (int c = 0; c < CH; ++c) {
       // dual step scale: sigma mu_l (primal, d/dgamma), sigma beta_l (d/dmu)
       const float qc = MODE == WAVE_ITERATE ? (c == 1 ? sbl : sbl * mu) : 1.f;
-      ana_dispatch<MODE>(bb + 1, a, in_s + c * A_RH * A_IP, lo_s, hi_s, l, bb, c,
+      ana_dispatch<MODE>(bb + 1, a, in_s + c * A_RP * A_IP, lo_s, hi_s, l, bb, c,
                          kx0, ky0, qc, keep);
     }
   }
@@ -444,8 +471,7 @@ __global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
   const int h = a.M >> 1;
   const int ntx = (h + TX - 1) / TX;
   const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
-  const int l = LEVEL1 ? blockIdx.y : blockIdx.y / a.K;
-  const int b = LEVEL1 ? 0 : blockIdx.y % a.K;
+  const int l = blockIdx.y;
   const float mu = (MODE == WAVE_ITERATE) ? (float)a.sc[l / a.Lc].mu : 0.f;
   const int sx = threadIdx.x % (TX / QXP), my = threadIdx.x / (TX / QXP);
   const int yy = 2 * ky0 + my, xx0 = 2 * kx0 + 2 * QXP * sx;
@@ -454,15 +480,15 @@ __global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
   for (int c = 0; c < CH; ++c)
 #pragma unroll
     for (int e = 0; e < 2 * QXP; ++e) acc[c][e] = 0.f;
-  const int nsteps = (LEVEL1 ? a.K : 1) * CH;
-  syn_issue(a, cf0, l, LEVEL1 ? 0 : b, 0, kx0, ky0);
+  // (basis, chain) steps; coarser levels write each basis' LL_{j-1}
+  const int nsteps = a.K * CH;
+  syn_issue(a, cf0, l, 0, 0, kx0, ky0);
   cp_commit();
   for (int i = 0; i < nsteps; ++i) {
-    const int bb = LEVEL1 ? i / CH : b, c = i % CH;
+    const int bb = i / CH, c = i % CH;
     float *cf = cf0 + (i & 1) * 4 * SUB;
     if (i + 1 < nsteps) {
-      const int nb = LEVEL1 ? (i + 1) / CH : b;
-      syn_issue(a, cf0 + ((i + 1) & 1) * 4 * SUB, l, nb, (i + 1) % CH, kx0, ky0);
+      syn_issue(a, cf0 + ((i + 1) & 1) * 4 * SUB, l, (i + 1) / CH, (i + 1) % CH, kx0, ky0);
       cp_commit();
       cp_wait<1>();
     } else {
@@ -483,7 +509,7 @@ __global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
         }
       }
     } else if (yy < a.M) {
-      float *dst = a.ll_out + (((size_t)(c * a.L + l) * a.K + b) * a.M + yy) * a.M;
+      float *dst = a.ll_out + (((size_t)(c * a.L + l) * a.K + bb) * a.M + yy) * a.M;
 #pragma unroll
       for (int e = 0; e < 2 * QXP; ++e)
         if (xx0 + e < a.M) dst[xx0 + e] = o[e];
@@ -686,7 +712,7 @@ cudaError_t synthesis_all(const WaveArgs &w, const SynArgs &base, cudaStream_t s
     a.top = (j == w.J);
     a.ll_in = a.top ? nullptr : w.scratch + w.lvl_off[j];
     a.ll_out = w.scratch + w.lvl_off[j - 1];
-    e = launch_syn<CH, MODE, false>(a, w.L * w.K, st, w.prof);
+    e = launch_syn<CH, MODE, false>(a, w.L, st, w.prof);
     if (e != cudaSuccess) return e;
   }
   a.M = w.n;
@@ -723,14 +749,26 @@ cudaError_t analysis_all(const WaveArgs &w, const AnaArgs &base, cudaStream_t st
 
 cudaError_t upload_filters(const double h[8][16]) {
   float hf[8][16], gf[8][16];
-  for (int p = 1; p <= 8; ++p)
+  float2 hh[8][16], gg[8][16], hp[8][8], gp[8][8];
+  for (int p = 1; p <= 8; ++p) {
     for (int i = 0; i < 16; ++i) {
       hf[p - 1][i] = i < 2 * p ? (float)h[p - 1][i] : 0.f;
       gf[p - 1][i] = i < 2 * p ? (float)((i & 1 ? -1.0 : 1.0) * h[p - 1][2 * p - 1 - i]) : 0.f;
+      hh[p - 1][i] = make_float2(hf[p - 1][i], hf[p - 1][i]);
+      gg[p - 1][i] = make_float2(gf[p - 1][i], gf[p - 1][i]);
     }
+    for (int j = 0; j < 8; ++j) {
+      hp[p - 1][j] = make_float2(hf[p - 1][2 * j], hf[p - 1][2 * j + 1]);
+      gp[p - 1][j] = make_float2(gf[p - 1][2 * j], gf[p - 1][2 * j + 1]);
+    }
+  }
   cudaError_t e = cudaMemcpyToSymbol(c_h, hf, sizeof(hf));
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_g, gf, sizeof(gf));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_g, gf, sizeof(gf));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_hh, hh, sizeof(hh));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gg, gg, sizeof(gg));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_hp, hp, sizeof(hp));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_gp, gp, sizeof(gp));
+  return e;
 }
 
 cudaError_t wavelet_synthesis_prox(const WaveArgs &w, const Group &gr,

@@ -42,6 +42,7 @@ WORKLOADS = {
     "c5crop_256x256x16": (256, 16, 125, 6, 15625, 5),
     # a mid-size cube for profiler captures (state ~2 GB, inputs > L2)
     "prof_512x512x32": (512, 32, 500, 25, 50000, 6),
+    "prof_512x512x64": (512, 64, 500, 25, 50000, 7),
 }
 
 
