@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace muffin {
@@ -39,6 +41,17 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4],
       "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_wait0() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 struct DctKArgs {
@@ -87,6 +100,69 @@ __device__ __forceinline__ void tile_gemm(const float *__restrict__ Ahi,
       mma_tf32(acc[nt], al, h0, h1);
       mma_tf32(acc[nt], ah, l0, l1);
       mma_tf32(acc[nt], ah, h0, h1);
+    }
+  }
+}
+
+// tile_gemm with A in shared memory ([Lp][CP], TF32 hi/lo halves of C):
+// TR = false multiplies by C, TR = true by C^T (transposed indexing)
+template <int PT, bool TR>
+__device__ __forceinline__ void tile_gemm_s(const float *Ahi, const float *Alo, int CP,
+                                            int Lp, int m0, const float *B, int PP,
+                                            float (&acc)[PT / 8][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < PT / 8; ++nt)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+  for (int k0 = 0; k0 < Lp; k0 += 8) {
+    uint32_t ah[4], al[4];
+    // fragment element (row, col): row m0 + g (+8), col k0 + t (+4)
+    int o[4];
+    if (!TR) {
+      o[0] = (m0 + g) * CP + k0 + t;   o[1] = (m0 + g + 8) * CP + k0 + t;
+      o[2] = o[0] + 4;                 o[3] = o[1] + 4;
+    } else {
+      o[0] = (k0 + t) * CP + m0 + g;   o[1] = o[0] + 8;
+      o[2] = o[0] + 4 * CP;            o[3] = o[2] + 8;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ah[q] = __float_as_uint(Ahi[o[q]]);
+      al[q] = __float_as_uint(Alo[o[q]]);
+    }
+    const float *b0p = B + (k0 + t) * PP + g;
+    const float *b1p = B + (k0 + t + 4) * PP + g;
+#pragma unroll
+    for (int nt = 0; nt < PT / 8; ++nt) {
+      const float f0 = b0p[nt * 8], f1 = b1p[nt * 8];
+      const uint32_t h0 = to_tf32(f0), h1 = to_tf32(f1);
+      const uint32_t l0 = to_tf32(f0 - __uint_as_float(h0));
+      const uint32_t l1 = to_tf32(f1 - __uint_as_float(h1));
+      mma_tf32(acc[nt], al, h0, h1);
+      mma_tf32(acc[nt], ah, l0, l1);
+      mma_tf32(acc[nt], ah, h0, h1);
+    }
+  }
+}
+
+// rows [0, L) of a [Lp][PT + 8] shared tile -> dst[l * N + n0 + p] with
+// 16-byte stores (guarded scalar stores for a ragged last tile)
+template <int PT>
+__device__ __forceinline__ void store_rows(const float *src, float *dst, int L, int Lp,
+                                           size_t N, size_t n0, bool full) {
+  constexpr int PP = PT + 8, Q = PT / 4;
+  for (int it = threadIdx.x; it < Lp * Q; it += DT) {
+    const int l = it / Q, p4 = (it - l * Q) * 4;
+    if (l >= L) continue;
+    const float *s = src + l * PP + p4;
+    float *d = dst + (size_t)l * N + n0 + p4;
+    if (full) {
+      *reinterpret_cast<float4 *>(d) = *reinterpret_cast<const float4 *>(s);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (n0 + p4 + e < N) d[e] = s[e];
     }
   }
 }
@@ -197,145 +273,150 @@ __global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
   }
 }
 
-// Iteration kernel for L <= 64 (one 16-row m-tile per warp): the input
-// tile is loaded with 16-byte loads, both chains' products of the first GEMM
-// stay in registers, and the updated duals overwrite the input tile in
-// shared memory, so a CTA needs a single [CH][Lp][PT+8] buffer (higher
-// occupancy for this HBM-bound step).
+// Iteration kernel for L <= 64 (one 16-row m-tile per warp).  Persistent:
+// each CTA copies the TF32 hi/lo halves of C into shared memory once and
+// then walks pixel tiles, so the A fragments of both products come from
+// shared memory (C^T by transposed indexing).  Global traffic is coalesced:
+// the input tile is read with 16-byte loads, each chain's old duals arrive
+// by cp.async while the chain's first product runs, and the new duals and
+// t are staged in shared memory and written back as whole 128-byte rows.
 template <int CH, int PT>
-__global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
+__global__ void __launch_bounds__(DT, 3) k_dct_small(DctKArgs a) {
   extern __shared__ float sm[];
   constexpr int PP = PT + 8;
-  const int Lp = a.Lp, L = a.L;
-  float *zb = sm;                        // [CH][Lp][PP]
+  constexpr int Q = PT / 4;               // float4 per tile row
+  const int Lp = a.Lp, L = a.L, CP = a.Lp + 4;
+  float *chs = sm;                        // [Lp][CP] C, TF32 high part
+  float *cls = chs + Lp * CP;             // [Lp][CP] C, TF32 low part
+  float *zb = cls + Lp * CP;              // [CH][Lp][PP] products' B operands
+  float *vb = zb + CH * Lp * PP;          // [Lp][PP] old duals / t staging
+  float *als = vb + Lp * PP;              // [PT] alpha of the tile
   const size_t N = (size_t)a.n * a.n;
-  const size_t CS = (size_t)a.B * L * N;     // chain stride
-  const size_t n0 = (size_t)blockIdx.x * PT;
-  const int cube = blockIdx.y;
+  const size_t CS = (size_t)a.B * L * N;  // chain stride
+  const int tpc = (int)((N + PT - 1) / PT);
+  const int ntiles = tpc * a.B;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const float gamma = (float)a.sc[cube].gamma;
-  const float sigma = (float)a.sc[cube].sigma;
-  const size_t cb = (size_t)cube * L * N;    // the cube's first band
-  const float *__restrict__ alpha = a.alpha + (size_t)cube * N;
-  const bool full = n0 + PT <= N;
-  for (int it = threadIdx.x; it < Lp * (PT / 4); it += DT) {
-    const int l = it / (PT / 4), p4 = (it - l * (PT / 4)) * 4;
-    float z[CH][4];
-    if (l < L && full) {
-      const size_t j = cb + (size_t)l * N + n0 + p4;
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const float4 xt = *reinterpret_cast<const float4 *>(a.xt + c * CS + j);
-        const float4 xx = *reinterpret_cast<const float4 *>(a.x + c * CS + j);
-        z[c][0] = 2.f * xt.x - xx.x; z[c][1] = 2.f * xt.y - xx.y;
-        z[c][2] = 2.f * xt.z - xx.z; z[c][3] = 2.f * xt.w - xx.w;
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < CH; ++c)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const size_t pix = n0 + p4 + e;
-          const size_t j = cb + (size_t)l * N + pix;
-          z[c][e] = (l < L && pix < N) ? 2.f * a.xt[c * CS + j] - a.x[c * CS + j] : 0.f;
-        }
-    }
-    if (CH == 3)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) z[2][e] = fmaf(gamma, z[2][e], z[0][e]);  // Algorithm 4
-#pragma unroll
-    for (int c = 0; c < CH; ++c)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) zb[(c * Lp + l) * PP + p4 + e] = z[c][e];
-  }
-  __syncthreads();
   const int mt = warp;
   const bool has = mt * 16 < Lp;
-  // one chain at a time: product, then (after every warp has read the
-  // chain's input tile) the dual update written over that tile
-  uint32_t keep = 0;
+  for (int it = threadIdx.x; it < Lp * Lp; it += DT) {
+    const int r = it / Lp, c = it - r * Lp;
+    chs[r * CP + c] = a.a1hi[it];
+    cls[r * CP + c] = a.a1lo[it];
+  }
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int cube = tile / tpc;
+    const size_t n0 = (size_t)(tile - cube * tpc) * PT;
+    const float gamma = (float)a.sc[cube].gamma;
+    const float sigma = (float)a.sc[cube].sigma;
+    const size_t cb = (size_t)cube * L * N;    // the cube's first band
+    const bool full = n0 + PT <= N;
+    __syncthreads();                           // previous tile done with zb, vb, als
+    for (int it = threadIdx.x; it < Lp * Q; it += DT) {
+      const int l = it / Q, p4 = (it - l * Q) * 4;
+      float z[CH][4];
+      if (l < L && full) {
+        const size_t j = cb + (size_t)l * N + n0 + p4;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const float4 xt = *reinterpret_cast<const float4 *>(a.xt + c * CS + j);
+          const float4 xx = *reinterpret_cast<const float4 *>(a.x + c * CS + j);
+          z[c][0] = 2.f * xt.x - xx.x; z[c][1] = 2.f * xt.y - xx.y;
+          z[c][2] = 2.f * xt.z - xx.z; z[c][3] = 2.f * xt.w - xx.w;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const size_t pix = n0 + p4 + e;
+            const size_t j = cb + (size_t)l * N + pix;
+            z[c][e] = (l < L && pix < N) ? 2.f * a.xt[c * CS + j] - a.x[c * CS + j] : 0.f;
+          }
+      }
+      if (CH == 3)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) z[2][e] = fmaf(gamma, z[2][e], z[0][e]);  // Algorithm 4
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+        *reinterpret_cast<float4 *>(zb + (c * Lp + l) * PP + p4) =
+            make_float4(z[c][0], z[c][1], z[c][2], z[c][3]);
+    }
+    for (int it = threadIdx.x; it < PT; it += DT)
+      als[it] = n0 + it < N ? a.alpha[(size_t)cube * N + n0 + it] : 0.f;
+    // first product and dual update, one chain at a time
+    uint32_t keep = 0;
 #pragma unroll 1
-  for (int c = 0; c < CH; ++c) {
-    float acc[PT / 8][4];
-    if (has) tile_gemm<PT>(a.a1hi, a.a1lo, Lp, mt * 16, zb + c * Lp * PP, PP, acc);
-    __syncthreads();
-    if (has) {
-      const float sg = c == 2 ? sigma : sigma * gamma;
-      // all loads of the fragment first (independent), then update and store
-      float vold[PT / 8][4], alw[PT / 8][2];
-#pragma unroll
-      for (int nt = 0; nt < PT / 8; ++nt) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int k = mt * 16 + g + (e >= 2 ? 8 : 0);
-          const size_t pix = n0 + nt * 8 + 2 * t + (e & 1);
-          vold[nt][e] = (k < L && pix < N) ? a.v[c * CS + cb + (size_t)k * N + pix] : 0.f;
-        }
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const size_t pix = n0 + nt * 8 + 2 * t + e;
-          alw[nt][e] = pix < N ? alpha[pix] : 0.f;
-        }
-      }
-#pragma unroll
-      for (int nt = 0; nt < PT / 8; ++nt) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int k = mt * 16 + g + (e >= 2 ? 8 : 0);
-          const int p = nt * 8 + 2 * t + (e & 1);
-          const size_t pix = n0 + p;
-          float vn = 0.f;
-          if (k < L && pix < N) {
-            const float vt = fmaf(sg * alw[nt][e & 1], acc[nt][e], vold[nt][e]);
-            const uint32_t bit = 1u << (nt * 4 + e);
-            if (c == 0) {
-              vn = satf(vt);
-              if (fabsf(vt) <= 1.f) keep |= bit;
-            } else {
-              vn = (keep & bit) ? vt : 0.f;
-            }
-            a.v[c * CS + cb + (size_t)k * N + pix] = vn;
-          }
-          zb[(c * Lp + k) * PP + p] = vn;
-        }
-      }
-    }
-  }
-  __syncthreads();
-  if (CH == 3) {
-    for (int it = threadIdx.x; it < Lp * PT; it += DT) {
-      const int l = it / PT, p = it - l * PT;
-      float *d = zb + (2 * Lp + l) * PP + p;
-      *d = fmaf(gamma, *d, zb[l * PP + p]);     // gamma v'_gamma + v
-    }
-    __syncthreads();
-  }
-  if (has) {
-#pragma unroll
     for (int c = 0; c < CH; ++c) {
-      float acc2[PT / 8][4];
-      tile_gemm<PT>(a.a2hi, a.a2lo, Lp, mt * 16, zb + c * Lp * PP, PP, acc2);
-      float alw[PT / 8][2];
+      // vb is free: the barrier after the previous chain's epilogue
+      for (int it = threadIdx.x; it < Lp * Q; it += DT) {
+        const int l = it / Q, p4 = (it - l * Q) * 4;
+        float *d = vb + l * PP + p4;
+        const size_t j = c * CS + cb + (size_t)l * N + n0 + p4;
+        if (l < L && full) {
+          cp_async16(d, a.v + j);
+        } else {
 #pragma unroll
-      for (int nt = 0; nt < PT / 8; ++nt)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const size_t pix = n0 + nt * 8 + 2 * t + e;
-          alw[nt][e] = pix < N ? alpha[pix] : 0.f;
-        }
-#pragma unroll
-      for (int nt = 0; nt < PT / 8; ++nt) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int l = mt * 16 + g + (e >= 2 ? 8 : 0);
-          const int p = nt * 8 + 2 * t + (e & 1);
-          const size_t pix = n0 + p;
-          if (l < L && pix < N) {
-            const float s2 = (c == 2) ? alw[nt][e & 1] : gamma * alw[nt][e & 1];
-            a.t[c * CS + cb + (size_t)l * N + pix] = s2 * acc2[nt][e];
-          }
+          for (int e = 0; e < 4; ++e) d[e] = (l < L && n0 + p4 + e < N) ? a.v[j + e] : 0.f;
         }
       }
+      cp_commit();
+      if (c == 0) __syncthreads();             // the input tile and alpha are in place
+      float acc[PT / 8][4];
+      if (has) tile_gemm_s<PT, false>(chs, cls, CP, Lp, mt * 16, zb + c * Lp * PP, PP, acc);
+      cp_wait0();
+      __syncthreads();                         // vb landed; every warp has read zb[c]
+      if (has) {
+        const float sg = c == 2 ? sigma : sigma * gamma;
+#pragma unroll
+        for (int nt = 0; nt < PT / 8; ++nt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = mt * 16 + g + (e >= 2 ? 8 : 0);
+            const int p = nt * 8 + 2 * t + (e & 1);
+            float vn = 0.f;
+            if (k < L && n0 + p < N) {
+              const float vt = fmaf(sg * als[p], acc[nt][e], vb[k * PP + p]);
+              const uint32_t bit = 1u << (nt * 4 + e);
+              if (c == 0) {
+                vn = satf(vt);
+                if (fabsf(vt) <= 1.f) keep |= bit;
+              } else {
+                vn = (keep & bit) ? vt : 0.f;
+              }
+            }
+            zb[(c * Lp + k) * PP + p] = vn;
+          }
+      }
+      __syncthreads();
+      store_rows<PT>(zb + c * Lp * PP, a.v + c * CS + cb, L, Lp, N, n0, full);
+    }
+    if (CH == 3) {
+      __syncthreads();                         // the stores above read zb[0], zb[2]
+      for (int it = threadIdx.x; it < Lp * PT; it += DT) {
+        const int l = it / PT, p = it - l * PT;
+        float *d = zb + (2 * Lp + l) * PP + p;
+        *d = fmaf(gamma, *d, zb[l * PP + p]);  // gamma v'_gamma + v
+      }
+    }
+    // back-projection t = gamma_n C^T v (per chain scale of Algorithms 3/4)
+#pragma unroll 1
+    for (int c = 0; c < CH; ++c) {
+      __syncthreads();                         // zb[c] final; vb free
+      float acc2[PT / 8][4];
+      if (has) {
+        tile_gemm_s<PT, true>(chs, cls, CP, Lp, mt * 16, zb + c * Lp * PP, PP, acc2);
+#pragma unroll
+        for (int nt = 0; nt < PT / 8; ++nt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int l = mt * 16 + g + (e >= 2 ? 8 : 0);
+            const int p = nt * 8 + 2 * t + (e & 1);
+            const float s2 = (c == 2) ? als[p] : gamma * als[p];
+            vb[l * PP + p] = s2 * acc2[nt][e];
+          }
+      }
+      __syncthreads();
+      store_rows<PT>(vb, a.t + c * CS + cb, L, Lp, N, n0, full);
     }
   }
 }
@@ -343,17 +424,30 @@ __global__ void __launch_bounds__(DT, 6) k_dct_small(DctKArgs a) {
 template <int CH>
 cudaError_t launch_dct_small(const DctKArgs &a, cudaStream_t st, Prof *prof) {
   constexpr int PT = 32;
-  const size_t sm = (size_t)CH * a.Lp * (PT + 8) * sizeof(float);
+  const size_t sm = ((size_t)2 * a.Lp * (a.Lp + 4) + (size_t)(CH + 1) * a.Lp * (PT + 8) + PT) *
+                    sizeof(float);
   static bool attr = false;
+  static int per_sm = 0, sms = 0;
   if (!attr) {
     cudaFuncSetAttribute(k_dct_small<CH, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     attr = true;
   }
+  static size_t sm_seen = 0;
+  if (sm != sm_seen) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dct_small<CH, PT>, DT, sm);
+    if (per_sm < 1) per_sm = 1;
+    sm_seen = sm;
+  }
   const size_t N = (size_t)a.n * a.n;
+  const size_t ntiles = ((N + PT - 1) / PT) * (size_t)a.B;
+  const size_t grid = std::min(ntiles, (size_t)per_sm * (size_t)sms);
   const double vox = (double)N * a.L * a.B;
   ProfScope ps(prof, "spectral_dual", CH * vox * 20.0, 2.0 * CH * 2.0 * a.L * vox, st);
-  k_dct_small<CH, PT><<<dim3((unsigned)((N + PT - 1) / PT), a.B), DT, sm, st>>>(a);
+  k_dct_small<CH, PT><<<(unsigned)grid, DT, sm, st>>>(a);
   return cudaGetLastError();
 }
 
