@@ -45,9 +45,24 @@ k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S, int n, int RB,
   float2 *d = sm2, *tws = sm2 + nq * pitch;
   load_tw(tws, tw, tlen);
   const float *xi = x + (size_t)img * n * n + (size_t)y0 * n;
-  for (int i = threadIdx.x; i < nq * n; i += blockDim.x) {
-    const int q = i / n, col = i - q * n;
-    d[q * pitch + fpad(col)] = make_float2(xi[(2 * q) * n + col], xi[(2 * q + 1) * n + col]);
+  // every thread owns at most VPT row-pair elements: all loads first
+  constexpr int VPT = fft_vpt(NN);
+  float2 v[VPT];
+#pragma unroll
+  for (int u = 0; u < VPT; ++u) {
+    const int i = threadIdx.x + u * kThreads;
+    if (i < nq * n) {
+      const int q = i / n, col = i - q * n;
+      v[u] = make_float2(xi[(2 * q) * n + col], xi[(2 * q + 1) * n + col]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < VPT; ++u) {
+    const int i = threadIdx.x + u * kThreads;
+    if (i < nq * n) {
+      const int q = i / n, col = i - q * n;
+      d[q * pitch + fpad(col)] = v[u];
+    }
   }
   __syncthreads();
   fft_inplace<NN, false>(d, nq, pitch, tws);
@@ -87,9 +102,21 @@ k_cols(float2 *__restrict__ S, const float *__restrict__ kspec, int n, int L,
     const int i = threadIdx.x + u * kThreads;
     kr[u] = i < ncol * n ? __ldg(Ki + i) : 0.f;
   }
-  for (int i = threadIdx.x; i < ncol * n; i += blockDim.x) {
-    const int c = i / n, y = i - c * n;
-    d[c * pitch + fpad(y)] = Si[i];
+  {
+    float2 v[KPT];
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+      const int i = threadIdx.x + u * kThreads;
+      if (i < ncol * n) v[u] = Si[i];
+    }
+#pragma unroll
+    for (int u = 0; u < KPT; ++u) {
+      const int i = threadIdx.x + u * kThreads;
+      if (i < ncol * n) {
+        const int c = i / n, y = i - c * n;
+        d[c * pitch + fpad(y)] = v[u];
+      }
+    }
   }
   __syncthreads();
   fft_inplace<NN, false>(d, ncol, pitch, tws);

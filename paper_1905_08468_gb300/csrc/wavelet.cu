@@ -66,7 +66,7 @@ constexpr int S_LP = (TX + PMAX - 1) | 1;            // column-pass output pitch
 constexpr int QXP = 4, QYP = 2;                      // coefficient pairs per thread
 
 constexpr size_t ana_smem(int ch) {
-  return ((size_t)ch * A_RP * A_IP + 2 * A_RP * A_LP) * sizeof(float2);
+  return ((size_t)ch * A_RP * A_IP + 4 * A_RP * A_LP) * sizeof(float2);
 }
 constexpr size_t syn_smem(int) {
   return (size_t)(8 * S_CH * S_CP + 2 * (2 * TY) * S_LP) * sizeof(float);
@@ -123,52 +123,26 @@ __device__ __forceinline__ void ana_emit(const AnaArgs &a, int l, int bb,
   }
 }
 
-// One (basis, chain) step of an analysis level: rows of the resident input
-// tile -> lo/hi, then the thread's own column item (TY/QY x TX items ==
-// NT threads): four subbands of QY coefficients, fused with the dual update.
-// The U values the item updates are loaded before the row pass so their
-// latency overlaps the filtering.  Channel 0 records the mask Pi(p) of each
-// output in `keep`; derivative channels (c > 0) apply it.
-//
-// Row pass: item = (row pair, QX outputs); (lo_2r, lo_2r+1) accumulate
-// (h_i, h_i) * (in_2r, in_2r+1), so the result is already the row pair the
-// column pass reads.  Column pass: out = sum_s (h_2s, h_2s+1) . (lo_2(k+s),
-// lo_2(k+s)+1), the even and odd taps summed in the two lanes.
-template <int P, int MODE>
-__device__ __forceinline__ void ana_step(const AnaArgs &a, const float2 *in_c,
-                                         float2 *lo_s, float2 *hi_s, int l, int bb,
-                                         int c, int kx0, int ky0, float q,
-                                         uint32_t &keep) {
+// One (basis, chain) step of an analysis level is split into
+//   row pass:  rows of the resident input tile -> lo/hi (shared), item =
+//              (row pair, QX outputs); (lo_2r, lo_2r+1) accumulate
+//              (h_i, h_i) * (in_2r, in_2r+1), so the result is already the
+//              row pair the column pass reads;
+//   column pass + dual update: the thread's own item (TY/QY x TX items ==
+//              NT threads), four subbands of QY coefficients; out = sum_s
+//              (h_2s, h_2s+1) . (lo_2(k+s), lo_2(k+s)+1), the even and odd
+//              taps summed in the two lanes.
+// The CTA runs them as a pipeline: in the phase of step s it does the
+// column pass and dual update of step s, then requests the U values of step
+// s + 1 and runs the row pass of step s + 1 into the other lo/hi buffer, so
+// one barrier separates the steps and the U loads have a whole phase to
+// arrive.  Channel 0 records the mask Pi(p) of each output in `keep`;
+// derivative channels (c > 0) apply it.
+template <int P>
+__device__ __forceinline__ void ana_rows(const float2 *in_c, float2 *lo_s, float2 *hi_s) {
   constexpr int RP = TY + P - 1;
   constexpr int NSX = TX / QX;
   constexpr int NV = 2 * QX + 2 * P - 2;
-  constexpr int NW = QY + P - 1;
-  static_assert((TY / QY) * TX == NT, "one column item per thread");
-  const int h = a.M >> 1;
-  const int kx = threadIdx.x % TX, s = threadIdx.x / TX;
-  const int kxg = kx0 + kx;
-  const size_t NN = (size_t)a.n * a.n;
-  float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * NN;
-  // subband offsets from the LL position: DX (low y, high x), DY, HH
-  const int hn = h * a.n;
-  const int sbo[4] = {h, hn, hn + h, 0};
-  float pre[4][QY];
-  int off[QY];
-  bool act[QY];
-#pragma unroll
-  for (int qq = 0; qq < QY; ++qq) {
-    const int ky = ky0 + QY * s + qq;
-    act[qq] = ky < h && kxg < h;
-    off[qq] = ky * a.n + kxg;
-#pragma unroll
-    for (int sb = 0; sb < 4; ++sb) pre[sb][qq] = 0.f;
-    if (MODE == WAVE_ITERATE && act[qq]) {
-#pragma unroll
-      for (int sb = 0; sb < 3; ++sb) pre[sb][qq] = up[off[qq] + sbo[sb]];
-      if (a.last) pre[3][qq] = up[off[qq]];
-    }
-  }
-  // rows: lo/hi along x, two rows per item
   for (int it = threadIdx.x; it < RP * NSX; it += NT) {
     const int rp = it % RP, sx = it / RP;
     const float2 *src = in_c + rp * A_IP + 2 * QX * sx;
@@ -187,34 +161,101 @@ __device__ __forceinline__ void ana_step(const AnaArgs &a, const float2 *in_c,
       hi_s[rp * A_LP + QX * sx + qq] = hi;
     }
   }
-  __syncthreads();
-  // columns: the thread's item
-  float cf[4][QY];
-  {
-    const float2 *pl = lo_s + (QY * s) * A_LP + kx;
-    const float2 *ph = hi_s + (QY * s) * A_LP + kx;
-    float2 vl[NW], vh[NW];
-#pragma unroll
-    for (int i = 0; i < NW; ++i) { vl[i] = pl[i * A_LP]; vh[i] = ph[i * A_LP]; }
-#pragma unroll
-    for (int qq = 0; qq < QY; ++qq) {
-      float2 ll = make_float2(0.f, 0.f), dy = ll, dx = ll, hh = ll;
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        ll = ffma2(c_hp[P - 1][j], vl[qq + j], ll);
-        dy = ffma2(c_gp[P - 1][j], vl[qq + j], dy);
-        dx = ffma2(c_hp[P - 1][j], vh[qq + j], dx);
-        hh = ffma2(c_gp[P - 1][j], vh[qq + j], hh);
-      }
-      cf[0][qq] = dx.x + dx.y; cf[1][qq] = dy.x + dy.y;
-      cf[2][qq] = hh.x + hh.y; cf[3][qq] = ll.x + ll.y;
-    }
+}
+
+__device__ __forceinline__ void ana_rows_dispatch(int p, const float2 *in_c, float2 *lo_s,
+                                                  float2 *hi_s) {
+  switch (p) {
+    case 1: ana_rows<1>(in_c, lo_s, hi_s); break;
+    case 2: ana_rows<2>(in_c, lo_s, hi_s); break;
+    case 3: ana_rows<3>(in_c, lo_s, hi_s); break;
+    case 4: ana_rows<4>(in_c, lo_s, hi_s); break;
+    case 5: ana_rows<5>(in_c, lo_s, hi_s); break;
+    case 6: ana_rows<6>(in_c, lo_s, hi_s); break;
+    case 7: ana_rows<7>(in_c, lo_s, hi_s); break;
+    default: ana_rows<8>(in_c, lo_s, hi_s); break;
   }
-  if (c == 0) keep = 0;
-  float *llp = a.last ? nullptr : a.ll_out + ((size_t)(c * a.L + l) * a.K + bb) * h * h;
+}
+
+template <int P>
+__device__ __forceinline__ void ana_cols(const float2 *lo_s, const float2 *hi_s,
+                                         float (&cf)[4][QY]) {
+  constexpr int NW = QY + P - 1;
+  const int kx = threadIdx.x % TX, s = threadIdx.x / TX;
+  const float2 *pl = lo_s + (QY * s) * A_LP + kx;
+  const float2 *ph = hi_s + (QY * s) * A_LP + kx;
+  float2 vl[NW], vh[NW];
+#pragma unroll
+  for (int i = 0; i < NW; ++i) { vl[i] = pl[i * A_LP]; vh[i] = ph[i * A_LP]; }
 #pragma unroll
   for (int qq = 0; qq < QY; ++qq) {
-    if (!act[qq]) continue;
+    float2 ll = make_float2(0.f, 0.f), dy = ll, dx = ll, hh = ll;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      ll = ffma2(c_hp[P - 1][j], vl[qq + j], ll);
+      dy = ffma2(c_gp[P - 1][j], vl[qq + j], dy);
+      dx = ffma2(c_hp[P - 1][j], vh[qq + j], dx);
+      hh = ffma2(c_gp[P - 1][j], vh[qq + j], hh);
+    }
+    cf[0][qq] = dx.x + dx.y; cf[1][qq] = dy.x + dy.y;
+    cf[2][qq] = hh.x + hh.y; cf[3][qq] = ll.x + ll.y;
+  }
+}
+
+__device__ __forceinline__ void ana_cols_dispatch(int p, const float2 *lo_s,
+                                                  const float2 *hi_s, float (&cf)[4][QY]) {
+  switch (p) {
+    case 1: ana_cols<1>(lo_s, hi_s, cf); break;
+    case 2: ana_cols<2>(lo_s, hi_s, cf); break;
+    case 3: ana_cols<3>(lo_s, hi_s, cf); break;
+    case 4: ana_cols<4>(lo_s, hi_s, cf); break;
+    case 5: ana_cols<5>(lo_s, hi_s, cf); break;
+    case 6: ana_cols<6>(lo_s, hi_s, cf); break;
+    case 7: ana_cols<7>(lo_s, hi_s, cf); break;
+    default: ana_cols<8>(lo_s, hi_s, cf); break;
+  }
+}
+
+// U values the thread's column item updates in step (bb, c): subbands DX
+// (low y, high x), DY, HH and, at the last level, LL
+template <int MODE>
+__device__ __forceinline__ void ana_prefetch(const AnaArgs &a, int l, int bb, int c,
+                                             int kx0, int ky0, float (&pre)[4][QY]) {
+  const int h = a.M >> 1, hn = h * a.n;
+  const int kx = threadIdx.x % TX, s = threadIdx.x / TX;
+  const int kxg = kx0 + kx;
+  const float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * ((size_t)a.n * a.n);
+#pragma unroll
+  for (int qq = 0; qq < QY; ++qq) {
+    const int ky = ky0 + QY * s + qq;
+    const int o = ky * a.n + kxg;
+    const bool act = MODE == WAVE_ITERATE && ky < h && kxg < h;
+    pre[0][qq] = act ? up[o + h] : 0.f;
+    pre[1][qq] = act ? up[o + hn] : 0.f;
+    pre[2][qq] = act ? up[o + hn + h] : 0.f;
+    pre[3][qq] = (act && a.last) ? up[o] : 0.f;
+  }
+}
+
+// dual update p = u + q w, u = sat(p) (or the mask of channel 0) and the
+// stores of step (bb, c)
+template <int MODE>
+__device__ __forceinline__ void ana_emit_step(const AnaArgs &a, int l, int bb, int c,
+                                              int kx0, int ky0, float q,
+                                              const float (&cf)[4][QY],
+                                              const float (&pre)[4][QY], uint32_t &keep) {
+  const int h = a.M >> 1, hn = h * a.n;
+  const int kx = threadIdx.x % TX, s = threadIdx.x / TX;
+  const int kxg = kx0 + kx;
+  float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * ((size_t)a.n * a.n);
+  float *llp = a.last ? nullptr : a.ll_out + ((size_t)(c * a.L + l) * a.K + bb) * h * h;
+  const int sbo[4] = {h, hn, hn + h, 0};
+  if (c == 0) keep = 0;
+#pragma unroll
+  for (int qq = 0; qq < QY; ++qq) {
+    const int ky = ky0 + QY * s + qq;
+    if (ky >= h || kxg >= h) continue;
+    const int o = ky * a.n + kxg;
     const int nsb = a.last ? 4 : 3;
 #pragma unroll
     for (int sb = 0; sb < 4; ++sb) {
@@ -232,28 +273,9 @@ __device__ __forceinline__ void ana_step(const AnaArgs &a, const float2 *in_c,
           val = (keep & bit) ? p : 0.f;
         }
       }
-      up[off[qq] + sbo[sb]] = val;
+      up[o + sbo[sb]] = val;
     }
-    if (!a.last) llp[(ky0 + QY * s + qq) * h + kxg] = cf[3][qq];
-  }
-  __syncthreads();
-}
-
-template <int MODE>
-__device__ __forceinline__ void ana_dispatch(int p, const AnaArgs &a,
-                                             const float2 *in_c, float2 *lo_s,
-                                             float2 *hi_s, int l, int bb, int c,
-                                             int kx0, int ky0, float q,
-                                             uint32_t &keep) {
-  switch (p) {
-    case 1: ana_step<1, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
-    case 2: ana_step<2, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
-    case 3: ana_step<3, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
-    case 4: ana_step<4, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
-    case 5: ana_step<5, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
-    case 6: ana_step<6, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
-    case 7: ana_step<7, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
-    default: ana_step<8, MODE>(a, in_c, lo_s, hi_s, l, bb, c, kx0, ky0, q, keep); break;
+    if (!a.last) llp[ky * h + kxg] = cf[3][qq];
   }
 }
 
@@ -261,8 +283,7 @@ template <int CH, int MODE, bool LEVEL1>
 __global__ void __launch_bounds__(NT, 3) k_ana(AnaArgs a) {
   extern __shared__ float2 smem2[];
   float2 *in_s = smem2;                     // [CH][A_RP][A_IP] row pairs
-  float2 *lo_s = in_s + CH * A_RP * A_IP;   // [A_RP][A_LP]
-  float2 *hi_s = lo_s + A_RP * A_LP;
+  float2 *lohi = in_s + CH * A_RP * A_IP;   // 2 x ([A_RP][A_LP] lo, hi)
   const int h = a.M >> 1;
   const int ntx = (h + TX - 1) / TX;
   const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
@@ -279,10 +300,11 @@ __global__ void __launch_bounds__(NT, 3) k_ana(AnaArgs a) {
     mu = (float)S.mu;
     sbl = (float)(S.sigma * (double)a.beta[l]);
   }
-  for (int it = threadIdx.x; it < RP * RW; it += NT) {
+  // input tile, two items per thread per round so twice the loads are in
+  // flight before the first use
+  auto load_item = [&](int it, float (&w)[2][CH]) {
     const int rp = it / RW, cc = it - rp * RW;
     const int xx = (2 * kx0 + cc) & Mm;
-    float w[2][CH];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int yy = (2 * ky0 + 2 * rp + e) & Mm;
@@ -304,20 +326,52 @@ __global__ void __launch_bounds__(NT, 3) k_ana(AnaArgs a) {
           w[e][c] = a.in[(((size_t)(c * a.L + l) * a.K + b) * a.M + yy) * a.M + xx];
       }
     }
+  };
+  auto store_item = [&](int it, const float (&w)[2][CH]) {
+    const int rp = it / RW, cc = it - rp * RW;
 #pragma unroll
     for (int c = 0; c < CH; ++c) in_s[(c * A_RP + rp) * A_IP + cc] = make_float2(w[0][c], w[1][c]);
+  };
+  const int items = RP * RW;
+  for (int it = threadIdx.x; it < items; it += 2 * NT) {
+    float w0[2][CH], w1[2][CH];
+    const bool two = it + NT < items;
+    load_item(it, w0);
+    if (two) load_item(it + NT, w1);
+    store_item(it, w0);
+    if (two) store_item(it + NT, w1);
   }
   __syncthreads();
+  // (basis, chain) steps, pipelined: column pass + dual update of step s,
+  // then the U loads and the row pass of step s + 1 (other lo/hi buffer)
+  const int b0 = LEVEL1 ? 0 : b;
+  const int nsteps = (LEVEL1 ? a.K : 1) * CH;
+  constexpr int LH = A_RP * A_LP;
+  float pre[4][QY], nxt[4][QY];
+  ana_prefetch<MODE>(a, l, b0, 0, kx0, ky0, pre);
+  ana_rows_dispatch(b0 + 1, in_s, lohi, lohi + LH);
+  __syncthreads();
   uint32_t keep = 0;
-  const int b0 = LEVEL1 ? 0 : b, b1 = LEVEL1 ? a.K : b + 1;
-  for (int bb = b0; bb < b1; ++bb) {
 #pragma unroll 1
-    for (int c = 0; c < CH; ++c) {
-      // dual step scale: sigma mu_l (primal, d/dgamma), sigma beta_l (d/dmu)
-      const float qc = MODE == WAVE_ITERATE ? (c == 1 ? sbl : sbl * mu) : 1.f;
-      ana_dispatch<MODE>(bb + 1, a, in_s + c * A_RP * A_IP, lo_s, hi_s, l, bb, c,
-                         kx0, ky0, qc, keep);
+  for (int s = 0; s < nsteps; ++s) {
+    const int bb = b0 + s / CH, c = s % CH;
+    float2 *lo_s = lohi + (s & 1) * 2 * LH;
+    float cf[4][QY];
+    ana_cols_dispatch(bb + 1, lo_s, lo_s + LH, cf);
+    // dual step scale: sigma mu_l (primal, d/dgamma), sigma beta_l (d/dmu)
+    const float qc = MODE == WAVE_ITERATE ? (c == 1 ? sbl : sbl * mu) : 1.f;
+    ana_emit_step<MODE>(a, l, bb, c, kx0, ky0, qc, cf, pre, keep);
+    if (s + 1 < nsteps) {
+      const int nb = b0 + (s + 1) / CH, nc = (s + 1) % CH;
+      ana_prefetch<MODE>(a, l, nb, nc, kx0, ky0, nxt);
+      float2 *lo_n = lohi + ((s + 1) & 1) * 2 * LH;
+      ana_rows_dispatch(nb + 1, in_s + nc * A_RP * A_IP, lo_n, lo_n + LH);
+#pragma unroll
+      for (int sb = 0; sb < 4; ++sb)
+#pragma unroll
+        for (int qq = 0; qq < QY; ++qq) pre[sb][qq] = nxt[sb][qq];
     }
+    __syncthreads();
   }
 }
 
@@ -509,10 +563,15 @@ __global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
         }
       }
     } else if (yy < a.M) {
-      float *dst = a.ll_out + (((size_t)(c * a.L + l) * a.K + bb) * a.M + yy) * a.M;
+      float *dst = a.ll_out + (((size_t)(c * a.L + l) * a.K + bb) * a.M + yy) * a.M + xx0;
+      if (xx0 + 2 * QXP <= a.M && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4 *>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
+      } else {
 #pragma unroll
-      for (int e = 0; e < 2 * QXP; ++e)
-        if (xx0 + e < a.M) dst[xx0 + e] = o[e];
+        for (int e = 0; e < 2 * QXP; ++e)
+          if (xx0 + e < a.M) dst[e] = o[e];
+      }
     }
     __syncthreads();
   }
@@ -520,9 +579,15 @@ __global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
   const size_t NN = (size_t)a.n * a.n;
   const size_t row = (size_t)l * NN + (size_t)yy * a.n;
   if (MODE == WAVE_TRANSFORM) {
+    float *dst = a.out + row + xx0;
+    if (xx0 + 2 * QXP <= a.n && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+      *reinterpret_cast<float4 *>(dst) = make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
+      *reinterpret_cast<float4 *>(dst + 4) = make_float4(acc[0][4], acc[0][5], acc[0][6], acc[0][7]);
+    } else {
 #pragma unroll
-    for (int e = 0; e < 2 * QXP; ++e)
-      if (xx0 + e < a.n) a.out[row + xx0 + e] = acc[0][e];
+      for (int e = 0; e < 2 * QXP; ++e)
+        if (xx0 + e < a.n) dst[e] = acc[0][e];
+    }
     return;
   }
   const float tau = (float)a.sc[l / a.Lc].tau;
