@@ -344,6 +344,8 @@ def main() -> None:
     ap.add_argument("--window", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch variants instead of tuning them for the shape")
     ap.add_argument("--serve", action="store_true",
                     help="served Poisson stream (continuous batching vs one cube per launch)")
     ap.add_argument("--serve-requests", type=int, default=64)
@@ -379,6 +381,12 @@ def main() -> None:
     x = torch.zeros_like(dirty)
     plan = pkg.Plan(c.n, c.L, psf, sure=True)
     del psf
+    tuning = None
+    if not args.no_autotune:
+        ti = plan.autotune()            # launch variants for this shape (results unchanged)
+        tuning = {"syn_packed": ti.syn_packed, "dct_ctas_per_sm": ti.dct_ctas_per_sm,
+                  "candidates": ti.candidates, "iter_ms_default": ti.ms_default,
+                  "iter_ms_tuned": ti.ms_best}
     kw = dict(window=args.window, eta=ETA, eps=eps)
 
     def step(xb, d, dl):
@@ -456,7 +464,7 @@ def main() -> None:
                "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-               "data": "synthetic", "config": workload_config(args),
+               "data": "synthetic", "config": dict(workload_config(args), tuning=tuning),
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks,
                "theta": list(theta), "kernels": kernels,

@@ -122,6 +122,43 @@ MUFFIN_API muffin_status muffin_plan_load_psf(muffin_plan plan, int32_t b0,
  * every kernel directly.  Results are identical either way. */
 MUFFIN_API muffin_status muffin_plan_graphs(muffin_plan plan, int32_t on);
 
+/* ---- per-shape tuning (launch variants of the hot kernels)
+ *
+ * Two launch choices change speed but not results (every variant computes
+ * the same sums in the same order, so outputs are bit-identical):
+ *   syn_packed       bit 0: coarse wavelet synthesis levels, bit 1: level 1;
+ *                    0 = scalar row pass (one pixel row per thread),
+ *                    1 = packed row pass (two rows per fma.rn.f32x2);
+ *   dct_ctas_per_sm  CTAs per SM of the persistent spectral kernel
+ *                    (0 = as many as fit).
+ * Which is fastest depends on the cube shape and the GPU. */
+typedef struct {
+  int32_t syn_packed;      /* chosen synthesis variant bits */
+  int32_t dct_ctas_per_sm; /* chosen spectral grid (0 = all resident) */
+  int32_t from_cache;      /* 1: taken from the in-process or file cache */
+  int32_t candidates;      /* configurations timed (0 when cached) */
+  double ms_default;       /* one iteration of every chain group, default */
+  double ms_best;          /* the same with the chosen variants */
+} muffin_tune_info;
+
+/* Times each candidate configuration on this plan's own buffers (a few
+ * iterations of every chain group it advances: two groups of three chains
+ * with sure = 1, one plain group otherwise), keeps the fastest and caches it
+ * per shape (n, bands, batch, chains, levels, bases, SM count, device name):
+ * in process, and in the text file `cache_path` when it is not NULL (read
+ * first, one line appended per new shape; lines that do not parse are
+ * ignored).  The timing iterations overwrite the plan's iterate state: a
+ * following solve or sure_tune must start cold (warm = 0; a warm call
+ * returns MUFFIN_ESTATE), and captured graphs are rebuilt.  info may be NULL.
+ * Errors: EINVAL (plan NULL), ECUDA. */
+MUFFIN_API muffin_status muffin_plan_autotune(muffin_plan plan, const char *cache_path,
+                                              muffin_tune_info *info);
+
+/* Sets the variants directly (syn_packed in 0..3, dct_ctas_per_sm >= 0);
+ * drops captured graphs.  Errors: EINVAL. */
+MUFFIN_API muffin_status muffin_plan_set_tuning(muffin_plan plan, int32_t syn_packed,
+                                                int32_t dct_ctas_per_sm);
+
 typedef struct {
   int32_t iters_done; /* iterations run by this call */
   double tau;         /* primal step used (last window for ADA-PT) */

@@ -9,6 +9,7 @@ cubes are float32 ``[L, n, n]``.
 from __future__ import annotations
 
 import ctypes
+import os
 
 import numpy as np
 
@@ -128,6 +129,18 @@ class Plan:
 
     def graphs(self, on: bool = True) -> None:
         native.check(self._lib.muffin_plan_graphs(self._h, int(on)))
+
+    def autotune(self, cache: str | None = None) -> native.TuneInfo:
+        """Pick the fastest launch variants for this shape (results do not
+        change); the next solve must start cold."""
+        info = native.TuneInfo()
+        path = None if cache is None else os.fsencode(cache)
+        native.check(self._lib.muffin_plan_autotune(self._h, path, ctypes.byref(info)))
+        return info
+
+    def set_tuning(self, syn_packed: int = 0, dct_ctas_per_sm: int = 0) -> None:
+        native.check(self._lib.muffin_plan_set_tuning(self._h, int(syn_packed),
+                                                      int(dct_ctas_per_sm)))
 
     # -- solvers
     def solve(self, dirty, x, iters: int, mu, gamma, warm: bool = False) -> native.Info:

@@ -56,6 +56,7 @@ __device__ __forceinline__ void cp_wait0() {
 
 struct DctKArgs {
   int n, L, Lp, inverse;
+  int ctas_per_sm;            // persistent grid size (0: max resident)
   int B;                      // cubes; blockIdx.y selects the cube
   const float *a1hi, *a1lo;   // first product: C (or C^T for the inverse operator)
   const float *a2hi, *a2lo;   // second product: C^T
@@ -444,7 +445,8 @@ cudaError_t launch_dct_small(const DctKArgs &a, cudaStream_t st, Prof *prof) {
   }
   const size_t N = (size_t)a.n * a.n;
   const size_t ntiles = ((N + PT - 1) / PT) * (size_t)a.B;
-  const size_t grid = std::min(ntiles, (size_t)per_sm * (size_t)sms);
+  const int use = a.ctas_per_sm > 0 ? std::min(a.ctas_per_sm, per_sm) : per_sm;
+  const size_t grid = std::min(ntiles, (size_t)use * (size_t)sms);
   const double vox = (double)N * a.L * a.B;
   ProfScope ps(prof, "spectral_dual", CH * vox * 20.0, 2.0 * CH * 2.0 * a.L * vox, st);
   k_dct_small<CH, PT><<<(unsigned)grid, DT, sm, st>>>(a);
@@ -483,7 +485,7 @@ cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st) {
   DctKArgs a{};
   a.n = d.n; a.L = d.L; a.Lp = d.Lp; a.B = d.B > 0 ? d.B : 1;
   a.a1hi = d.chi; a.a1lo = d.clo; a.a2hi = d.cthi; a.a2lo = d.ctlo;
-  a.alpha = d.alpha; a.sc = d.sc;
+  a.alpha = d.alpha; a.sc = d.sc; a.ctas_per_sm = d.ctas_per_sm;
   a.xt = gr.xt; a.x = gr.x; a.v = gr.v; a.t = gr.t;
   if (d.Lp <= 64) {
     if (gr.C == 3) return launch_dct_small<3>(a, st, d.prof);

@@ -180,6 +180,8 @@ struct WaveArgs {
   float *scratch;          // LL scratch: level j (1 <= j < J) holds
                            // [C][L][K][n>>j][n>>j] at scratch + lvl_off[j]
   size_t lvl_off[16];
+  int syn_packed;          // synthesis variant: bit 0 coarse levels, bit 1
+                           // level 1 (0 scalar row pass, 1 packed row pairs)
   Prof *prof;              // optional per-kernel timing
 };
 
@@ -205,6 +207,7 @@ struct DctArgs {
   const float *cthi, *ctlo;// [Lp][Lp] C^T split
   const float *alpha;      // [B][n*n] pixel weights
   const DevScalars *sc;    // [B]
+  int ctas_per_sm;         // persistent spectral grid: CTAs per SM (0: max resident)
   Prof *prof;              // optional per-kernel timing
 };
 // Spectral dual update and back-projection (Alg. 2 eqs. vt, v, upt and the

@@ -387,6 +387,22 @@ muffin_status enter(muffin_plan P) {
   return MUFFIN_OK;
 }
 
+muffin_status iterate_all(muffin_plan P) {
+  muffin_status s = iterate_group(P, P->grp[0]);
+  if (s == MUFFIN_OK && P->p.sure) s = iterate_group(P, P->grp[1]);
+  return s;
+}
+
+void drop_graphs_and_state(muffin_plan P) {
+  for (auto &kv : P->gplain) cudaGraphExecDestroy(kv.second);
+  P->gplain.clear();
+  for (int i = 0; i < 2; ++i)
+    if (P->gsure[i]) { cudaGraphExecDestroy(P->gsure[i]); P->gsure[i] = nullptr; }
+  P->have_state = false;
+  P->have_sure_state = false;
+  P->k_done = 0;
+}
+
 muffin_status leave(muffin_plan P, bool sync) {
   CK(cudaEventRecord(P->ev_out, P->ws));
   CK(cudaStreamWaitEvent(P->st, P->ev_out, 0));

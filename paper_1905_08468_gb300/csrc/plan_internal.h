@@ -69,6 +69,8 @@ struct muffin_plan_s {
   muffin::Prof prof;
   bool profiling = false;
   bool use_graphs = true;
+  int syn_packed = 0;     // synthesis variant bits (see WaveArgs::syn_packed)
+  int dct_ctas = 0;       // spectral kernel CTAs per SM (0: all resident)
   std::map<std::pair<int, int>, cudaGraphExec_t> gplain;   // (parity, cubes)
   cudaGraphExec_t gsure[2] = {nullptr, nullptr};
   int gsure_window = 0, gsure_reset = -1;
@@ -105,6 +107,7 @@ struct muffin_plan_s {
     w.n = n; w.L = Lt; w.Lc = L; w.K = K; w.J = J; w.C = C;
     w.beta = beta; w.sc = sc; w.scratch = llscr;
     for (int j = 0; j < 16; ++j) w.lvl_off[j] = lvl_off[j];
+    w.syn_packed = syn_packed;
     w.prof = pp();
     return w;
   }
@@ -113,6 +116,7 @@ struct muffin_plan_s {
     d.n = n; d.L = L; d.Lp = Lp; d.C = C; d.B = B;
     d.chi = chi; d.clo = clo; d.cthi = cthi; d.ctlo = ctlo;
     d.alpha = alpha; d.sc = sc;
+    d.ctas_per_sm = dct_ctas;
     d.prof = pp();
     return d;
   }
@@ -141,6 +145,12 @@ muffin_status fetch_x(muffin_plan P, int b0, int b1, float *dst);
 // order the work stream after the caller's stream / the caller's after it
 muffin_status enter(muffin_plan P);
 muffin_status leave(muffin_plan P, bool sync);
+// one iteration of every chain group the plan advances (work stream, direct
+// launches); used by the tuner
+muffin_status iterate_all(muffin_plan P);
+// destroy the captured graphs (they bake in kernel variants) and forget the
+// iterate state, so the next solve starts cold
+void drop_graphs_and_state(muffin_plan P);
 
 }  // namespace pi
 }  // namespace muffin

@@ -1,0 +1,207 @@
+// Per-shape choice of launch variants for the hot kernels (the wavelet
+// synthesis row pass and the persistent spectral kernel's grid).  Every
+// variant yields identical results; only speed differs, and it depends on
+// the cube shape and the GPU, so the plan times the candidates on its own
+// buffers and caches the winner per shape, in process and optionally in a
+// text file.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "plan_internal.h"
+
+namespace {
+
+using muffin::fail;
+
+struct Choice {
+  int syn_packed = 0;
+  int dct_ctas = 0;
+};
+
+std::mutex g_mu;
+std::map<std::string, Choice> g_cache;
+
+std::string shape_key(muffin_plan P) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, dev);
+  std::string name(prop.name);
+  for (char &ch : name)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  char buf[256];
+  std::snprintf(buf, sizeof buf, "n=%d,L=%d,B=%d,C=%d,J=%d,K=%d,sure=%d,sm=%d,dev=%s", P->n,
+                P->L, P->B, P->Cmax, P->J, P->K, P->p.sure ? 1 : 0, sms, name.c_str());
+  return buf;
+}
+
+// the last line "muffin-tune-1 <key> <syn_packed> <dct_ctas>" with this key
+bool file_lookup(const char *path, const std::string &key, Choice *c) {
+  FILE *f = std::fopen(path, "r");
+  if (!f) return false;
+  char line[512], tag[32], k[400];
+  bool found = false;
+  while (std::fgets(line, sizeof line, f)) {
+    int a = 0, b = 0;
+    if (std::sscanf(line, "%31s %399s %d %d", tag, k, &a, &b) != 4) continue;
+    if (std::strcmp(tag, "muffin-tune-1") != 0 || key != k) continue;
+    if (a < 0 || a > 3 || b < 0) continue;
+    c->syn_packed = a;
+    c->dct_ctas = b;
+    found = true;
+  }
+  std::fclose(f);
+  return found;
+}
+
+void file_append(const char *path, const std::string &key, const Choice &c) {
+  FILE *f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "muffin-tune-1 %s %d %d\n", key.c_str(), c.syn_packed, c.dct_ctas);
+  std::fclose(f);
+}
+
+void apply(muffin_plan P, const Choice &c) {
+  P->syn_packed = c.syn_packed;
+  P->dct_ctas = c.dct_ctas;
+}
+
+// mean time of one iteration of every chain group with choice c
+muffin_status time_choice(muffin_plan P, const Choice &c, int reps, cudaEvent_t e0,
+                          cudaEvent_t e1, double *ms) {
+  apply(P, c);
+  for (int w = 0; w < 2; ++w) {
+    muffin_status s = muffin::pi::iterate_all(P);
+    if (s != MUFFIN_OK) return s;
+  }
+  MUFFIN_CK(cudaEventRecord(e0, P->ws));
+  for (int r = 0; r < reps; ++r) {
+    muffin_status s = muffin::pi::iterate_all(P);
+    if (s != MUFFIN_OK) return s;
+  }
+  MUFFIN_CK(cudaEventRecord(e1, P->ws));
+  MUFFIN_CK(cudaEventSynchronize(e1));
+  float t = 0.f;
+  MUFFIN_CK(cudaEventElapsedTime(&t, e0, e1));
+  *ms = t / reps;
+  return MUFFIN_OK;
+}
+
+muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MUFFIN_CK(cudaEventCreate(&e0));
+  cudaError_t ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(MUFFIN_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(ce));
+  }
+  const bool was_profiling = P->profiling;
+  P->profiling = false;
+  muffin_status s = muffin::pi::enter(P);
+  // about 3 repetitions per candidate above a million voxels, more below
+  const double vox = (double)P->NL * P->Cmax * (P->p.sure ? 2 : 1);
+  const int reps = vox >= 2e7 ? 3 : (vox >= 1e6 ? 5 : 10);
+  Choice cur{};
+  double t_def = 0.0, t_best = 0.0;
+  int cand = 0;
+  if (s == MUFFIN_OK) s = time_choice(P, cur, reps, e0, e1, &t_def);
+  t_best = t_def;
+  *best = cur;
+  ++cand;
+  // coordinate search: synthesis variants, then the spectral grid
+  for (int v = 1; v <= 3 && s == MUFFIN_OK; ++v) {
+    Choice c = *best;
+    c.syn_packed = v;
+    double t = 0.0;
+    s = time_choice(P, c, reps, e0, e1, &t);
+    ++cand;
+    if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
+  }
+  for (int k = 1; k <= 2 && s == MUFFIN_OK; ++k) {
+    Choice c = *best;
+    c.dct_ctas = k;
+    double t = 0.0;
+    s = time_choice(P, c, reps, e0, e1, &t);
+    ++cand;
+    if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
+  }
+  if (s == MUFFIN_OK) s = muffin::pi::leave(P, true);
+  P->profiling = was_profiling;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != MUFFIN_OK) return s;
+  if (info) {
+    info->candidates = cand;
+    info->ms_default = t_def;
+    info->ms_best = t_best;
+  }
+  return MUFFIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+muffin_status muffin_plan_set_tuning(muffin_plan P, int32_t syn_packed, int32_t dct_ctas_per_sm) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  if (syn_packed < 0 || syn_packed > 3)
+    return fail(MUFFIN_EINVAL, "syn_packed must be in 0..3 (got %d)", syn_packed);
+  if (dct_ctas_per_sm < 0)
+    return fail(MUFFIN_EINVAL, "dct_ctas_per_sm must be >= 0 (got %d)", dct_ctas_per_sm);
+  muffin::pi::drop_graphs_and_state(P);
+  P->syn_packed = syn_packed;
+  P->dct_ctas = dct_ctas_per_sm;
+  return MUFFIN_OK;
+}
+
+muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin_tune_info *info) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  const std::string key = shape_key(P);
+  Choice c;
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) { c = it->second; cached = true; }
+  }
+  if (!cached && cache_path && file_lookup(cache_path, key, &c)) {
+    cached = true;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache[key] = c;
+  }
+  if (info) std::memset(info, 0, sizeof *info);
+  if (cached) {
+    muffin::pi::drop_graphs_and_state(P);
+    apply(P, c);
+    if (info) {
+      info->syn_packed = c.syn_packed;
+      info->dct_ctas_per_sm = c.dct_ctas;
+      info->from_cache = 1;
+    }
+    return MUFFIN_OK;
+  }
+  muffin::pi::drop_graphs_and_state(P);
+  muffin_status s = tune(P, &c, info);
+  muffin::pi::drop_graphs_and_state(P);
+  if (s != MUFFIN_OK) return s;
+  apply(P, c);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache[key] = c;
+  }
+  if (cache_path) file_append(cache_path, key, c);
+  if (info) {
+    info->syn_packed = c.syn_packed;
+    info->dct_ctas_per_sm = c.dct_ctas;
+    info->from_cache = 0;
+  }
+  return MUFFIN_OK;
+}
+
+}  // extern "C"

@@ -21,10 +21,10 @@
 // The analysis filters run on packed pairs (fma.rn.f32x2): the row pass
 // filters two image rows at once (the tile is stored as row pairs) and the
 // column pass splits each output into its even- and odd-tap halves.  The
-// synthesis keeps scalar FMAs: a packed form needs each coefficient twice in
-// shared memory, and the doubled shared-memory traffic costs more than the
-// halved FMA issue saves.  Filters live in constant memory and every pass
-// keeps a sliding window of taps' inputs in registers.
+// synthesis column pass is scalar (its inputs arrive by cp.async in the
+// coefficient layout) and stores row pairs, so the synthesis row pass is
+// packed too.  Filters live in constant memory and every pass keeps a
+// sliding window of taps' inputs in registers.
 //
 // Chains: a launch advances C = 1 (plain) or C = 3 chains {x, dx/dmu,
 // dx/dgamma} of one ADA-PT group.  The derivative channels use the masks of
@@ -62,14 +62,15 @@ constexpr int QX = 4, QY = 2;                        // outputs per thread
 constexpr int S_HALO = 8;
 constexpr int S_CH = TY + S_HALO;                    // coefficient rows held
 constexpr int S_CP = TX + S_HALO;                    // coefficient pitch (x4 aligned)
-constexpr int S_LP = (TX + PMAX - 1) | 1;            // column-pass output pitch
-constexpr int QXP = 4, QYP = 2;                      // coefficient pairs per thread
+constexpr int S_LP = (TX + PMAX - 1) | 1;            // column-pass output pitch (float2)
+constexpr int QXP = 2, QYP = 2;                      // coefficient positions per thread
+constexpr int QXS = 4;                               // scalar synthesis row item
 
 constexpr size_t ana_smem(int ch) {
   return ((size_t)ch * A_RP * A_IP + 4 * A_RP * A_LP) * sizeof(float2);
 }
 constexpr size_t syn_smem(int) {
-  return (size_t)(8 * S_CH * S_CP + 2 * (2 * TY) * S_LP) * sizeof(float);
+  return (size_t)(8 * S_CH * S_CP) * sizeof(float) + (size_t)(2 * TY * S_LP) * sizeof(float2);
 }
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
@@ -440,10 +441,85 @@ __device__ __forceinline__ void syn_issue(const SynArgs &a, float *cf, int l,
   }
 }
 
-// one step: column pass into lo/hi, then the thread's row item -> o[8]
+// one step: column pass into lo/hi, then the thread's row item -> o.
+// Column pass (scalar): item = (column, QYP coefficient rows) -> lo/hi of
+// the four pixel rows 4j .. 4j+3, stored as row pairs (4j+e, 4j+2+e) so the
+// row pass can filter two rows with one packed FMA: (x_r, x_r+2) +=
+// (h_i, h_i) * (lo_r, lo_r+2).  The thread's row item is row pair `rp` and
+// QXP coefficient positions: o[qq][e] = pixels 2k+e of rows (r, r+2).
 template <int P>
-__device__ __forceinline__ void syn_step(const float *cf, float *lo_s, float *hi_s,
-                                         float (&o)[2 * QXP]) {
+__device__ __forceinline__ void syn_step_p(const float *cf, float2 *lo_s, float2 *hi_s,
+                                           float2 (&o)[QXP][2]) {
+  constexpr int NCOL = TX + P - 1;
+  constexpr int NSY = TY / QYP;
+  constexpr int NWC = QYP + P - 1;
+  constexpr int OFF = S_HALO - (P - 1);     // window offset of this basis' halo
+  static_assert(QYP == 2, "a column item covers one row-pair group");
+  for (int it = threadIdx.x; it < NSY * NCOL; it += NT) {
+    const int kc = it % NCOL, sy = it / NCOL;
+    const int base = (QYP * sy + OFF) * S_CP + kc + OFF;
+    float vLL[NWC], vDY[NWC], vDX[NWC], vHH[NWC];
+#pragma unroll
+    for (int i = 0; i < NWC; ++i) {
+      vLL[i] = cf[base + i * S_CP];
+      vDY[i] = cf[SUB + base + i * S_CP];
+      vDX[i] = cf[2 * SUB + base + i * S_CP];
+      vHH[i] = cf[3 * SUB + base + i * S_CP];
+    }
+    float lo[QYP][2], hi[QYP][2];
+#pragma unroll
+    for (int qq = 0; qq < QYP; ++qq) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        float vl = 0.f, vh = 0.f;
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+          const int ci = qq + P - 1 - s;
+          vl = fmaf(c_h[P - 1][2 * s + e], vLL[ci], vl);
+          vl = fmaf(c_g[P - 1][2 * s + e], vDY[ci], vl);
+          vh = fmaf(c_h[P - 1][2 * s + e], vDX[ci], vh);
+          vh = fmaf(c_g[P - 1][2 * s + e], vHH[ci], vh);
+        }
+        lo[qq][e] = vl;
+        hi[qq][e] = vh;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      lo_s[(2 * sy + e) * S_LP + kc] = make_float2(lo[0][e], lo[1][e]);
+      hi_s[(2 * sy + e) * S_LP + kc] = make_float2(hi[0][e], hi[1][e]);
+    }
+  }
+  __syncthreads();
+  constexpr int NWR = QXP + P - 1;
+  const int rp = threadIdx.x % TY, sx = threadIdx.x / TY;
+  const float2 *pl = lo_s + rp * S_LP + QXP * sx;
+  const float2 *ph = hi_s + rp * S_LP + QXP * sx;
+  float2 vl[NWR], vh[NWR];
+#pragma unroll
+  for (int i = 0; i < NWR; ++i) { vl[i] = pl[i]; vh[i] = ph[i]; }
+#pragma unroll
+  for (int qq = 0; qq < QXP; ++qq) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int s = 0; s < P; ++s) {
+        const int ci = qq + P - 1 - s;
+        v = ffma2(c_hh[P - 1][2 * s + e], vl[ci], v);
+        v = ffma2(c_gg[P - 1][2 * s + e], vh[ci], v);
+      }
+      o[qq][e] = v;
+    }
+  }
+}
+
+// Scalar variant of a step: column pass into lo/hi ([2TY][S_LP] floats),
+// then the thread's row item: one pixel row, QXS coefficient positions.
+template <int P>
+__device__ __forceinline__ void syn_step_s(const float *cf, float *lo_s, float *hi_s,
+                                           float (&o)[1][2 * QXS]) {
+  constexpr int SLP = S_LP;
   constexpr int NCOL = TX + P - 1;
   constexpr int NSY = TY / QYP;
   constexpr int NWC = QYP + P - 1;
@@ -473,21 +549,22 @@ __device__ __forceinline__ void syn_step(const float *cf, float *lo_s, float *hi
           hi = fmaf(c_g[P - 1][2 * s + e], vHH[ci], hi);
         }
         const int my = 2 * (QYP * sy + qq) + e;
-        lo_s[my * S_LP + kc] = lo;
-        hi_s[my * S_LP + kc] = hi;
+        lo_s[my * SLP + kc] = lo;
+        hi_s[my * SLP + kc] = hi;
       }
     }
   }
   __syncthreads();
-  constexpr int NWR = QXP + P - 1;
-  const int sx = threadIdx.x % (TX / QXP), my = threadIdx.x / (TX / QXP);
-  const float *pl = lo_s + my * S_LP + QXP * sx;
-  const float *ph = hi_s + my * S_LP + QXP * sx;
+  constexpr int NWR = QXS + P - 1;
+  const int sx = threadIdx.x % (TX / QXS), my = threadIdx.x / (TX / QXS);
+  static_assert((TX / QXS) * 2 * TY == NT, "one row item per thread");
+  const float *pl = lo_s + my * SLP + QXS * sx;
+  const float *ph = hi_s + my * SLP + QXS * sx;
   float vl[NWR], vh[NWR];
 #pragma unroll
   for (int i = 0; i < NWR; ++i) { vl[i] = pl[i]; vh[i] = ph[i]; }
 #pragma unroll
-  for (int qq = 0; qq < QXP; ++qq) {
+  for (int qq = 0; qq < QXS; ++qq) {
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       float v = 0.f;
@@ -497,43 +574,78 @@ __device__ __forceinline__ void syn_step(const float *cf, float *lo_s, float *hi
         v = fmaf(c_h[P - 1][2 * s + e], vl[ci], v);
         v = fmaf(c_g[P - 1][2 * s + e], vh[ci], v);
       }
-      o[2 * qq + e] = v;
+      o[0][2 * qq + e] = v;
     }
   }
 }
 
-__device__ __forceinline__ void syn_dispatch(int p, const float *cf, float *lo_s,
-                                             float *hi_s, float (&o)[2 * QXP]) {
-  switch (p) {
-    case 1: syn_step<1>(cf, lo_s, hi_s, o); break;
-    case 2: syn_step<2>(cf, lo_s, hi_s, o); break;
-    case 3: syn_step<3>(cf, lo_s, hi_s, o); break;
-    case 4: syn_step<4>(cf, lo_s, hi_s, o); break;
-    case 5: syn_step<5>(cf, lo_s, hi_s, o); break;
-    case 6: syn_step<6>(cf, lo_s, hi_s, o); break;
-    case 7: syn_step<7>(cf, lo_s, hi_s, o); break;
-    default: syn_step<8>(cf, lo_s, hi_s, o); break;
+// o[ROWS][NO]: the thread's pixels of this step (see k_syn)
+template <bool PACKED>
+__device__ __forceinline__ void syn_dispatch(int p, const float *cf, float *lo,
+                                             float (&o)[PACKED ? 2 : 1][PACKED ? 2 * QXP : 2 * QXS]) {
+  if constexpr (PACKED) {
+    float2 *lo_s = reinterpret_cast<float2 *>(lo), *hi_s = lo_s + TY * S_LP;
+    float2 op[QXP][2];
+    switch (p) {
+      case 1: syn_step_p<1>(cf, lo_s, hi_s, op); break;
+      case 2: syn_step_p<2>(cf, lo_s, hi_s, op); break;
+      case 3: syn_step_p<3>(cf, lo_s, hi_s, op); break;
+      case 4: syn_step_p<4>(cf, lo_s, hi_s, op); break;
+      case 5: syn_step_p<5>(cf, lo_s, hi_s, op); break;
+      case 6: syn_step_p<6>(cf, lo_s, hi_s, op); break;
+      case 7: syn_step_p<7>(cf, lo_s, hi_s, op); break;
+      default: syn_step_p<8>(cf, lo_s, hi_s, op); break;
+    }
+#pragma unroll
+    for (int qq = 0; qq < QXP; ++qq)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) { o[0][2 * qq + e] = op[qq][e].x; o[1][2 * qq + e] = op[qq][e].y; }
+  } else {
+    float *lo_s = lo, *hi_s = lo + 2 * TY * S_LP;
+    switch (p) {
+      case 1: syn_step_s<1>(cf, lo_s, hi_s, o); break;
+      case 2: syn_step_s<2>(cf, lo_s, hi_s, o); break;
+      case 3: syn_step_s<3>(cf, lo_s, hi_s, o); break;
+      case 4: syn_step_s<4>(cf, lo_s, hi_s, o); break;
+      case 5: syn_step_s<5>(cf, lo_s, hi_s, o); break;
+      case 6: syn_step_s<6>(cf, lo_s, hi_s, o); break;
+      case 7: syn_step_s<7>(cf, lo_s, hi_s, o); break;
+      default: syn_step_s<8>(cf, lo_s, hi_s, o); break;
+    }
   }
 }
 
-template <int CH, int MODE, bool LEVEL1>
+// PACKED = false: each thread owns one pixel row and 2 QXS pixels;
+// PACKED = true: rows r and r + 2 (row pair rp) and 2 QXP pixels each.
+// Both variants compute the same sums in the same order (identical results);
+// which is faster depends on the shape, so the plan's tuner picks one.
+template <int CH, int MODE, bool LEVEL1, bool PACKED>
 __global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
+  constexpr int ROWS = PACKED ? 2 : 1;   // pixel rows per thread
+  constexpr int NO = PACKED ? 2 * QXP : 2 * QXS;   // pixels per row
   extern __shared__ float smem[];
   float *cf0 = smem;                  // two [4][S_CH][S_CP] buffers
-  float *lo_s = smem + 8 * SUB;       // [2TY][S_LP]
-  float *hi_s = lo_s + 2 * TY * S_LP;
+  float *lo = smem + 8 * SUB;         // lo/hi of the column pass
   const int h = a.M >> 1;
   const int ntx = (h + TX - 1) / TX;
   const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
   const int l = blockIdx.y;
   const float mu = (MODE == WAVE_ITERATE) ? (float)a.sc[l / a.Lc].mu : 0.f;
-  const int sx = threadIdx.x % (TX / QXP), my = threadIdx.x / (TX / QXP);
-  const int yy = 2 * ky0 + my, xx0 = 2 * kx0 + 2 * QXP * sx;
-  float acc[CH][2 * QXP];
+  int r0, dr, xx0;
+  if (PACKED) {
+    const int rp = threadIdx.x % TY, sx = threadIdx.x / TY;
+    r0 = 4 * (rp >> 1) + (rp & 1); dr = 2; xx0 = 2 * kx0 + NO * sx;
+  } else {
+    const int sx = threadIdx.x % (TX / QXS), my = threadIdx.x / (TX / QXS);
+    r0 = my; dr = 0; xx0 = 2 * kx0 + NO * sx;
+  }
+  float acc[CH][ROWS][NO];
 #pragma unroll
   for (int c = 0; c < CH; ++c)
 #pragma unroll
-    for (int e = 0; e < 2 * QXP; ++e) acc[c][e] = 0.f;
+    for (int j = 0; j < ROWS; ++j)
+#pragma unroll
+      for (int e = 0; e < NO; ++e) acc[c][j][e] = 0.f;
   // (basis, chain) steps; coarser levels write each basis' LL_{j-1}
   const int nsteps = a.K * CH;
   syn_issue(a, cf0, l, 0, 0, kx0, ky0);
@@ -549,100 +661,119 @@ __global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
       cp_wait<0>();
     }
     __syncthreads();
-    float o[2 * QXP];
-    syn_dispatch(bb + 1, cf, lo_s, hi_s, o);
+    float o[ROWS][NO];
+    syn_dispatch<PACKED>(bb + 1, cf, lo, o);
     if (LEVEL1) {
 #pragma unroll
-      for (int e = 0; e < 2 * QXP; ++e) {
-        if (CH == 3) {
-          if (c == 0) { acc[0][e] += o[e]; acc[1][e] += o[e]; }
-          else if (c == 1) acc[1][e] = fmaf(mu, o[e], acc[1][e]);
-          else acc[2][e] += o[e];
-        } else {
-          acc[0][e] += o[e];
-        }
-      }
-    } else if (yy < a.M) {
-      float *dst = a.ll_out + (((size_t)(c * a.L + l) * a.K + bb) * a.M + yy) * a.M + xx0;
-      if (xx0 + 2 * QXP <= a.M && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-        *reinterpret_cast<float4 *>(dst) = make_float4(o[0], o[1], o[2], o[3]);
-        *reinterpret_cast<float4 *>(dst + 4) = make_float4(o[4], o[5], o[6], o[7]);
-      } else {
+      for (int j = 0; j < ROWS; ++j)
 #pragma unroll
-        for (int e = 0; e < 2 * QXP; ++e)
-          if (xx0 + e < a.M) dst[e] = o[e];
+        for (int e = 0; e < NO; ++e) {
+          if (CH == 3) {
+            if (c == 0) { acc[0][j][e] += o[j][e]; acc[1][j][e] += o[j][e]; }
+            else if (c == 1) acc[1][j][e] = fmaf(mu, o[j][e], acc[1][j][e]);
+            else acc[2][j][e] += o[j][e];
+          } else {
+            acc[0][j][e] += o[j][e];
+          }
+        }
+    } else {
+#pragma unroll
+      for (int j = 0; j < ROWS; ++j) {
+        const int yy = 2 * ky0 + r0 + dr * j;
+        if (yy >= a.M) continue;
+        float *dst = a.ll_out + (((size_t)(c * a.L + l) * a.K + bb) * a.M + yy) * a.M + xx0;
+        if (xx0 + NO <= a.M && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+          for (int q = 0; q < NO; q += 4)
+            *reinterpret_cast<float4 *>(dst + q) =
+                make_float4(o[j][q], o[j][q + 1], o[j][q + 2], o[j][q + 3]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < NO; ++e)
+            if (xx0 + e < a.M) dst[e] = o[j][e];
+        }
       }
     }
     __syncthreads();
   }
-  if (!LEVEL1 || yy >= a.M) return;
+  if (!LEVEL1 || xx0 >= a.n) return;
   const size_t NN = (size_t)a.n * a.n;
-  const size_t row = (size_t)l * NN + (size_t)yy * a.n;
   if (MODE == WAVE_TRANSFORM) {
-    float *dst = a.out + row + xx0;
-    if (xx0 + 2 * QXP <= a.n && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-      *reinterpret_cast<float4 *>(dst) = make_float4(acc[0][0], acc[0][1], acc[0][2], acc[0][3]);
-      *reinterpret_cast<float4 *>(dst + 4) = make_float4(acc[0][4], acc[0][5], acc[0][6], acc[0][7]);
-    } else {
 #pragma unroll
-      for (int e = 0; e < 2 * QXP; ++e)
-        if (xx0 + e < a.n) dst[e] = acc[0][e];
+    for (int j = 0; j < ROWS; ++j) {
+      const int yy = 2 * ky0 + r0 + dr * j;
+      if (yy >= a.n) continue;
+      float *dst = a.out + (size_t)l * NN + (size_t)yy * a.n + xx0;
+      if (xx0 + NO <= a.n && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+        for (int q = 0; q < NO; q += 4)
+          *reinterpret_cast<float4 *>(dst + q) =
+              make_float4(acc[0][j][q], acc[0][j][q + 1], acc[0][j][q + 2], acc[0][j][q + 3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < NO; ++e)
+          if (xx0 + e < a.n) dst[e] = acc[0][j][e];
+      }
     }
     return;
   }
   const float tau = (float)a.sc[l / a.Lc].tau;
   const float bl = a.beta[l];
   const size_t CS = (size_t)a.L * NN;
-  if (xx0 >= a.n) return;
-  // vector path: the thread's 8 pixels are inside the row and 32-byte aligned
-  const bool vec = (a.n & 7) == 0 && xx0 + 2 * QXP <= a.n;
-  // chains in order; each loads its x, grad, t first, then stores x-tilde
-  uint32_t keep = 0;
+  // vector path: the thread's NO pixels of a row are inside it and aligned
+  const bool vec = (a.n % NO) == 0 && xx0 + NO <= a.n;
 #pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    const float sc = (CH == 3 && c == 1) ? bl : bl * mu;   // mu_l, beta_l, mu_l
-    const size_t i0 = row + xx0 + c * CS;
-    float xv[2 * QXP], gv[2 * QXP], tv[2 * QXP];
-    if (vec) {
+  for (int j = 0; j < ROWS; ++j) {
+    const int yy = 2 * ky0 + r0 + dr * j;
+    if (yy >= a.n) continue;
+    const size_t row = (size_t)l * NN + (size_t)yy * a.n;
+    // chains in order; each loads its x, grad, t first, then stores x-tilde
+    uint32_t keep = 0;
 #pragma unroll
-      for (int h4 = 0; h4 < 2 * QXP; h4 += 4) {
-        const float4 x4 = *reinterpret_cast<const float4 *>(a.x + i0 + h4);
-        const float4 g4 = *reinterpret_cast<const float4 *>(a.g + i0 + h4);
-        const float4 t4 = *reinterpret_cast<const float4 *>(a.t + i0 + h4);
-        xv[h4] = x4.x; xv[h4 + 1] = x4.y; xv[h4 + 2] = x4.z; xv[h4 + 3] = x4.w;
-        gv[h4] = g4.x; gv[h4 + 1] = g4.y; gv[h4 + 2] = g4.z; gv[h4 + 3] = g4.w;
-        tv[h4] = t4.x; tv[h4 + 1] = t4.y; tv[h4 + 2] = t4.z; tv[h4 + 3] = t4.w;
-      }
-    } else {
+    for (int c = 0; c < CH; ++c) {
+      const float sc = (CH == 3 && c == 1) ? bl : bl * mu;   // mu_l, beta_l, mu_l
+      const size_t i0 = row + xx0 + c * CS;
+      float xv[NO], gv[NO], tv[NO];
+      if (vec) {
 #pragma unroll
-      for (int e = 0; e < 2 * QXP; ++e) {
-        const bool ok = xx0 + e < a.n;
-        xv[e] = ok ? a.x[i0 + e] : 0.f;
-        gv[e] = ok ? a.g[i0 + e] : 0.f;
-        tv[e] = ok ? a.t[i0 + e] : 0.f;
-      }
-    }
-    float o[2 * QXP];
-#pragma unroll
-    for (int e = 0; e < 2 * QXP; ++e) {
-      const float m = xv[e] - tau * (gv[e] + sc * acc[c][e] + tv[e]);
-      if (c == 0) {
-        const bool k = !a.positivity || m > 0.f;
-        if (k) keep |= 1u << e;
-        o[e] = k ? m : 0.f;
+        for (int q = 0; q < NO; q += 4) {
+          const float4 x4 = *reinterpret_cast<const float4 *>(a.x + i0 + q);
+          const float4 g4 = *reinterpret_cast<const float4 *>(a.g + i0 + q);
+          const float4 t4 = *reinterpret_cast<const float4 *>(a.t + i0 + q);
+          xv[q] = x4.x; xv[q + 1] = x4.y; xv[q + 2] = x4.z; xv[q + 3] = x4.w;
+          gv[q] = g4.x; gv[q + 1] = g4.y; gv[q + 2] = g4.z; gv[q + 3] = g4.w;
+          tv[q] = t4.x; tv[q + 1] = t4.y; tv[q + 2] = t4.z; tv[q + 3] = t4.w;
+        }
       } else {
-        o[e] = (keep >> e) & 1u ? m : 0.f;
+#pragma unroll
+        for (int e = 0; e < NO; ++e) {
+          const bool ok = xx0 + e < a.n;
+          xv[e] = ok ? a.x[i0 + e] : 0.f;
+          gv[e] = ok ? a.g[i0 + e] : 0.f;
+          tv[e] = ok ? a.t[i0 + e] : 0.f;
+        }
       }
-    }
-    if (vec) {
+      float o[NO];
 #pragma unroll
-      for (int h4 = 0; h4 < 2 * QXP; h4 += 4)
-        *reinterpret_cast<float4 *>(a.xt + i0 + h4) =
-            make_float4(o[h4], o[h4 + 1], o[h4 + 2], o[h4 + 3]);
-    } else {
+      for (int e = 0; e < NO; ++e) {
+        const float m = xv[e] - tau * (gv[e] + sc * acc[c][j][e] + tv[e]);
+        if (c == 0) {
+          const bool k = !a.positivity || m > 0.f;
+          if (k) keep |= 1u << e;
+          o[e] = k ? m : 0.f;
+        } else {
+          o[e] = (keep >> e) & 1u ? m : 0.f;
+        }
+      }
+      if (vec) {
 #pragma unroll
-      for (int e = 0; e < 2 * QXP; ++e)
-        if (xx0 + e < a.n) a.xt[i0 + e] = o[e];
+        for (int q = 0; q < NO; q += 4)
+          *reinterpret_cast<float4 *>(a.xt + i0 + q) = make_float4(o[q], o[q + 1], o[q + 2], o[q + 3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < NO; ++e)
+          if (xx0 + e < a.n) a.xt[i0 + e] = o[e];
+      }
     }
   }
 }
@@ -739,22 +870,28 @@ cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st, Prof *prof
   return cudaGetLastError();
 }
 
+template <int CH, int MODE, bool L1, bool PACKED>
+cudaError_t launch_syn_v(const SynArgs &a, int nblk_y, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_syn<CH, MODE, L1, PACKED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)syn_smem(CH));
+    attr = true;
+  }
+  k_syn<CH, MODE, L1, PACKED><<<dim3(tiles(a.M >> 1), nblk_y), NT, syn_smem(CH), st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int CH, int MODE, bool L1>
-cudaError_t launch_syn(const SynArgs &a, int nblk_y, cudaStream_t st, Prof *prof) {
+cudaError_t launch_syn(const SynArgs &a, int nblk_y, int packed, cudaStream_t st, Prof *prof) {
   const double h = a.M >> 1;
   const double det = (double)CH * a.L * a.K * 4.0 * h * h * 4.0;   // 3 details + LL
   const double out = L1 ? (double)CH * a.L * a.M * a.M * (MODE == WAVE_ITERATE ? 16.0 : 4.0)
                         : (double)CH * a.L * a.K * a.M * a.M * 4.0;
   ProfScope ps(prof, L1 ? "syn_level1_prox" : "syn_level", det + out,
                level_flops(CH, a.L, a.K, (int)h), st);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_syn<CH, MODE, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)syn_smem(CH));
-    attr = true;
-  }
-  k_syn<CH, MODE, L1><<<dim3(tiles(a.M >> 1), nblk_y), NT, syn_smem(CH), st>>>(a);
-  return cudaGetLastError();
+  return packed ? launch_syn_v<CH, MODE, L1, true>(a, nblk_y, st)
+                : launch_syn_v<CH, MODE, L1, false>(a, nblk_y, st);
 }
 
 inline int grid_elem(size_t count) {
@@ -777,14 +914,14 @@ cudaError_t synthesis_all(const WaveArgs &w, const SynArgs &base, cudaStream_t s
     a.top = (j == w.J);
     a.ll_in = a.top ? nullptr : w.scratch + w.lvl_off[j];
     a.ll_out = w.scratch + w.lvl_off[j - 1];
-    e = launch_syn<CH, MODE, false>(a, w.L, st, w.prof);
+    e = launch_syn<CH, MODE, false>(a, w.L, w.syn_packed & 1, st, w.prof);
     if (e != cudaSuccess) return e;
   }
   a.M = w.n;
   a.top = (w.J == 1);
   a.ll_in = a.top ? nullptr : w.scratch + w.lvl_off[1];
   a.ll_out = nullptr;
-  return launch_syn<CH, MODE, true>(a, w.L, st, w.prof);
+  return launch_syn<CH, MODE, true>(a, w.L, (w.syn_packed >> 1) & 1, st, w.prof);
 }
 
 template <int CH, int MODE>

@@ -45,6 +45,12 @@ class ServerParams(ctypes.Structure):
                 ("max_active_voxels", c_size_t)]
 
 
+class TuneInfo(ctypes.Structure):
+    _fields_ = [("syn_packed", c_int32), ("dct_ctas_per_sm", c_int32),
+                ("from_cache", c_int32), ("candidates", c_int32),
+                ("ms_default", c_double), ("ms_best", c_double)]
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64),
                 ("total_ms", c_double), ("bytes_per_launch", c_double),
@@ -69,6 +75,8 @@ SIGNATURES = {
                                      ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                                      c_int32, ctypes.POINTER(Info)]),
     "muffin_plan_graphs": (c_int32, [c_void_p, c_int32]),
+    "muffin_plan_autotune": (c_int32, [c_void_p, ctypes.c_char_p, ctypes.POINTER(TuneInfo)]),
+    "muffin_plan_set_tuning": (c_int32, [c_void_p, c_int32, c_int32]),
     "muffin_sure_params_default": (None, [ctypes.POINTER(SureParams)]),
     "muffin_sure_tune": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p,
                                    ctypes.POINTER(SureParams), c_void_p,

@@ -1,0 +1,102 @@
+"""Per-shape launch tuning: every variant must give bit-identical results,
+the tuner must pick a valid variant, invalidate the iterate state and cache
+its choice (in process and in a text file)."""
+import numpy as np
+import pytest
+
+from synth import fdmc_eps, make_cube
+from tests.gpu_util import cuda, dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(pkg, torch, c, syn, ctas, iters=13):
+    x = torch.zeros((c.L, c.n, c.n), device="cuda")
+    with pkg.Plan(c.n, c.L, c.psf) as p:
+        p.set_tuning(syn, ctas)
+        p.solve(dev(c.dirty, torch), x, iters, 1e-2, 2e-2)
+    return x
+
+
+@pytest.mark.parametrize("n,L", [(64, 8), (16, 20), (128, 64)])
+def test_plain_variants_bit_identical(n, L):
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    c = make_cube(n, L, max(2, n // 4), 1, 30 * n, seed=800 + n)
+    ref = _solve(pkg, torch, c, 0, 0)
+    for syn in range(4):
+        for ctas in (0, 1, 2):
+            if syn == 0 and ctas == 0:
+                continue
+            assert torch.equal(_solve(pkg, torch, c, syn, ctas), ref), (syn, ctas)
+
+
+def test_sure_batch_variants_bit_identical():
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    n, L, B = 32, 4, 2
+    cs = [make_cube(n, L, 8, 1, 900, seed=820 + i) for i in range(B)]
+    nv = np.concatenate([c.noise_var for c in cs])
+    args = dict(window=5, eta=(2e-4, 2e-4), eps=fdmc_eps(nv))
+    psf = np.stack([c.psf for c in cs])
+    d = dev(np.stack([c.dirty for c in cs]), torch)
+    de = dev(np.stack([c.delta for c in cs]), torch)
+    out = []
+    for syn, ctas in [(0, 0), (3, 1), (1, 2), (2, 0)]:
+        x = torch.zeros((B, L, n, n), device="cuda")
+        with pkg.Plan(n, L, psf, sure=True, batch=B) as p:
+            p.set_tuning(syn, ctas)
+            th, tr, _ = p.sure_tune(d, de, nv, x, [(0.05, 0.05), (0.02, 0.08)], 15, **args)
+        out.append((x, th, tr))
+    for x, th, tr in out[1:]:
+        assert torch.equal(x, out[0][0])
+        assert th == out[0][1] and tr == out[0][2]
+
+
+def test_autotune_choice_state_and_file_cache(tmp_path):
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    c = make_cube(64, 8, 16, 1, 1900, seed=840)
+    cache = tmp_path / "tune.txt"
+    ref = _solve(pkg, torch, c, 0, 0)
+    with pkg.Plan(64, 8, c.psf) as p:
+        x = torch.zeros_like(ref)
+        p.solve(dev(c.dirty, torch), x, 3, 1e-2, 2e-2)
+        info = p.autotune(str(cache))
+        assert info.from_cache == 0 and info.candidates == 6
+        assert 0 <= info.syn_packed <= 3 and info.dct_ctas_per_sm >= 0
+        assert 0 < info.ms_best <= info.ms_default
+        # the timing iterations replaced the iterate state: no warm start
+        with pytest.raises(pkg.MuffinError) as e:
+            p.solve(None, x, 2, 1e-2, 2e-2, warm=True)
+        assert e.value.status == 6
+        x = torch.zeros_like(ref)
+        p.solve(dev(c.dirty, torch), x, 13, 1e-2, 2e-2)
+        assert torch.equal(x, ref)
+    lines = [ln.split() for ln in cache.read_text().splitlines()]
+    assert len(lines) == 1 and lines[0][0] == "muffin-tune-1" and "n=64,L=8" in lines[0][1]
+    # the same shape again: in-process cache
+    with pkg.Plan(64, 8, c.psf) as p:
+        again = p.autotune(str(cache))
+        assert again.from_cache == 1 and again.candidates == 0
+        assert (again.syn_packed, again.dct_ctas_per_sm) == (info.syn_packed, info.dct_ctas_per_sm)
+    # a shape only the file knows (written by hand), beside lines to ignore
+    key = lines[0][1].replace("n=64,L=8", "n=16,L=8")
+    cache.write_text("garbage line\nmuffin-tune-1 %s 9 1\nmuffin-tune-1 %s 2 1\n" % (key, key))
+    c16 = make_cube(16, 8, 4, 1, 480, seed=841)
+    with pkg.Plan(16, 8, c16.psf) as p:
+        got = p.autotune(str(cache))
+        assert got.from_cache == 1
+        assert (got.syn_packed, got.dct_ctas_per_sm) == (2, 1)
+
+
+def test_set_tuning_rejects_bad_values():
+    cuda()
+    import paper_1905_08468_gb300 as pkg
+    psf = np.zeros((4, 16, 16), np.float32)
+    psf[:, 0, 0] = 1
+    with pkg.Plan(16, 4, psf) as p:
+        for bad in [(4, 0), (-1, 0), (0, -1)]:
+            with pytest.raises(pkg.MuffinError) as e:
+                p.set_tuning(*bad)
+            assert e.value.status == 1
