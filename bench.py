@@ -246,7 +246,7 @@ def run_serve(args) -> None:
     import paper_1905_08468_gb300 as pkg
 
     torch.cuda.set_device(0)
-    stream = serve_stream(seed=4)[: args.serve_requests]
+    stream = serve_stream(seed=args.serve_seed)[: args.serve_requests]
     if args.serve_rate != 4.0:          # same draws, arrivals rescaled (0: one burst)
         k = 0.0 if args.serve_rate <= 0 else 4.0 / args.serve_rate
         stream = [(t * k, n, L, sd) for t, n, L, sd in stream]
@@ -313,6 +313,7 @@ def run_serve(args) -> None:
            "higher_is_better": True, "data": "synthetic", "dtype": "f32",
            "config": {"workload": "served Poisson stream, n in {128,256,512}, "
                                   "L in {16,32,64}", "requests": len(stream),
+                      "arrival_seed": args.serve_seed,
                       "iters": iters, "mu": mu, "gamma": mu, "max_batch": args.serve_batch,
                       "chunk": 10},
            "batched": {"p50_s": nearest_rank(lb, 0.5), "p99_s": nearest_rank(lb, 0.99),
@@ -351,6 +352,8 @@ def main() -> None:
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-iters", type=int, default=300)
     ap.add_argument("--serve-batch", type=int, default=8)
+    ap.add_argument("--serve-seed", type=int, default=4,
+                    help="arrival-stream seed (request i draws its cube from seed 4000 + i)")
     ap.add_argument("--serve-rate", type=float, default=4.0,
                     help="mean arrivals per second (0: all requests at once)")
     args = ap.parse_args()
