@@ -18,6 +18,8 @@ Modules (each function cites the passage it follows):
   (Eqs. probopt, RegAll), Algorithm 2 (parallel MUFFIN update);
 * ``sure``       -- Algorithms 3 and 4 (derivative iterates), PSURE-FDMC
   (Eq. PSURE0), SUGAR-FDMC (Eq. SUGAR), ADA-PT (Algorithm 5, Eq. adaptgrad);
+* ``weights``    -- weights alpha_n, beta_l from an initial cube (Eq. 2regpar)
+  and the global SUGAR gradient descent (Eq. globalgrad);
 * ``metrics``    -- SNR and WMSE (Sec. 4.1).
 
 Parity pins: every function is checked by ``tests/test_oracle_*.py`` against

@@ -141,11 +141,11 @@ def ada_pt(prob: Problem, delta, eps: float, noise_var, theta0, n_iter: int,
     for k in range(n_iter):
         mu, gamma = theta
         mu_l, gamma_n = weights(prob, mu, gamma)
-        rec = iteration(S, prob, y, mu_l, gamma_n, tau)          # line 2
-        recb = iteration(Sb, prob, ybar, mu_l, gamma_n, tau)     # line 3
-        dmu_iteration(D[0], rec, prob, mu, gamma, tau)           # line 4
+        rec = iteration(S, prob, y, mu_l, gamma_n, tau)          # primal on y
+        recb = iteration(Sb, prob, ybar, mu_l, gamma_n, tau)     # primal on y + eps delta
+        dmu_iteration(D[0], rec, prob, mu, gamma, tau)           # derivatives, both primals
         dgamma_iteration(D[1], rec, prob, mu, gamma, tau)
-        dmu_iteration(D[2], recb, prob, mu, gamma, tau)          # line 5
+        dmu_iteration(D[2], recb, prob, mu, gamma, tau)
         dgamma_iteration(D[3], recb, prob, mu, gamma, tau)
         if (k + 1) % Delta == 0:
             g = np.array([
