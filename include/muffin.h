@@ -122,6 +122,30 @@ MUFFIN_API muffin_status muffin_plan_load_psf(muffin_plan plan, int32_t b0,
  * every kernel directly.  Results are identical either way. */
 MUFFIN_API muffin_status muffin_plan_graphs(muffin_plan plan, int32_t on);
 
+/* ---- weights (Eq. 2regpar)
+ *
+ * mu_l = mu beta_l and gamma_n = gamma alpha_n.  Replaces the plan's weights:
+ *   alpha [B][n*n], beta [B][L] (host or device arrays, >= 0, finite); NULL
+ *   keeps the current values.  The step condition (tau) follows the new
+ *   weights from the next call on.  Errors: EINVAL (NULL plan, bad value). */
+MUFFIN_API muffin_status muffin_plan_set_weights(muffin_plan plan, const float *alpha,
+                                                 const float *beta);
+
+/* Weights from an initial cube x0 [B][L][n][n] (host or device), as defined
+ * right after Eq. 2regpar:
+ *   alpha_n = 1 / (||W_lambda (x^n)_0||_2 + eps_alpha)   (pixel spectra)
+ *   beta_l  = 1 / (||W_s (x_l)_0||_2 + eps_beta)          (band images)
+ * computed with Parseval's identity (the DCT and each of the K bases are
+ * orthonormal, so ||W_lambda x^n|| = ||x^n|| and ||W_s x_l|| = sqrt(K) ||x_l||)
+ * in FP64, rounded to FP32, and installed in the plan as by
+ * muffin_plan_set_weights.  A coarse x0 is, e.g., a few plain iterations.
+ * alpha_out [B][n*n] and beta_out [B][L] (host or device) receive the
+ * weights when not NULL.  Errors: EINVAL (NULL plan or x0, eps < 0 or not
+ * finite), ECUDA. */
+MUFFIN_API muffin_status muffin_plan_weights_from_x0(muffin_plan plan, const float *x0,
+                                                     double eps_alpha, double eps_beta,
+                                                     float *alpha_out, float *beta_out);
+
 /* ---- per-shape tuning (launch variants of the hot kernels)
  *
  * Two launch choices change speed but not results (every variant computes
@@ -237,6 +261,22 @@ MUFFIN_API muffin_status muffin_sure_tune(muffin_plan plan, const float *dirty,
                                const muffin_sure_params *sp, float *x,
                                double *theta, muffin_sure_record *trace,
                                int32_t flags, muffin_info *info);
+
+/* Global SUGAR descent (Eq. globalgrad): `outer` steps of
+ *   theta <- max(theta - eta * SUGAR_{0:n_c}(theta), theta_min)
+ * where every step restarts both primal chains from the same initial cube
+ * and runs n_c = sp->iters iterations of MUFFIN and of the derivative
+ * chains with theta fixed (sp->window is ignored: one window of n_c).
+ * Arguments as muffin_sure_tune, plus
+ *   outer  number of descent steps (0 leaves x and theta unchanged);
+ *   x      in: X0, out: X after the last step's n_c iterations;
+ *   trace  host array [B][outer] (cube-major) of one record per step, or NULL.
+ * Errors: EINVAL, ESTATE (plan without ADA-PT chains), ENOMEM, ECUDA. */
+MUFFIN_API muffin_status muffin_sure_global(muffin_plan plan, const float *dirty,
+                                            const float *delta, const double *noise_var,
+                                            const muffin_sure_params *sp, int32_t outer,
+                                            float *x, double *theta, muffin_sure_record *trace,
+                                            muffin_info *info);
 
 /* ---- checkpoint / resume ------------------------------------------------
  * The state blob holds the iterates (X, U, V, T of every chain), the

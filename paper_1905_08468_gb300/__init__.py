@@ -195,6 +195,60 @@ class Plan:
         return ([(th[2 * c], th[2 * c + 1]) for c in range(B)],
                 [cube_trace(c) for c in range(B)], info)
 
+    def sure_global(self, dirty, delta, noise_var, x, theta, n_c: int, outer: int, *,
+                    eta=(1e-3, 1e-3), theta_min: float = 1e-8, eps: float):
+        """Global SUGAR descent (Eq. globalgrad): `outer` steps, each after n_c
+        iterations from the same initial cube x.  Returns (theta, trace, info)
+        with one trace record per step (lists over cubes when B > 1)."""
+        keep = []
+        sp = native.SureParams()
+        self._lib.muffin_sure_params_default(ctypes.byref(sp))
+        sp.iters, sp.window = int(n_c), int(n_c)
+        sp.eta_mu, sp.eta_gamma = float(eta[0]), float(eta[1])
+        sp.theta_min, sp.reset_each_window, sp.eps = theta_min, 1, float(eps)
+        B = self.B
+        th_in = np.broadcast_to(np.asarray(theta, dtype=np.float64).reshape(-1, 2), (B, 2))
+        th = (ctypes.c_double * (2 * B))(*th_in.ravel())
+        cap = max(1, int(outer))
+        rec = (SureRecord * (cap * B))()
+        nv_arr = np.ascontiguousarray(noise_var, dtype=np.float64)
+        keep.append(nv_arr)
+        info = native.Info()
+        native.check(self._lib.muffin_sure_global(
+            self._h, _ptr(dirty, keep), _ptr(delta, keep), ctypes.c_void_p(nv_arr.ctypes.data),
+            ctypes.byref(sp), int(outer), _ptr(x, keep), th, rec, ctypes.byref(info)))
+        def cube_trace(c):
+            return [dict(k=r.k, mu=r.mu, gamma=r.gamma, sugar_mu=r.sugar_mu,
+                         sugar_gamma=r.sugar_gamma, psure=r.psure, tau=r.tau)
+                    for r in rec[c * cap: c * cap + info.records]]
+        if B == 1:
+            return (th[0], th[1]), cube_trace(0), info
+        return ([(th[2 * c], th[2 * c + 1]) for c in range(B)],
+                [cube_trace(c) for c in range(B)], info)
+
+    # -- weights (Eq. 2regpar)
+    def set_weights(self, alpha=None, beta=None) -> None:
+        """alpha [B][n*n] pixel weights, beta [B][L] band weights (None keeps)."""
+        keep = []
+        a = None if alpha is None else _ptr(np.ascontiguousarray(alpha, np.float32)
+                                             if isinstance(alpha, np.ndarray) else alpha, keep)
+        b = None if beta is None else _ptr(np.ascontiguousarray(beta, np.float32)
+                                           if isinstance(beta, np.ndarray) else beta, keep)
+        native.check(self._lib.muffin_plan_set_weights(self._h, a, b))
+
+    def weights_from_x0(self, x0, eps_alpha: float, eps_beta: float):
+        """Install alpha_n = 1/(||W_lambda x0^n|| + eps_alpha) and beta_l =
+        1/(||W_s x0_l|| + eps_beta); returns them as (alpha [B][n][n],
+        beta [B][L]) numpy arrays (the cube axis dropped when B == 1)."""
+        keep = []
+        B, L, n = self.B, self.L, self.n
+        a = np.empty((B, n, n), np.float32)
+        b = np.empty((B, L), np.float32)
+        native.check(self._lib.muffin_plan_weights_from_x0(
+            self._h, _ptr(x0, keep), float(eps_alpha), float(eps_beta),
+            ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(b.ctypes.data)))
+        return (a[0], b[0]) if B == 1 else (a, b)
+
     # -- profile
     def profile(self, on: bool = True) -> None:
         native.check(self._lib.muffin_profile_enable(self._h, int(on)))

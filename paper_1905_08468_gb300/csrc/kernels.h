@@ -123,6 +123,9 @@ cudaError_t max_abs2_c64(const double2 *hh, size_t count, double *scratch,
 // per-band sum of squares: out[l] = sum y[l]^2 (FP64)
 cudaError_t band_sumsq(const float *y, int L, size_t per_band, double *out,
                        cudaStream_t st);
+// alpha[b][n] = 1 / (||x[b][:, n]||_2 + eps) over the L bands of cube b (FP64 sum)
+cudaError_t pixel_weights(const float *x, int B, int L, size_t N, double eps, float *alpha,
+                          cudaStream_t st);
 // ybar = y + eps * delta ; hd unchanged
 cudaError_t axpy_f32(const float *y, const float *d, float eps, float *out,
                      size_t count, cudaStream_t st);

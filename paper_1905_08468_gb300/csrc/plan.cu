@@ -207,6 +207,32 @@ muffin_status upload_cube_const(muffin_plan P) {
   return MUFFIN_OK;
 }
 
+// validate and install pixel weights a [B][N] and band weights bw [B][L]
+// (Eq. 2regpar); the sums of their squares enter the step condition
+muffin_status set_weights(muffin_plan P, const std::vector<float> &a,
+                          const std::vector<float> &bw) {
+  const int B = P->B, L = P->L;
+  const size_t N = P->N;
+  std::vector<double> as(B, 0), am(B, 0), bs(B, 0), bm(B, 0);
+  for (int c = 0; c < B; ++c) {
+    for (size_t i = 0; i < N; ++i) {
+      const double v = a[(size_t)c * N + i];
+      if (!(v >= 0) || !std::isfinite(v)) return fail(MUFFIN_EINVAL, "alpha must be finite and >= 0");
+      as[c] += v * v; am[c] = std::fmax(am[c], v * v);
+    }
+    for (int l = 0; l < L; ++l) {
+      const double v = bw[(size_t)c * L + l];
+      if (!(v >= 0) || !std::isfinite(v)) return fail(MUFFIN_EINVAL, "beta must be finite and >= 0");
+      bs[c] += v * v; bm[c] = std::fmax(bm[c], v * v);
+    }
+  }
+  P->Asum = as; P->Amax2 = am; P->Bsum = bs; P->Bmax2 = bm;
+  CK(cudaMemcpyAsync(P->alpha, a.data(), a.size() * 4, cudaMemcpyHostToDevice, P->ws));
+  CK(cudaMemcpyAsync(P->beta, bw.data(), bw.size() * 4, cudaMemcpyHostToDevice, P->ws));
+  CK(cudaStreamSynchronize(P->ws));
+  return MUFFIN_OK;
+}
+
 muffin_status plan_alloc_init(muffin_plan P, const float *alpha, const float *beta) {
   const int n = P->n, L = P->L, Lt = P->Lt, B = P->B;
   const size_t N = P->N, NL = P->NL;
@@ -302,22 +328,9 @@ muffin_status plan_alloc_init(muffin_plan P, const float *alpha, const float *be
     if (is_device_ptr(beta)) CK(cudaMemcpy(bw.data(), beta, bw.size() * 4, cudaMemcpyDeviceToHost));
     else std::memcpy(bw.data(), beta, bw.size() * 4);
   }
-  P->Asum.assign(B, 0); P->Amax2.assign(B, 0); P->Bsum.assign(B, 0); P->Bmax2.assign(B, 0);
   P->lips.assign(B, 0); P->psc.assign(B, 0); P->mu.assign(B, 0); P->gamma.assign(B, 0);
-  for (int c = 0; c < B; ++c) {
-    for (size_t i = 0; i < N; ++i) {
-      const double v = a[(size_t)c * N + i];
-      if (!(v >= 0) || !std::isfinite(v)) return fail(MUFFIN_EINVAL, "alpha must be finite and >= 0");
-      P->Asum[c] += v * v; P->Amax2[c] = std::fmax(P->Amax2[c], v * v);
-    }
-    for (int l = 0; l < L; ++l) {
-      const double v = bw[(size_t)c * L + l];
-      if (!(v >= 0) || !std::isfinite(v)) return fail(MUFFIN_EINVAL, "beta must be finite and >= 0");
-      P->Bsum[c] += v * v; P->Bmax2[c] = std::fmax(P->Bmax2[c], v * v);
-    }
-  }
-  CK(cudaMemcpyAsync(P->alpha, a.data(), a.size() * 4, cudaMemcpyHostToDevice, P->ws));
-  CK(cudaMemcpyAsync(P->beta, bw.data(), bw.size() * 4, cudaMemcpyHostToDevice, P->ws));
+  muffin_status s2 = set_weights(P, a, bw);
+  if (s2 != MUFFIN_OK) return s2;
   CK(cudaMemsetAsync(P->sc, 0, (size_t)B * sizeof(DevScalars), P->ws));
   CK(cudaStreamSynchronize(P->ws));
   return MUFFIN_OK;
@@ -922,6 +935,84 @@ std::vector<Seg> segments(muffin_plan P) {
 }  // namespace
 
 extern "C" {
+
+// ---------------------------------------------------------------- weights
+muffin_status muffin_plan_set_weights(muffin_plan P, const float *alpha, const float *beta) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  std::vector<float> a((size_t)P->B * P->N), bw((size_t)P->Lt);
+  // NULL keeps the current values
+  CK(cudaMemcpy(a.data(), alpha ? alpha : P->alpha, a.size() * 4,
+                alpha && !is_device_ptr(alpha) ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(bw.data(), beta ? beta : P->beta, bw.size() * 4,
+                beta && !is_device_ptr(beta) ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost));
+  return set_weights(P, a, bw);
+}
+
+muffin_status muffin_plan_weights_from_x0(muffin_plan P, const float *x0, double eps_alpha,
+                                          double eps_beta, float *alpha_out, float *beta_out) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  if (!x0) return fail(MUFFIN_EINVAL, "x0 is NULL");
+  if (!(eps_alpha >= 0) || !(eps_beta >= 0) || !std::isfinite(eps_alpha) || !std::isfinite(eps_beta))
+    return fail(MUFFIN_EINVAL, "eps_alpha and eps_beta must be finite and >= 0");
+  muffin_status s = pi::enter(P);
+  if (s != MUFFIN_OK) return s;
+  const size_t N = P->N, NL = P->NL;
+  s = fetch(P, x0, P->stage_a, NL);
+  if (s != MUFFIN_OK) return s;
+  // alpha: norm of every pixel spectrum (= ||W_lambda x^n||, orthonormal DCT)
+  CK(pixel_weights(P->stage_a, P->B, P->L, N, eps_alpha, P->stage_b, P->ws));
+  // beta: ||W_s x_l|| = sqrt(K) ||x_l|| (K orthonormal bases, or K identities)
+  CK(band_sumsq(P->stage_a, P->Lt, N, P->dred, P->ws));
+  std::vector<float> a((size_t)P->B * N), bw((size_t)P->Lt);
+  std::vector<double> ss((size_t)P->Lt);
+  CK(cudaMemcpyAsync(a.data(), P->stage_b, a.size() * 4, cudaMemcpyDeviceToHost, P->ws));
+  CK(cudaMemcpyAsync(ss.data(), P->dred, ss.size() * sizeof(double), cudaMemcpyDeviceToHost, P->ws));
+  CK(cudaStreamSynchronize(P->ws));
+  for (int l = 0; l < P->Lt; ++l)
+    bw[l] = (float)(1.0 / (std::sqrt((double)P->K * ss[l]) + eps_beta));
+  s = set_weights(P, a, bw);
+  if (s != MUFFIN_OK) return s;
+  if (alpha_out) s = store(P, P->alpha, alpha_out, a.size());
+  if (s == MUFFIN_OK && beta_out) s = store(P, P->beta, beta_out, bw.size());
+  if (s == MUFFIN_OK) s = pi::leave(P, true);
+  return s;
+}
+
+// ---------------------------------------------------------------- global descent
+muffin_status muffin_sure_global(muffin_plan P, const float *dirty, const float *delta,
+                                 const double *noise_var, const muffin_sure_params *sp,
+                                 int32_t outer, float *x, double *theta,
+                                 muffin_sure_record *trace, muffin_info *info) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  if (!P->p.sure) return fail(MUFFIN_ESTATE, "plan was created without the ADA-PT chains (sure=0)");
+  if (!sp || !x || !theta) return fail(MUFFIN_EINVAL, "NULL argument");
+  if (outer < 0 || sp->iters < 1) return fail(MUFFIN_EINVAL, "outer >= 0 and iters >= 1 required");
+  const int B = P->B;
+  const size_t NL = P->NL;
+  // the initial cube, restored before every outer step
+  float *x0 = nullptr;
+  CK(cudaMalloc(&x0, NL * sizeof(float)));
+  struct Guard { float *p; ~Guard() { cudaFree(p); } } guard{x0};
+  CK(cudaMemcpy(x0, x, NL * sizeof(float), cudaMemcpyDefault));
+  muffin_sure_params q = *sp;
+  q.window = sp->iters;              // one window of n_c iterations, theta fixed
+  q.reset_each_window = 1;
+  std::vector<muffin_sure_record> rec((size_t)B * 2);
+  muffin_info inf{};
+  for (int i = 0; i < outer; ++i) {
+    if (i > 0) CK(cudaMemcpy(x, x0, NL * sizeof(float), cudaMemcpyDefault));
+    muffin_status s = muffin_sure_tune(P, dirty, delta, noise_var, &q, x, theta, rec.data(), 0, &inf);
+    if (s != MUFFIN_OK) return s;
+    if (trace)
+      for (int c = 0; c < B; ++c) trace[(size_t)c * outer + i] = rec[(size_t)c * 2];
+  }
+  if (info) {
+    *info = inf;
+    info->iters_done = outer * sp->iters;
+    info->records = outer;
+  }
+  return MUFFIN_OK;
+}
 
 muffin_status muffin_state_size(muffin_plan P, size_t *bytes) {
   if (!P || !bytes) return fail(MUFFIN_EINVAL, "NULL argument");

@@ -201,6 +201,33 @@ cudaError_t band_sumsq(const float *y, int L, size_t per_band, double *out,
   return cudaGetLastError();
 }
 
+// alpha[b][n] = 1 / (sqrt(sum_l x[b][l][n]^2) + eps): the norm of pixel
+// n's spectrum, which equals ||W_lambda x^n||_2 for the orthonormal DCT
+// (Eq. 2regpar weights); FP64 sum in band order
+__global__ void k_pixel_weights(const float *__restrict__ x, int B, int L, size_t N,
+                                double eps, float *__restrict__ alpha) {
+  const size_t total = (size_t)B * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = i / N, px = i - b * N;
+    const float *xb = x + b * L * N + px;
+    double s = 0.0;
+    for (int l = 0; l < L; ++l) {
+      const double v = xb[(size_t)l * N];
+      s = fma(v, v, s);
+    }
+    alpha[i] = (float)(1.0 / (sqrt(s) + eps));
+  }
+}
+
+cudaError_t pixel_weights(const float *x, int B, int L, size_t N, double eps, float *alpha,
+                          cudaStream_t st) {
+  const size_t g = ((size_t)B * N + 255) / 256;
+  const int nb = (int)(g > 152 * 16 ? 152 * 16 : (g ? g : 1));
+  k_pixel_weights<<<nb, 256, 0, st>>>(x, B, L, N, eps, alpha);
+  return cudaGetLastError();
+}
+
 cudaError_t axpy_f32(const float *y, const float *d, float eps, float *out,
                      size_t count, cudaStream_t st) {
   size_t g = (count + 255) / 256;

@@ -82,6 +82,12 @@ SIGNATURES = {
                                    ctypes.POINTER(SureParams), c_void_p,
                                    ctypes.POINTER(c_double), ctypes.POINTER(SureRecord),
                                    c_int32, ctypes.POINTER(Info)]),
+    "muffin_sure_global": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                     c_void_p, ctypes.POINTER(c_double),
+                                     ctypes.POINTER(SureRecord), ctypes.POINTER(Info)]),
+    "muffin_plan_set_weights": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "muffin_plan_weights_from_x0": (c_int32, [c_void_p, c_void_p, c_double, c_double,
+                                              c_void_p, c_void_p]),
     "muffin_state_size": (c_int32, [c_void_p, ctypes.POINTER(c_size_t)]),
     "muffin_state_export": (c_int32, [c_void_p, c_void_p, c_size_t]),
     "muffin_state_import": (c_int32, [c_void_p, c_void_p, c_size_t]),
