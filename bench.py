@@ -325,6 +325,75 @@ def run_serve(args) -> None:
     print(json.dumps(out), flush=True)
 
 
+def run_convergence(args) -> None:
+    """ADA-PT'ed MUFFIN from several initial (mu, gamma) on a synthetic cube
+    (the convergence experiment of Sec. 4.2.2, on a stand-in for its data):
+    theta and SUGAR at every window, SNR and WMSE (Sec. 4.1) of the
+    reconstruction every chunk.  WMSE uses the library's own H^T H operator:
+    ||H d||^2 = <d, H^T H d>."""
+    import math
+    import numpy as np
+    import torch
+    from synth import fdmc_eps, make_workload
+    import paper_1905_08468_gb300 as pkg
+
+    torch.cuda.set_device(0)
+    c = make_workload(args.workload)
+    eps = fdmc_eps(c.noise_var)
+    dev = torch.device("cuda")
+    dirty = torch.from_numpy(c.dirty).to(dev)
+    delta = torch.from_numpy(c.delta).to(dev)
+    sky = torch.from_numpy(c.sky).to(dev)
+    plan = pkg.Plan(c.n, c.L, c.psf, sure=True)
+    g = torch.empty_like(dirty)
+    nl = sky.numel()
+    sky_e = float((sky.double() ** 2).sum())
+
+    def metrics(x):
+        d = (sky - x).contiguous()
+        plan.op_gradient(d, g)
+        err = float((d.double() ** 2).sum())
+        return 10.0 * math.log10(sky_e / err), float((d.double() * g.double()).sum()) / nl
+
+    inits = [tuple(float(v) for v in t.split(",")) for t in args.conv_inits.split(";")]
+    eta = tuple(float(v) for v in args.conv_eta.split(","))
+    runs = []
+    t0 = time.perf_counter()
+    for th0 in inits:
+        x = torch.zeros_like(dirty)
+        th, windows, curve, k, warm = th0, [], [], 0, False
+        while k < args.conv_iters:
+            it = min(args.conv_chunk, args.conv_iters - k)
+            th, tr, _ = plan.sure_tune(dirty, delta, c.noise_var, x, th, it, window=args.window,
+                                       eta=eta, eps=eps, warm=warm)
+            warm = True
+            k += it
+            windows += tr
+            snr, wm = metrics(x)
+            curve.append({"k": k, "snr_db": snr, "wmse": wm})
+        last = windows[-10:]
+        runs.append({"theta0": list(th0), "theta": list(th),
+                     "sugar_last": [float(np.mean([w["sugar_mu"] for w in last])),
+                                    float(np.mean([w["sugar_gamma"] for w in last]))],
+                     "sugar_first": [windows[0]["sugar_mu"], windows[0]["sugar_gamma"]],
+                     "snr_db": curve[-1]["snr_db"], "wmse": curve[-1]["wmse"],
+                     "curve": curve,
+                     "theta_every": [[w["k"], w["mu"], w["gamma"], w["sugar_mu"], w["sugar_gamma"]]
+                                     for w in windows[:: max(1, len(windows) // 50)]]})
+    secs = time.perf_counter() - t0
+    mus = [r["theta"][0] for r in runs]
+    gammas = [r["theta"][1] for r in runs]
+    out = {"metric": "ADA-PT convergence from %d initialisations" % len(runs),
+           "value": max(mus) / min(mus), "unit": "final mu spread (max/min)",
+           "gamma_spread": max(gammas) / min(gammas), "n_gpus": 1, "steps": 1, "warmup": 0,
+           "higher_is_better": False, "data": "synthetic", "dtype": "f32",
+           "config": {"workload": args.workload, "iters": args.conv_iters,
+                      "window": args.window, "eta": list(eta), "eps": eps},
+           "seconds": secs, "runs": runs}
+    print(json.dumps(out), flush=True)
+    plan.close()
+
+
 def measured_peak_gbs():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -352,6 +421,12 @@ def main() -> None:
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-iters", type=int, default=300)
     ap.add_argument("--serve-batch", type=int, default=8)
+    ap.add_argument("--convergence", action="store_true",
+                    help="ADA-PT from several initial (mu, gamma): theta, SUGAR, SNR, WMSE curves")
+    ap.add_argument("--conv-inits", default="3e-2,1e-1;3e-2,1e-3;3e-4,1e-3;3e-4,1e-1")
+    ap.add_argument("--conv-eta", default="1e-6,1e-5")
+    ap.add_argument("--conv-iters", type=int, default=5000)
+    ap.add_argument("--conv-chunk", type=int, default=250)
     ap.add_argument("--serve-seed", type=int, default=4,
                     help="arrival-stream seed (request i draws its cube from seed 4000 + i)")
     ap.add_argument("--serve-rate", type=float, default=4.0,
@@ -364,6 +439,11 @@ def main() -> None:
         return
     if args.serve:
         run_serve(args)
+        return
+    if args.convergence:
+        if args.workload == "c3_1024x1024x64":
+            args.workload = "c2_256x256x32"
+        run_convergence(args)
         return
 
     import numpy as np

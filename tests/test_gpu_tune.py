@@ -100,3 +100,26 @@ def test_set_tuning_rejects_bad_values():
             with pytest.raises(pkg.MuffinError) as e:
                 p.set_tuning(*bad)
             assert e.value.status == 1
+
+
+def test_convergence_mode_reports_trajectories():
+    """bench.py --convergence on a small cube: one record per window, SNR and
+    WMSE per chunk, finite values (the experiment itself is run at 256^2 x 32)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    cuda()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--convergence",
+                        "--workload", "c1_64x64x8", "--conv-iters", "120", "--conv-chunk", "60",
+                        "--conv-inits", "3e-2,1e-1;3e-4,1e-3"],
+                       capture_output=True, text=True, cwd=root, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    assert len(out["runs"]) == 2
+    for run in out["runs"]:
+        assert [p["k"] for p in run["curve"]] == [60, 120]
+        assert all(np.isfinite(p["snr_db"]) and p["wmse"] > 0 for p in run["curve"])
+        assert run["theta_every"][0][0] == 10
+        assert all(t >= 1e-8 for t in run["theta"])
