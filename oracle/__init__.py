@@ -11,6 +11,8 @@ Modules (each function cites the passage it follows):
   (the spatial dictionary of Sec. 4.2.1: union of the first 8 Daubechies bases);
 * ``wavelets``   -- periodised orthonormal 2D DWT (Mallat layout), the union
   W_s and its adjoint;
+* ``iuwt``       -- the isotropic undecimated wavelet transform (starlet), the
+  alternative spatial dictionary named in Sec. 2.1;
 * ``spectral``   -- the orthonormal DCT-II W_lambda (Sec. 4.2.1);
 * ``convolution``-- H_l, H_l^T as circular convolutions (Eq. model), the
   Lipschitz constant beta;

@@ -21,7 +21,7 @@ import dataclasses
 
 import numpy as np
 
-from . import convolution, spectral, wavelets
+from . import convolution, iuwt, spectral, wavelets
 
 
 @dataclasses.dataclass
@@ -35,6 +35,7 @@ class Problem:
     alpha_w: np.ndarray = None   # pixel weights alpha_n [n, n]
     beta_w: np.ndarray = None    # band weights beta_l [L]
     positivity: bool = True
+    dictionary: str = "daubechies"   # or "iuwt" (Sec. 2.1)
 
     @property
     def L(self):
@@ -46,11 +47,37 @@ class Problem:
 
     @property
     def K(self):
+        """Number of Daubechies bases of the union."""
         return len(self.bank)
+
+    @property
+    def planes(self):
+        """Coefficient planes per image: K bases, or J + 1 IUWT planes."""
+        return self.J + 1 if self.dictionary == "iuwt" else self.K
+
+    @property
+    def ws_norm2(self):
+        """||W_s||^2: K for the unscaled union of K orthonormal bases, the
+        exact starlet norm for the IUWT."""
+        if self.dictionary == "iuwt":
+            return iuwt.norm2(self.n, self.J)
+        return float(self.K)
+
+    def Ws(self, x):
+        """W_s x: images [..., n, n] -> [..., planes, n, n]."""
+        if self.dictionary == "iuwt":
+            return iuwt.analysis(x, self.J)
+        return wavelets.Ws(x, self.bank, self.J)
+
+    def WsT(self, u):
+        """W_s^T u: [..., planes, n, n] -> images."""
+        if self.dictionary == "iuwt":
+            return iuwt.adjoint(u, self.J)
+        return wavelets.WsT(u, self.bank, self.J)
 
 
 def make_problem(dirty, psf, n_wavelets=8, J=3, sigma=10.0, alpha_w=None,
-                 beta_w=None, positivity=True) -> Problem:
+                 beta_w=None, positivity=True, dictionary="daubechies") -> Problem:
     from .daubechies import filter_bank
     y = np.asarray(dirty, dtype=np.float64)
     L, n, _ = y.shape
@@ -59,7 +86,7 @@ def make_problem(dirty, psf, n_wavelets=8, J=3, sigma=10.0, alpha_w=None,
         J=J, C=spectral.dct_matrix(L), sigma=sigma,
         alpha_w=np.ones((n, n)) if alpha_w is None else np.asarray(alpha_w, np.float64),
         beta_w=np.ones(L) if beta_w is None else np.asarray(beta_w, np.float64),
-        positivity=positivity)
+        positivity=positivity, dictionary=dictionary)
 
 
 def weights(prob: Problem, mu: float, gamma: float):
@@ -72,9 +99,9 @@ def step_tau(prob: Problem, mu_l, gamma_n, rule: int = 0,
     """tau from the convergence condition of Sec. 2.2 given sigma."""
     beta = convolution.lipschitz(prob.hhat)
     if rule == 0:
-        Lnorm2 = prob.K * np.sum(mu_l ** 2) + np.sum(gamma_n ** 2)
+        Lnorm2 = prob.ws_norm2 * np.sum(mu_l ** 2) + np.sum(gamma_n ** 2)
     else:
-        Lnorm2 = prob.K * np.max(mu_l ** 2) + np.max(gamma_n ** 2)
+        Lnorm2 = prob.ws_norm2 * np.max(mu_l ** 2) + np.max(gamma_n ** 2)
     return safety / (beta / 2.0 + prob.sigma * Lnorm2)
 
 
@@ -100,7 +127,7 @@ class State:
 
 
 def zero_state(prob: Problem, x0=None) -> State:
-    L, n, K = prob.L, prob.n, prob.K
+    L, n, K = prob.L, prob.n, prob.planes
     x = np.zeros((L, n, n)) if x0 is None else np.array(x0, dtype=np.float64)
     return State(x=x, u=np.zeros((L, K, n, n)), v=np.zeros((L, n, n)),
                  t=np.zeros((L, n, n)))
@@ -112,12 +139,11 @@ def iteration(st: State, prob: Problem, y, mu_l, gamma_n, tau) -> dict:
     updated v, x and x-tilde)."""
     x = st.x                                               # eq. updatenode2
     grad = convolution.HT(convolution.H(x, prob.hhat) - y, prob.hhat)  # grad2
-    s = mu_l[:, None, None] * wavelets.WsT(st.u, prob.bank, prob.J)  # adjointspat2
+    s = mu_l[:, None, None] * prob.WsT(st.u)               # eq. adjointspat2
     m = x - tau * (grad + s + st.t)                         # eq. stpm
     xt = pos(m) if prob.positivity else m                   # eq. stpx
     z = 2.0 * xt - x
-    p = st.u + prob.sigma * mu_l[:, None, None, None] * \
-        wavelets.Ws(z, prob.bank, prob.J)                   # eq. stpp
+    p = st.u + prob.sigma * mu_l[:, None, None, None] * prob.Ws(z)  # eq. stpp
     u_new = sat(p)                                          # eq. stpu
     # master step, every pixel spectrum n
     vt = st.v + prob.sigma * gamma_n[None] * spectral.apply_spectra(prob.C, z)  # vt
@@ -147,7 +173,7 @@ def objective(X, prob: Problem, mu: float, gamma: float) -> float:
         return float("inf")
     r = prob.y - convolution.H(X, prob.hhat)
     f = 0.5 * np.sum(r * r)
-    f += np.sum(mu_l * np.sum(np.abs(wavelets.Ws(X, prob.bank, prob.J)),
+    f += np.sum(mu_l * np.sum(np.abs(prob.Ws(X)),
                               axis=(1, 2, 3)))
     f += np.sum(gamma_n * np.sum(np.abs(spectral.apply_spectra(prob.C, X)),
                                  axis=0))

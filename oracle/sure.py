@@ -24,7 +24,7 @@ import dataclasses
 
 import numpy as np
 
-from . import convolution, spectral, wavelets
+from . import convolution, spectral
 from .muffin import Problem, State, iteration, step_tau, weights, zero_state
 
 
@@ -49,12 +49,12 @@ def dmu_iteration(d: State, rec: dict, prob: Problem, mu, gamma, tau):
     a = prob.alpha_w[None]
     x_d = d.x                                                # eq. updatenode_mu
     grad_d = convolution.HT(convolution.H(x_d, prob.hhat), prob.hhat)
-    s_d = mu * b * wavelets.WsT(d.u, prob.bank, prob.J) + \
-        b * wavelets.WsT(rec["u_old"], prob.bank, prob.J)    # eq. adjointspat_mu
+    s_d = mu * b * prob.WsT(d.u) + \
+        b * prob.WsT(rec["u_old"])    # eq. adjointspat_mu
     m_d = x_d - tau * (grad_d + s_d + d.t)
     xt_d = (U_mask(rec["m"]) if prob.positivity else 1.0) * m_d   # eq. U_mu
     w = 2.0 * rec["xt"] - rec["x"] + mu * (2.0 * xt_d - x_d)
-    p_d = d.u + prob.sigma * b[:, None] * wavelets.Ws(w, prob.bank, prob.J)
+    p_d = d.u + prob.sigma * b[:, None] * prob.Ws(w)
     u_d = Pi_mask(rec["p"]) * p_d                            # eq. pi_mu
     vt_d = d.v + prob.sigma * gamma * a * \
         spectral.apply_spectra(prob.C, 2.0 * xt_d - x_d)
@@ -69,11 +69,11 @@ def dgamma_iteration(d: State, rec: dict, prob: Problem, mu, gamma, tau):
     a = prob.alpha_w[None]
     x_d = d.x                                                # eq. updatenode
     grad_d = convolution.HT(convolution.H(x_d, prob.hhat), prob.hhat)  # grad
-    s_d = mu * b * wavelets.WsT(d.u, prob.bank, prob.J)      # eq. adjointspat
+    s_d = mu * b * prob.WsT(d.u)      # eq. adjointspat
     m_d = x_d - tau * (grad_d + s_d + d.t)
     xt_d = (U_mask(rec["m"]) if prob.positivity else 1.0) * m_d
     p_d = d.u + prob.sigma * mu * b[:, None] * \
-        wavelets.Ws(2.0 * xt_d - x_d, prob.bank, prob.J)
+        prob.Ws(2.0 * xt_d - x_d)
     u_d = Pi_mask(rec["p"]) * p_d                            # eq. updateu
     w = 2.0 * rec["xt"] - rec["x"] + gamma * (2.0 * xt_d - x_d)
     vt_d = d.v + prob.sigma * a * spectral.apply_spectra(prob.C, w)
