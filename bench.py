@@ -202,7 +202,9 @@ def workload_config(args, oracle=False) -> dict:
     cfg = {"workload": f"ADA-PT'ed MUFFIN {n}x{n} px x {L} bands",
            "n": n, "bands": L, "sources": n_src, "blobs": n_blob, "uv_points": n_uv,
            "snr_db": 20, "seed": seed, "iters_per_step": args.iters,
-           "window": args.window, "wavelets": "db1..db8, 3 levels",
+           "window": args.window,
+           "wavelets": ("IUWT (starlet), 3 scales" if getattr(args, "dictionary", "daubechies") == "iuwt"
+                        else "db1..db8, 3 levels"),
            "spectral": "DCT-II (3xTF32 tensor cores)", "chains": 6,
            "theta0": list(THETA0), "eta": list(ETA),
            "l2": "inputs larger than L2 (state ~26 GB per cube)"}
@@ -414,6 +416,8 @@ def main() -> None:
     ap.add_argument("--window", type=int, default=10)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dictionary", default="daubechies", choices=["daubechies", "iuwt"],
+                    help="spatial dictionary W_s (union of 8 Daubechies bases, or the starlet)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch variants instead of tuning them for the shape")
     ap.add_argument("--serve", action="store_true",
@@ -462,7 +466,7 @@ def main() -> None:
     dirty = torch.from_numpy(c.dirty).to(dev)
     delta = torch.from_numpy(c.delta).to(dev)
     x = torch.zeros_like(dirty)
-    plan = pkg.Plan(c.n, c.L, psf, sure=True)
+    plan = pkg.Plan(c.n, c.L, psf, sure=True, dictionary=args.dictionary)
     del psf
     tuning = None
     if not args.no_autotune:

@@ -78,6 +78,12 @@ typedef struct {
                          by the same launches (default 1); every cube array
                          argument below then holds B cubes one after the
                          other: [B][L][n][n] */
+  int32_t dictionary; /* spatial dictionary W_s (Sec. 2.1): 0 = union of the
+                         first n_wavelets Daubechies bases (default), K =
+                         n_wavelets coefficient planes per band, ||W_s||^2 =
+                         K; 1 = isotropic undecimated wavelet transform
+                         (starlet, B3 spline, periodic) with J = levels <= 4
+                         scales, K = J + 1 planes, ||W_s||^2 = 1 */
 } muffin_params;
 
 /* Fill *p with the defaults above for an n x n x nbands cube. */

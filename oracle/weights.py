@@ -19,17 +19,18 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import spectral, wavelets
+from . import iuwt, spectral, wavelets
 from .daubechies import filter_bank
 from .muffin import Problem
 from .sure import ada_pt
 
 
 def weights_from_x0(x0, n_wavelets: int = 8, J: int = 3, eps_alpha: float = 1e-3,
-                    eps_beta: float = 1e-3):
+                    eps_beta: float = 1e-3, dictionary: str = "daubechies"):
     """alpha [n, n] and beta [L] of the initial cube x0 [L, n, n] (Eq.
     2regpar), with the transforms applied explicitly: the DCT of every
-    pixel spectrum and the union of Daubechies bases of every band image."""
+    pixel spectrum and W_s (the union of Daubechies bases, or the IUWT) of
+    every band image."""
     x0 = np.asarray(x0, np.float64)
     L, n, _ = x0.shape
     C = spectral.dct_matrix(L)
@@ -39,7 +40,10 @@ def weights_from_x0(x0, n_wavelets: int = 8, J: int = 3, eps_alpha: float = 1e-3
     bank = filter_bank(n_wavelets)
     beta = np.empty(L)
     for l in range(L):
-        u = wavelets.Ws(x0[l], bank, J)               # [K, n, n]
+        if dictionary == "iuwt":
+            u = iuwt.analysis(x0[l], J)                # [J + 1, n, n]
+        else:
+            u = wavelets.Ws(x0[l], bank, J)           # [K, n, n]
         beta[l] = 1.0 / (np.sqrt(np.sum(u ** 2)) + eps_beta)
     return alpha.reshape(n, n), beta
 

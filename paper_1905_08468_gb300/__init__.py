@@ -24,6 +24,15 @@ def library():
     return native.load()
 
 
+def _dictionary(name) -> int:
+    """Spatial dictionary code: "daubechies" (union of Daubechies bases) or
+    "iuwt" (starlet)."""
+    codes = {"daubechies": 0, "iuwt": 1}
+    if name not in codes:
+        raise ValueError(f"dictionary must be one of {sorted(codes)}, got {name!r}")
+    return codes[name]
+
+
 def _ptr(a, keep: list, dtype=np.float32):
     """Raw pointer of a contiguous float32 array (torch tensor or numpy)."""
     if a is None:
@@ -74,15 +83,19 @@ class Plan:
                  levels: int = 3, sigma: float = 10.0, step_rule: int = 0,
                  tau_safety: float = 0.99, positivity: bool = True,
                  sure: bool = False, alpha=None, beta=None, stream=None,
-                 batch: int = 1):
+                 batch: int = 1, dictionary: str = "daubechies"):
         lib = library()
         self._lib = lib
-        self.n, self.L, self.K, self.B = n, nbands, n_wavelets, batch
+        self.n, self.L, self.B = n, nbands, batch
+        self.dictionary = dictionary
+        # coefficient planes per band: K bases, or J + 1 starlet planes
+        self.K = levels + 1 if dictionary == "iuwt" else n_wavelets
         p = native.Params()
         lib.muffin_params_default(ctypes.byref(p), n, nbands)
         p.n_wavelets, p.levels, p.sigma = n_wavelets, levels, sigma
         p.step_rule, p.tau_safety = step_rule, tau_safety
         p.positivity, p.sure, p.batch = int(positivity), int(sure), int(batch)
+        p.dictionary = _dictionary(dictionary)
         keep = []
         handle = ctypes.c_void_p()
         st = stream if stream is not None else _stream_handle()
@@ -295,12 +308,13 @@ class Plan:
 
 
 def estimate_bytes(n: int, nbands: int, *, n_wavelets: int = 8, levels: int = 3,
-                   sure: bool = False, batch: int = 1) -> int:
+                   sure: bool = False, batch: int = 1, dictionary: str = "daubechies") -> int:
     """Device bytes a plan of this shape allocates."""
     lib = library()
     p = native.Params()
     lib.muffin_params_default(ctypes.byref(p), n, nbands)
     p.n_wavelets, p.levels, p.sure, p.batch = n_wavelets, levels, int(sure), batch
+    p.dictionary = _dictionary(dictionary)
     out = ctypes.c_size_t()
     native.check(lib.muffin_plan_estimate_bytes(ctypes.byref(p), ctypes.byref(out)))
     return int(out.value)

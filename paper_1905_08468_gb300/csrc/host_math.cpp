@@ -103,4 +103,28 @@ void dct2_matrix(int L, double *C) {
   }
 }
 
+double iuwt_norm2(int n, int J) {
+  const double pi = 3.14159265358979323846;
+  // 1D transfer function of the B3 spline at dilation d: (1 + cos w d)^2 / 4
+  std::vector<std::vector<double>> h(J, std::vector<double>(n));
+  for (int j = 0; j < J; ++j)
+    for (int k = 0; k < n; ++k) {
+      const double c = std::cos(2.0 * pi * (double)(k << j) / n);
+      h[j][k] = (1.0 + c) * (1.0 + c) / 4.0;
+    }
+  double best = 0.0;
+  for (int ky = 0; ky < n; ++ky)
+    for (int kx = 0; kx < n; ++kx) {
+      double a = 1.0, s = 0.0;
+      for (int j = 0; j < J; ++j) {
+        const double an = a * h[j][ky] * h[j][kx];
+        s += (a - an) * (a - an);
+        a = an;
+      }
+      s += a * a;
+      if (s > best) best = s;
+    }
+  return best;
+}
+
 }  // namespace muffin

@@ -183,6 +183,7 @@ struct WaveArgs {
   float *scratch;          // LL scratch: level j (1 <= j < J) holds
                            // [C][L][K][n>>j][n>>j] at scratch + lvl_off[j]
   size_t lvl_off[16];
+  int dict;                // 0: union of K Daubechies bases, 1: IUWT (K = J + 1 planes)
   int syn_packed;          // synthesis variant: bit 0 coarse levels, bit 1
                            // level 1 (0 scalar row pass, 1 packed row pairs)
   Prof *prof;              // optional per-kernel timing
@@ -196,6 +197,13 @@ cudaError_t wavelet_synthesis_prox(const WaveArgs &w, const Group &gr,
 // reads gr.xt, gr.x, gr.u -> gr.u.
 cudaError_t wavelet_analysis_dual(const WaveArgs &w, const Group &gr,
                                   cudaStream_t st);
+// IUWT (starlet) forms of the four calls above and below (iuwt.cu); the
+// scratch holds two [C][L][n][n] running images.  J >= 1.
+cudaError_t iuwt_analysis_dual(const WaveArgs &w, const Group &gr, cudaStream_t st);
+cudaError_t iuwt_synthesis_prox(const WaveArgs &w, const Group &gr, int positivity,
+                                cudaStream_t st);
+cudaError_t iuwt_analysis_op(const WaveArgs &w, const float *x, float *u, cudaStream_t st);
+cudaError_t iuwt_synthesis_op(const WaveArgs &w, const float *u, float *x, cudaStream_t st);
 // Operators: u = W_s x ; x = W_s^T u (C = 1, no weights).
 cudaError_t wavelet_analysis_op(const WaveArgs &w, const float *x, float *u,
                                 cudaStream_t st);

@@ -106,6 +106,10 @@ muffin_status validate(const muffin_params *p) {
     return fail(MUFFIN_EINVAL, "n_wavelets=%d out of range [1, 8]", p->n_wavelets);
   if (p->levels < 0 || p->levels > 15 || (1 << p->levels) > p->n)
     return fail(MUFFIN_EINVAL, "levels=%d needs 2^levels <= n", p->levels);
+  if (p->dictionary != 0 && p->dictionary != 1)
+    return fail(MUFFIN_EINVAL, "dictionary=%d must be 0 (Daubechies) or 1 (IUWT)", p->dictionary);
+  if (p->dictionary == 1 && p->levels > 4)
+    return fail(MUFFIN_EINVAL, "the IUWT supports levels <= 4 (got %d)", p->levels);
   if (!(p->sigma > 0)) return fail(MUFFIN_EINVAL, "sigma must be > 0");
   if (!(p->tau_safety > 0 && p->tau_safety < 1))
     return fail(MUFFIN_EINVAL, "tau_safety must be in (0, 1)");
@@ -260,10 +264,14 @@ muffin_status plan_alloc_init(muffin_plan P, const float *alpha, const float *be
   CK(P->alloc(&P->wband, (size_t)Lt));
   CK(P->alloc(&P->S, (size_t)P->Cmax * Lt * nh * n));
   size_t off = 0;
-  for (int j = 1; j < P->J; ++j) {
-    P->lvl_off[j] = off;
-    const size_t h = (size_t)(n >> j);
-    off += (size_t)P->Cmax * Lt * P->K * h * h;
+  if (P->dict == 1) {
+    off = 2 * (size_t)P->Cmax * Lt * N;       // IUWT: two running images
+  } else {
+    for (int j = 1; j < P->J; ++j) {
+      P->lvl_off[j] = off;
+      const size_t h = (size_t)(n >> j);
+      off += (size_t)P->Cmax * Lt * P->K * h * h;
+    }
   }
   CK(P->alloc(&P->llscr, off ? off : 1));
   CK(P->alloc(&P->b, NL));
@@ -374,7 +382,7 @@ muffin_status window_end(muffin_plan P, const muffin_sure_params *sp) {
   ta.B = P->B; ta.sc = P->sc; ta.partials = part; ta.nb_per_cube = bpb * P->L;
   ta.record = P->records; ta.rec_count = P->rec_count;
   ta.eta_mu = sp->eta_mu; ta.eta_gamma = sp->eta_gamma; ta.theta_min = sp->theta_min;
-  ta.cube_const = P->cube_const; ta.safety = P->p.tau_safety; ta.K = P->K;
+  ta.cube_const = P->cube_const; ta.safety = P->p.tau_safety; ta.K = P->wsn2;
   {
     ProfScope ps(P->pp(), "theta_update", 6.0 * 8.0 * bpb * P->Lt, 0.0, P->ws);
     CK(theta_update(ta, P->ws));
@@ -531,11 +539,14 @@ muffin_status fetch_x(muffin_plan P, int b0, int b1, float *dst) {
 
 size_t estimate_bytes(const muffin_params *p) {
   // mirrors plan_alloc_init (each allocation carries 16 bytes of slack)
-  const size_t n = p->n, L = p->nbands, B = p->batch, Lt = B * L, K = p->n_wavelets;
+  const size_t n = p->n, L = p->nbands, B = p->batch, Lt = B * L;
+  const size_t K = p->dictionary == 1 ? (size_t)p->levels + 1 : (size_t)p->n_wavelets;
   const size_t N = n * n, NL = N * Lt, nh = n / 2 + 1, C = p->sure ? 3 : 1;
   const size_t Lp = (L + 15) / 16 * 16;
   size_t ll = 0;
-  for (int j = 1; j < p->levels; ++j) ll += C * Lt * K * (n >> j) * (n >> j);
+  if (p->dictionary == 1) ll = 2 * C * Lt * N;
+  else
+    for (int j = 1; j < p->levels; ++j) ll += C * Lt * K * (n >> j) * (n >> j);
   size_t b = 3 * NL * 16 + Lt * nh * n * 4 + (size_t)fft32_table_len((int)n) * 8 + n * 16 +
              4 * Lp * Lp * 4 + B * N * 4 + Lt * 4 + B * sizeof(DevScalars) + B * 32 + 4 +
              (kRedSure + 65 * Lt + 6 * (Lt > 4096 ? Lt : 4096)) * 8 + Lt * 8 +
@@ -559,7 +570,10 @@ muffin_status create(const muffin_params *p, const float *psf, const float *alph
   muffin_plan P = new (std::nothrow) muffin_plan_s();
   if (!P) return fail(MUFFIN_ENOMEM, "host allocation failed");
   P->p = *p;
-  P->n = p->n; P->L = p->nbands; P->K = p->n_wavelets; P->J = p->levels;
+  P->n = p->n; P->L = p->nbands; P->J = p->levels;
+  P->dict = p->dictionary;
+  P->K = P->dict == 1 ? p->levels + 1 : p->n_wavelets;
+  P->wsn2 = P->dict == 1 ? iuwt_norm2(p->n, p->levels) : (double)p->n_wavelets;
   P->B = p->batch; P->Lt = P->B * P->L;
   P->Lp = (P->L + 15) / 16 * 16;
   P->Cmax = p->sure ? 3 : 1;
@@ -594,7 +608,7 @@ void muffin_params_default(muffin_params *p, int32_t n, int32_t nbands) {
   std::memset(p, 0, sizeof(*p));
   p->n = n; p->nbands = nbands; p->n_wavelets = 8; p->levels = 3;
   p->sigma = 10.0; p->step_rule = 0; p->tau_safety = 0.99; p->positivity = 1;
-  p->sure = 0; p->batch = 1;
+  p->sure = 0; p->batch = 1; p->dictionary = 0;
 }
 
 void muffin_sure_params_default(muffin_sure_params *s) {
@@ -904,7 +918,7 @@ struct BlobHeader {
   char magic[8];
   int32_t n, L, K, J, sure, B;
   long long k_done;
-  int32_t have_b, have_state, have_sure_state, pad;
+  int32_t have_b, have_state, have_sure_state, dict;
 };
 
 struct Seg {
@@ -961,15 +975,26 @@ muffin_status muffin_plan_weights_from_x0(muffin_plan P, const float *x0, double
   if (s != MUFFIN_OK) return s;
   // alpha: norm of every pixel spectrum (= ||W_lambda x^n||, orthonormal DCT)
   CK(pixel_weights(P->stage_a, P->B, P->L, N, eps_alpha, P->stage_b, P->ws));
-  // beta: ||W_s x_l|| = sqrt(K) ||x_l|| (K orthonormal bases, or K identities)
-  CK(band_sumsq(P->stage_a, P->Lt, N, P->dred, P->ws));
+  // beta: ||W_s x_l|| = sqrt(K) ||x_l|| for the union of K orthonormal bases
+  // (or K identities); the IUWT is not a tight frame, so there the planes
+  // W_s x_l are computed and summed
+  double bscale = (double)P->K;
+  if (P->dict == 1 && P->J > 0) {
+    s = ensure_op_buffers(P);
+    if (s != MUFFIN_OK) return s;
+    CK(wavelet_analysis_op(P->wave(1), P->stage_a, P->op_out, P->ws));
+    CK(band_sumsq(P->op_out, P->Lt, (size_t)P->K * N, P->dred, P->ws));
+    bscale = 1.0;
+  } else {
+    CK(band_sumsq(P->stage_a, P->Lt, N, P->dred, P->ws));
+  }
   std::vector<float> a((size_t)P->B * N), bw((size_t)P->Lt);
   std::vector<double> ss((size_t)P->Lt);
   CK(cudaMemcpyAsync(a.data(), P->stage_b, a.size() * 4, cudaMemcpyDeviceToHost, P->ws));
   CK(cudaMemcpyAsync(ss.data(), P->dred, ss.size() * sizeof(double), cudaMemcpyDeviceToHost, P->ws));
   CK(cudaStreamSynchronize(P->ws));
   for (int l = 0; l < P->Lt; ++l)
-    bw[l] = (float)(1.0 / (std::sqrt((double)P->K * ss[l]) + eps_beta));
+    bw[l] = (float)(1.0 / (std::sqrt(bscale * ss[l]) + eps_beta));
   s = set_weights(P, a, bw);
   if (s != MUFFIN_OK) return s;
   if (alpha_out) s = store(P, P->alpha, alpha_out, a.size());
@@ -1031,6 +1056,7 @@ muffin_status muffin_state_export(muffin_plan P, void *host_buf, size_t bytes) {
   BlobHeader h{};
   std::memcpy(h.magic, "MUFFIN2", 8);
   h.n = P->n; h.L = P->L; h.K = P->K; h.J = P->J; h.sure = P->p.sure; h.B = P->B;
+  h.dict = P->dict;
   h.k_done = P->k_done;
   h.have_b = P->have_b; h.have_state = P->have_state; h.have_sure_state = P->have_sure_state;
   std::memcpy(o, &h, sizeof(h));
@@ -1058,7 +1084,7 @@ muffin_status muffin_state_import(muffin_plan P, const void *host_buf, size_t by
   BlobHeader h;
   std::memcpy(&h, o, sizeof(h));
   if (std::memcmp(h.magic, "MUFFIN2", 8) != 0 || h.n != P->n || h.L != P->L ||
-      h.K != P->K || h.J != P->J || h.sure != P->p.sure || h.B != P->B)
+      h.K != P->K || h.J != P->J || h.sure != P->p.sure || h.B != P->B || h.dict != P->dict)
     return fail(MUFFIN_EINVAL, "state blob does not match this plan");
   o += sizeof(h);
   for (int c = 0; c < P->B; ++c) {

@@ -35,6 +35,8 @@ bool is_device_ptr(const void *p);
 struct muffin_plan_s {
   muffin_params p{};
   int n = 0, L = 0, K = 0, J = 0, Lp = 0, Cmax = 1, B = 1, Lt = 0;
+  int dict = 0;        // 0: Daubechies union (K bases), 1: IUWT (K = J + 1 planes)
+  double wsn2 = 0;     // ||W_s||^2 of the step condition
   size_t N = 0;      // pixels per band
   size_t NLc = 0;    // voxels per cube
   size_t NL = 0;     // voxels of all cubes
@@ -96,15 +98,15 @@ struct muffin_plan_s {
   ~muffin_plan_s();
 
   double lnorm2(int c, double m, double g) const {
-    if (p.step_rule == 0) return K * m * m * Bsum[c] + g * g * Asum[c];
-    return K * m * m * Bmax2[c] + g * g * Amax2[c];
+    if (p.step_rule == 0) return wsn2 * m * m * Bsum[c] + g * g * Asum[c];
+    return wsn2 * m * m * Bmax2[c] + g * g * Amax2[c];
   }
   double tau_for(int c, double m, double g) const {
     return p.tau_safety / (0.5 * lips[c] + p.sigma * lnorm2(c, m, g));
   }
   muffin::WaveArgs wave(int C) {
     muffin::WaveArgs w{};
-    w.n = n; w.L = Lt; w.Lc = L; w.K = K; w.J = J; w.C = C;
+    w.n = n; w.L = Lt; w.Lc = L; w.K = K; w.J = J; w.C = C; w.dict = dict;
     w.beta = beta; w.sc = sc; w.scratch = llscr;
     for (int j = 0; j < 16; ++j) w.lvl_off[j] = lvl_off[j];
     w.syn_packed = syn_packed;

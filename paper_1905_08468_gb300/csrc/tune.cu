@@ -36,8 +36,9 @@ std::string shape_key(muffin_plan P) {
   for (char &ch : name)
     if (ch == ' ' || ch == '\t') ch = '_';
   char buf[256];
-  std::snprintf(buf, sizeof buf, "n=%d,L=%d,B=%d,C=%d,J=%d,K=%d,sure=%d,sm=%d,dev=%s", P->n,
-                P->L, P->B, P->Cmax, P->J, P->K, P->p.sure ? 1 : 0, sms, name.c_str());
+  std::snprintf(buf, sizeof buf, "n=%d,L=%d,B=%d,C=%d,J=%d,K=%d,dict=%d,sure=%d,sm=%d,dev=%s",
+                P->n, P->L, P->B, P->Cmax, P->J, P->K, P->dict, P->p.sure ? 1 : 0, sms,
+                name.c_str());
   return buf;
 }
 

@@ -975,6 +975,7 @@ cudaError_t upload_filters(const double h[8][16]) {
 
 cudaError_t wavelet_synthesis_prox(const WaveArgs &w, const Group &gr,
                                    int positivity, cudaStream_t st) {
+  if (w.dict == 1 && w.J > 0) return iuwt_synthesis_prox(w, gr, positivity, st);
   SynArgs a{};
   a.n = w.n; a.L = w.L; a.K = w.K; a.positivity = positivity;
   a.Lc = w.Lc > 0 ? w.Lc : w.L;
@@ -986,6 +987,7 @@ cudaError_t wavelet_synthesis_prox(const WaveArgs &w, const Group &gr,
 
 cudaError_t wavelet_analysis_dual(const WaveArgs &w, const Group &gr,
                                   cudaStream_t st) {
+  if (w.dict == 1 && w.J > 0) return iuwt_analysis_dual(w, gr, st);
   AnaArgs a{};
   a.n = w.n; a.L = w.L; a.K = w.K;
   a.Lc = w.Lc > 0 ? w.Lc : w.L;
@@ -996,6 +998,7 @@ cudaError_t wavelet_analysis_dual(const WaveArgs &w, const Group &gr,
 
 cudaError_t wavelet_analysis_op(const WaveArgs &w, const float *x, float *u,
                                 cudaStream_t st) {
+  if (w.dict == 1 && w.J > 0) return iuwt_analysis_op(w, x, u, st);
   AnaArgs a{};
   a.n = w.n; a.L = w.L; a.K = w.K; a.Lc = w.L; a.in = x; a.u = u;
   return analysis_all<1, WAVE_TRANSFORM>(w, a, st);
@@ -1003,6 +1006,7 @@ cudaError_t wavelet_analysis_op(const WaveArgs &w, const float *x, float *u,
 
 cudaError_t wavelet_synthesis_op(const WaveArgs &w, const float *u, float *x,
                                  cudaStream_t st) {
+  if (w.dict == 1 && w.J > 0) return iuwt_synthesis_op(w, u, x, st);
   SynArgs a{};
   a.n = w.n; a.L = w.L; a.K = w.K; a.Lc = w.L; a.u = u; a.out = x;
   return synthesis_all<1, WAVE_TRANSFORM>(w, a, st);

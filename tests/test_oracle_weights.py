@@ -87,3 +87,16 @@ def test_global_descent_restarts_unlike_adapt():
     # the update is the descent step of Eq. globalgrad with SUGAR of that run
     expect = np.maximum(r1.theta - np.asarray(eta) * recs[1]["sugar"], 1e-8)
     np.testing.assert_allclose(theta, expect, rtol=1e-12)
+
+
+def test_iuwt_weights_are_below_parseval():
+    # the starlet has ||W|| = 1 but is not tight: ||W x|| <= ||x||, with
+    # equality only for constant images
+    rng = np.random.default_rng(4)
+    x0 = rng.normal(size=(3, 16, 16))
+    _, b = ow.weights_from_x0(x0, J=3, eps_alpha=0.0, eps_beta=0.0, dictionary="iuwt")
+    norms = np.sqrt((x0 ** 2).sum(axis=(1, 2)))
+    assert np.all(1.0 / b < norms)
+    const = np.full((2, 16, 16), 3.0)
+    _, bc = ow.weights_from_x0(const, J=3, eps_alpha=0.0, eps_beta=0.0, dictionary="iuwt")
+    np.testing.assert_allclose(bc, 1.0 / (3.0 * 16), rtol=1e-12)
