@@ -418,6 +418,8 @@ def main() -> None:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dictionary", default="daubechies", choices=["daubechies", "iuwt"],
                     help="spatial dictionary W_s (union of 8 Daubechies bases, or the starlet)")
+    ap.add_argument("--tuning", default="",
+                    help="fixed launch variants 'syn_packed,dct_ctas_per_sm' instead of tuning")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch variants instead of tuning them for the shape")
     ap.add_argument("--serve", action="store_true",
@@ -469,7 +471,11 @@ def main() -> None:
     plan = pkg.Plan(c.n, c.L, psf, sure=True, dictionary=args.dictionary)
     del psf
     tuning = None
-    if not args.no_autotune:
+    if args.tuning:
+        sp, dc = (int(v) for v in args.tuning.split(","))
+        plan.set_tuning(sp, dc)
+        tuning = {"syn_packed": sp, "dct_ctas_per_sm": dc, "candidates": 0}
+    elif not args.no_autotune:
         ti = plan.autotune()            # launch variants for this shape (results unchanged)
         tuning = {"syn_packed": ti.syn_packed, "dct_ctas_per_sm": ti.dct_ctas_per_sm,
                   "candidates": ti.candidates, "iter_ms_default": ti.ms_default,
