@@ -11,9 +11,10 @@
 //     then m = x - tau (grad + mu_l s + t), x~ = (m)_+ (eqs. stpm, stpx).
 //
 // S_j is the separable B3 spline [1 4 6 4 1]/16 dilated by 2^j with periodic
-// boundaries.  One launch per scale: a CTA loads its 16 x 32 tile of every
-// chain with a 2 * 2^j halo (wrapped) into shared memory, smooths it along y
-// then x, and does the scale's dual update (analysis) or Horner step
+// boundaries.  One launch per scale, specialised on the dilation: a CTA
+// loads its 32 x 64 tile of every chain with a 2 * 2^j halo (wrapped) into
+// shared memory (four items per thread in flight), smooths it along y then
+// x, and does the scale's dual update (analysis) or Horner step
 // (synthesis); the running image of the next scale goes to a ping-pong
 // scratch.  The derivative chains use the primal's masks from the same
 // thread (Pi(p) per coefficient, U(m) per pixel).  J <= 4 (halo <= 16).
@@ -27,17 +28,23 @@ namespace muffin {
 
 namespace {
 
-constexpr int IY = 16, IX = 32, INT = 256;   // output tile, threads
-constexpr int IDMAX = 8;                       // largest dilation (J <= 4)
-constexpr int IAY = IY + 4 * IDMAX, IAX = IX + 4 * IDMAX + 1;   // input tile (pitch odd)
-constexpr int IBX = IX + 4 * IDMAX + 1;                          // vertical-pass pitch
+constexpr int IY = 32, IX = 64, INT = 256;   // output tile, threads
+constexpr int IQ = IY * IX / INT;              // outputs per thread (one column)
+
 // B3 spline tap m of [1 4 6 4 1] / 16
 __device__ __forceinline__ constexpr float b3(int m) {
   return (m == 2 ? 6.f : (m == 1 || m == 3) ? 4.f : 1.f) * (1.f / 16.f);
 }
 
+// shared-memory geometry of a dilation D: input tile [IY + 4D][PA], vertical
+// pass [IY][PA] (odd pitch), per chain
+template <int D> struct Geo {
+  static constexpr int AY = IY + 4 * D, AX = IX + 4 * D;
+  static constexpr int PITCH = (AX & 1) ? AX : AX + 1;
+};
+template <int D>
 constexpr size_t iuwt_smem(int ch) {
-  return ((size_t)ch * IAY * IAX + (size_t)ch * IY * IBX) * sizeof(float);
+  return (size_t)ch * (Geo<D>::AY + IY) * Geo<D>::PITCH * sizeof(float);
 }
 
 struct IuwtArgs {
@@ -56,7 +63,7 @@ struct IuwtArgs {
 
 __device__ __forceinline__ int wrap(int v, int n) { return v & (n - 1); }
 
-// tile value of chain c at (yy, xx) for the source of scale j
+// tile value of chain c at pixel pix for the source of analysis scale j
 template <int CH, int MODE>
 __device__ __forceinline__ void ana_src(const IuwtArgs &a, int l, size_t pix, float mu,
                                         float (&w)[CH]) {
@@ -81,39 +88,89 @@ __device__ __forceinline__ void ana_src(const IuwtArgs &a, int l, size_t pix, fl
   }
 }
 
-// separable B3 smoothing at dilation d of the resident tile A -> out[2] of
-// the thread's two pixels (rows ry, ry + IY/2 of column rx)
-template <int CH>
-__device__ __forceinline__ void smooth_tile(const float *A, float *Bv, int d, int c,
-                                            int ry, int rx, float (&out)[2]) {
-  const float *Ac = A + c * IAY * IAX;
-  float *Bc = Bv + c * IY * IBX;
-  // vertical pass: IY rows x (IX + 4d) columns
-  const int wcols = IX + 4 * d;
-  for (int it = threadIdx.x; it < IY * wcols; it += INT) {
-    const int r = it / wcols, col = it - r * wcols;
+// synthesis source of scale j: P_J - P_{J-1} at the coarsest step, else the
+// running image of scale j + 1
+template <int CH, int MODE>
+__device__ __forceinline__ void syn_src(const IuwtArgs &a, int l, size_t pix, float (&w)[CH]) {
+  const size_t NN = (size_t)a.n * a.n, CS = (size_t)a.L * NN;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    if (a.j == a.J - 1) {
+      const float *u = (MODE == WAVE_TRANSFORM ? a.in : a.ur) +
+                       ((size_t)(c * a.L + l) * a.P) * NN + pix;
+      w[c] = u[(size_t)a.J * NN] - u[(size_t)(a.J - 1) * NN];
+    } else {
+      w[c] = a.buf[(a.j + 1) & 1][c * CS + (size_t)l * NN + pix];
+    }
+  }
+}
+
+// fill the wrapped input tile of every chain; LB items per thread per round
+// so their loads are in flight together
+template <int CH, int D, bool ANA, int MODE>
+__device__ __forceinline__ void load_tile(const IuwtArgs &a, float *A, int y0, int x0, int l,
+                                          float mu) {
+  using G = Geo<D>;
+  constexpr int LB = 4;
+  const int n = a.n;
+  constexpr int items = G::AY * G::AX;
+  for (int base = threadIdx.x; base < items; base += LB * INT) {
+    float w[LB][CH];
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int it = base + q * INT;
+      if (it < items) {
+        const int r = it / G::AX, col = it - r * G::AX;
+        const size_t pix = (size_t)wrap(y0 - 2 * D + r, n) * n + wrap(x0 - 2 * D + col, n);
+        if (ANA) ana_src<CH, MODE>(a, l, pix, mu, w[q]);
+        else syn_src<CH, MODE>(a, l, pix, w[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      const int it = base + q * INT;
+      if (it < items) {
+        const int r = it / G::AX, col = it - r * G::AX;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) A[(c * G::AY + r) * G::PITCH + col] = w[q][c];
+      }
+    }
+  }
+}
+
+// separable B3 smoothing at dilation D of chain c's resident tile -> out[q]
+// at the thread's pixels (rows ry + q * INT / IX of column rx)
+template <int D>
+__device__ __forceinline__ void smooth_tile(const float *A, float *Bv, int c, int ry, int rx,
+                                            float (&out)[IQ]) {
+  using G = Geo<D>;
+  const float *Ac = A + c * G::AY * G::PITCH;
+  float *Bc = Bv + c * IY * G::PITCH;
+  for (int it = threadIdx.x; it < IY * G::AX; it += INT) {
+    const int r = it / G::AX, col = it - r * G::AX;
     float s = 0.f;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) s = fmaf(b3(m), Ac[(r + m * d) * IAX + col], s);
-    Bc[r * IBX + col] = s;
+    for (int m = 0; m < 5; ++m) s = fmaf(b3(m), Ac[(r + m * D) * G::PITCH + col], s);
+    Bc[r * G::PITCH + col] = s;
   }
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int r = ry + q * (IY / 2);
+  for (int q = 0; q < IQ; ++q) {
+    const int r = ry + q * (INT / IX);
     float s = 0.f;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) s = fmaf(b3(m), Bc[r * IBX + rx + m * d], s);
+    for (int m = 0; m < 5; ++m) s = fmaf(b3(m), Bc[r * G::PITCH + rx + m * D], s);
     out[q] = s;
   }
 }
 
-template <int CH, int MODE>
+template <int CH, int MODE, int D>
 __global__ void __launch_bounds__(INT) k_iuwt_ana(IuwtArgs a) {
+  using G = Geo<D>;
   extern __shared__ float ism[];
-  float *A = ism;                       // [CH][IAY][IAX]
-  float *Bv = A + CH * IAY * IAX;       // [CH][IY][IBX]
-  const int n = a.n, d = 1 << a.j;
+  float *A = ism;                        // [CH][AY][PITCH]
+  float *Bv = A + CH * G::AY * G::PITCH; // [CH][IY][PITCH]
+  const int n = a.n;
   const int ntx = (n + IX - 1) / IX;
   const int x0 = (blockIdx.x % ntx) * IX, y0 = (blockIdx.x / ntx) * IY;
   const int l = blockIdx.y;
@@ -124,30 +181,22 @@ __global__ void __launch_bounds__(INT) k_iuwt_ana(IuwtArgs a) {
     mu = (float)S.mu;
     sbl = (float)(S.sigma * (double)a.beta[l]);
   }
-  const int ay = IY + 4 * d, ax = IX + 4 * d;
-  for (int it = threadIdx.x; it < ay * ax; it += INT) {
-    const int r = it / ax, col = it - r * ax;
-    const size_t pix = (size_t)wrap(y0 - 2 * d + r, n) * n + wrap(x0 - 2 * d + col, n);
-    float w[CH];
-    ana_src<CH, MODE>(a, l, pix, mu, w);
-#pragma unroll
-    for (int c = 0; c < CH; ++c) A[(c * IAY + r) * IAX + col] = w[c];
-  }
+  load_tile<CH, D, true, MODE>(a, A, y0, x0, l, mu);
   __syncthreads();
-  const int rx = threadIdx.x % IX, ry = threadIdx.x / IX;   // rows ry, ry + 8
+  const int rx = threadIdx.x % IX, ry = threadIdx.x / IX;
   const bool last = a.j == a.J - 1;
   uint32_t keep = 0;
 #pragma unroll 1
   for (int c = 0; c < CH; ++c) {
-    float cn[2];
-    smooth_tile<CH>(A, Bv, d, c, ry, rx, cn);
+    float cn[IQ];
+    smooth_tile<D>(A, Bv, c, ry, rx, cn);
     const float q = MODE == WAVE_ITERATE ? (c == 1 ? sbl : sbl * mu) : 1.f;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int r = ry + k * (IY / 2);
+    for (int k = 0; k < IQ; ++k) {
+      const int r = ry + k * (INT / IX);
       const int yy = y0 + r, xx = x0 + rx;
       if (yy >= n || xx >= n) continue;
-      const float cj = A[(c * IAY + r + 2 * d) * IAX + rx + 2 * d];
+      const float cj = A[(c * G::AY + r + 2 * D) * G::PITCH + rx + 2 * D];
       const size_t pix = (size_t)yy * n + xx;
       float *up = a.u + ((size_t)(c * a.L + l) * a.P) * NN + pix;
       // planes j (detail) and, at the last scale, J (coarse)
@@ -160,7 +209,7 @@ __global__ void __launch_bounds__(INT) k_iuwt_ana(IuwtArgs a) {
           *uq = val;
         } else {
           const float p = fmaf(q, val, *uq);
-          const uint32_t bit = 1u << (2 * s + k);
+          const uint32_t bit = 1u << (2 * k + s);
           if (c == 0) {
             *uq = satf(p);
             if (fabsf(p) <= 1.0f) keep |= bit;
@@ -171,50 +220,31 @@ __global__ void __launch_bounds__(INT) k_iuwt_ana(IuwtArgs a) {
       }
       if (!last) a.buf[(a.j + 1) & 1][c * CS + (size_t)l * NN + pix] = cn[k];
     }
-    __syncthreads();
   }
 }
 
-// synthesis source of scale j: P_J - P_{J-1} at the coarsest step, else the
-// running image of scale j + 1
-template <int CH, int MODE>
-__device__ __forceinline__ float syn_src(const IuwtArgs &a, int c, int l, size_t pix) {
-  const size_t NN = (size_t)a.n * a.n, CS = (size_t)a.L * NN;
-  if (a.j == a.J - 1) {
-    const float *u = (MODE == WAVE_TRANSFORM ? a.in : a.ur) +
-                     ((size_t)(c * a.L + l) * a.P) * NN + pix;
-    return u[(size_t)a.J * NN] - u[(size_t)(a.J - 1) * NN];
-  }
-  return a.buf[(a.j + 1) & 1][c * CS + (size_t)l * NN + pix];
-}
-
-template <int CH, int MODE>
+template <int CH, int MODE, int D>
 __global__ void __launch_bounds__(INT) k_iuwt_syn(IuwtArgs a) {
+  using G = Geo<D>;
   extern __shared__ float ism[];
   float *A = ism;
-  float *Bv = A + CH * IAY * IAX;
-  const int n = a.n, d = 1 << a.j;
+  float *Bv = A + CH * G::AY * G::PITCH;
+  const int n = a.n;
   const int ntx = (n + IX - 1) / IX;
   const int x0 = (blockIdx.x % ntx) * IX, y0 = (blockIdx.x / ntx) * IY;
   const int l = blockIdx.y;
   const size_t NN = (size_t)n * n, CS = (size_t)a.L * NN;
-  const int ay = IY + 4 * d, ax = IX + 4 * d;
-  for (int it = threadIdx.x; it < ay * ax; it += INT) {
-    const int r = it / ax, col = it - r * ax;
-    const size_t pix = (size_t)wrap(y0 - 2 * d + r, n) * n + wrap(x0 - 2 * d + col, n);
-#pragma unroll
-    for (int c = 0; c < CH; ++c) A[(c * IAY + r) * IAX + col] = syn_src<CH, MODE>(a, c, l, pix);
-  }
+  load_tile<CH, D, false, MODE>(a, A, y0, x0, l, 0.f);
   __syncthreads();
   const int rx = threadIdx.x % IX, ry = threadIdx.x / IX;
-  float o[CH][2];
+  float o[CH][IQ];
 #pragma unroll 1
   for (int c = 0; c < CH; ++c) {
-    float sr[2];
-    smooth_tile<CH>(A, Bv, d, c, ry, rx, sr);
+    float sr[IQ];
+    smooth_tile<D>(A, Bv, c, ry, rx, sr);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int yy = y0 + ry + k * (IY / 2), xx = x0 + rx;
+    for (int k = 0; k < IQ; ++k) {
+      const int yy = y0 + ry + k * (INT / IX), xx = x0 + rx;
       o[c][k] = 0.f;
       if (yy >= n || xx >= n) continue;
       const size_t pix = (size_t)yy * n + xx;
@@ -227,13 +257,14 @@ __global__ void __launch_bounds__(INT) k_iuwt_syn(IuwtArgs a) {
         o[c][k] = u[0] + sr[k];
       }
     }
-    __syncthreads();
   }
   if (a.j > 0) return;
   const float mu = (MODE == WAVE_ITERATE) ? (float)a.sc[l / a.Lc].mu : 0.f;
+  const float tau = (MODE == WAVE_ITERATE) ? (float)a.sc[l / a.Lc].tau : 0.f;
+  const float bl = (MODE == WAVE_ITERATE) ? a.beta[l] : 0.f;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int yy = y0 + ry + k * (IY / 2), xx = x0 + rx;
+  for (int k = 0; k < IQ; ++k) {
+    const int yy = y0 + ry + k * (INT / IX), xx = x0 + rx;
     if (yy >= n || xx >= n) continue;
     const size_t i0 = (size_t)l * NN + (size_t)yy * n + xx;
     if (MODE == WAVE_TRANSFORM) {
@@ -244,8 +275,6 @@ __global__ void __launch_bounds__(INT) k_iuwt_syn(IuwtArgs a) {
     float acc[CH];
     acc[0] = o[0][k];
     if (CH == 3) { acc[1] = fmaf(mu, o[1][k], o[0][k]); acc[2] = o[2][k]; }
-    const float tau = (float)a.sc[l / a.Lc].tau;
-    const float bl = a.beta[l];
     bool keep = true;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -260,15 +289,32 @@ __global__ void __launch_bounds__(INT) k_iuwt_syn(IuwtArgs a) {
 
 inline int itiles(int n) { return ((n + IX - 1) / IX) * ((n + IY - 1) / IY); }
 
-template <typename K>
-void set_smem(K kern, size_t bytes) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+template <int CH, int MODE, int D>
+cudaError_t launch_ana_d(const IuwtArgs &a, int L, int n, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_iuwt_ana<CH, MODE, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)iuwt_smem<D>(CH));
+    attr = true;
+  }
+  k_iuwt_ana<CH, MODE, D><<<dim3(itiles(n), L), INT, iuwt_smem<D>(CH), st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int CH, int MODE, int D>
+cudaError_t launch_syn_d(const IuwtArgs &a, int L, int n, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_iuwt_syn<CH, MODE, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)iuwt_smem<D>(CH));
+    attr = true;
+  }
+  k_iuwt_syn<CH, MODE, D><<<dim3(itiles(n), L), INT, iuwt_smem<D>(CH), st>>>(a);
+  return cudaGetLastError();
 }
 
 template <int CH, int MODE>
 cudaError_t ana_all(const WaveArgs &w, IuwtArgs a, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) { set_smem(k_iuwt_ana<CH, MODE>, iuwt_smem(CH)); attr = true; }
   const double vox = (double)CH * w.L * w.n * w.n;
   for (int j = 0; j < w.J; ++j) {
     a.j = j;
@@ -276,8 +322,13 @@ cudaError_t ana_all(const WaveArgs &w, IuwtArgs a, cudaStream_t st) {
                                 (MODE == WAVE_ITERATE ? 8.0 : 4.0) * (j == w.J - 1 ? 2 : 1) +
                                 (j == w.J - 1 ? 0.0 : 4.0));
     ProfScope ps(w.prof, "iuwt_ana_dual", bytes, vox * 22.0, st);
-    k_iuwt_ana<CH, MODE><<<dim3(itiles(w.n), w.L), INT, iuwt_smem(CH), st>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    switch (j) {
+      case 0: e = launch_ana_d<CH, MODE, 1>(a, w.L, w.n, st); break;
+      case 1: e = launch_ana_d<CH, MODE, 2>(a, w.L, w.n, st); break;
+      case 2: e = launch_ana_d<CH, MODE, 4>(a, w.L, w.n, st); break;
+      default: e = launch_ana_d<CH, MODE, 8>(a, w.L, w.n, st); break;
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -285,16 +336,19 @@ cudaError_t ana_all(const WaveArgs &w, IuwtArgs a, cudaStream_t st) {
 
 template <int CH, int MODE>
 cudaError_t syn_all(const WaveArgs &w, IuwtArgs a, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) { set_smem(k_iuwt_syn<CH, MODE>, iuwt_smem(CH)); attr = true; }
   const double vox = (double)CH * w.L * w.n * w.n;
   for (int j = w.J - 1; j >= 0; --j) {
     a.j = j;
     const double bytes = vox * ((j == w.J - 1 ? 8.0 : 4.0) + 8.0 * (j > 0) + 4.0 * (j == 0) +
                                 (j > 0 ? 4.0 : (MODE == WAVE_ITERATE ? 16.0 : 4.0)));
     ProfScope ps(w.prof, j == 0 ? "iuwt_syn_prox" : "iuwt_syn", bytes, vox * 22.0, st);
-    k_iuwt_syn<CH, MODE><<<dim3(itiles(w.n), w.L), INT, iuwt_smem(CH), st>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    switch (j) {
+      case 0: e = launch_syn_d<CH, MODE, 1>(a, w.L, w.n, st); break;
+      case 1: e = launch_syn_d<CH, MODE, 2>(a, w.L, w.n, st); break;
+      case 2: e = launch_syn_d<CH, MODE, 4>(a, w.L, w.n, st); break;
+      default: e = launch_syn_d<CH, MODE, 8>(a, w.L, w.n, st); break;
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
