@@ -67,7 +67,7 @@ constexpr int QXP = 2, QYP = 2;                      // coefficient positions pe
 constexpr int QXS = 4;                               // scalar synthesis row item
 
 constexpr size_t ana_smem(int ch) {
-  return ((size_t)ch * A_RP * A_IP + 4 * A_RP * A_LP) * sizeof(float2);
+  return ((size_t)ch * A_RP * A_IP + 2 * A_RP * A_LP) * sizeof(float2);
 }
 constexpr size_t syn_smem(int) {
   return (size_t)(8 * S_CH * S_CP) * sizeof(float) + (size_t)(2 * TY * S_LP) * sizeof(float2);
@@ -133,12 +133,9 @@ __device__ __forceinline__ void ana_emit(const AnaArgs &a, int l, int bb,
 //              NT threads), four subbands of QY coefficients; out = sum_s
 //              (h_2s, h_2s+1) . (lo_2(k+s), lo_2(k+s)+1), the even and odd
 //              taps summed in the two lanes.
-// The CTA runs them as a pipeline: in the phase of step s it does the
-// column pass and dual update of step s, then requests the U values of step
-// s + 1 and runs the row pass of step s + 1 into the other lo/hi buffer, so
-// one barrier separates the steps and the U loads have a whole phase to
-// arrive.  Channel 0 records the mask Pi(p) of each output in `keep`;
-// derivative channels (c > 0) apply it.
+// The U values a step updates are requested before its row pass so their
+// latency overlaps the filtering.  Channel 0 records the mask Pi(p) of each
+// output in `keep`; derivative channels (c > 0) apply it.
 template <int P>
 __device__ __forceinline__ void ana_rows(const float2 *in_c, float2 *lo_s, float2 *hi_s) {
   constexpr int RP = TY + P - 1;
@@ -281,10 +278,10 @@ __device__ __forceinline__ void ana_emit_step(const AnaArgs &a, int l, int bb, i
 }
 
 template <int CH, int MODE, bool LEVEL1>
-__global__ void __launch_bounds__(NT, 3) k_ana(AnaArgs a) {
+__global__ void __launch_bounds__(NT, 4) k_ana(AnaArgs a) {
   extern __shared__ float2 smem2[];
   float2 *in_s = smem2;                     // [CH][A_RP][A_IP] row pairs
-  float2 *lohi = in_s + CH * A_RP * A_IP;   // 2 x ([A_RP][A_LP] lo, hi)
+  float2 *lohi = in_s + CH * A_RP * A_IP;   // [A_RP][A_LP] lo, then hi
   const int h = a.M >> 1;
   const int ntx = (h + TX - 1) / TX;
   const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
@@ -343,35 +340,25 @@ __global__ void __launch_bounds__(NT, 3) k_ana(AnaArgs a) {
     if (two) store_item(it + NT, w1);
   }
   __syncthreads();
-  // (basis, chain) steps, pipelined: column pass + dual update of step s,
-  // then the U loads and the row pass of step s + 1 (other lo/hi buffer)
+  // (basis, chain) steps: U requests, row pass, column pass + dual update.
+  // One lo/hi buffer keeps shared memory at 4 CTAs per SM, which hides the
+  // U loads better than software-pipelining the steps with two buffers.
   const int b0 = LEVEL1 ? 0 : b;
   const int nsteps = (LEVEL1 ? a.K : 1) * CH;
   constexpr int LH = A_RP * A_LP;
-  float pre[4][QY], nxt[4][QY];
-  ana_prefetch<MODE>(a, l, b0, 0, kx0, ky0, pre);
-  ana_rows_dispatch(b0 + 1, in_s, lohi, lohi + LH);
-  __syncthreads();
   uint32_t keep = 0;
 #pragma unroll 1
   for (int s = 0; s < nsteps; ++s) {
     const int bb = b0 + s / CH, c = s % CH;
-    float2 *lo_s = lohi + (s & 1) * 2 * LH;
+    float pre[4][QY];
+    ana_prefetch<MODE>(a, l, bb, c, kx0, ky0, pre);
+    ana_rows_dispatch(bb + 1, in_s + c * A_RP * A_IP, lohi, lohi + LH);
+    __syncthreads();
     float cf[4][QY];
-    ana_cols_dispatch(bb + 1, lo_s, lo_s + LH, cf);
+    ana_cols_dispatch(bb + 1, lohi, lohi + LH, cf);
     // dual step scale: sigma mu_l (primal, d/dgamma), sigma beta_l (d/dmu)
     const float qc = MODE == WAVE_ITERATE ? (c == 1 ? sbl : sbl * mu) : 1.f;
     ana_emit_step<MODE>(a, l, bb, c, kx0, ky0, qc, cf, pre, keep);
-    if (s + 1 < nsteps) {
-      const int nb = b0 + (s + 1) / CH, nc = (s + 1) % CH;
-      ana_prefetch<MODE>(a, l, nb, nc, kx0, ky0, nxt);
-      float2 *lo_n = lohi + ((s + 1) & 1) * 2 * LH;
-      ana_rows_dispatch(nb + 1, in_s + nc * A_RP * A_IP, lo_n, lo_n + LH);
-#pragma unroll
-      for (int sb = 0; sb < 4; ++sb)
-#pragma unroll
-        for (int qq = 0; qq < QY; ++qq) pre[sb][qq] = nxt[sb][qq];
-    }
     __syncthreads();
   }
 }
@@ -620,7 +607,7 @@ __device__ __forceinline__ void syn_dispatch(int p, const float *cf, float *lo,
 // Both variants compute the same sums in the same order (identical results);
 // which is faster depends on the shape, so the plan's tuner picks one.
 template <int CH, int MODE, bool LEVEL1, bool PACKED>
-__global__ void __launch_bounds__(NT, 3) k_syn(SynArgs a) {
+__global__ void __launch_bounds__(NT, 4) k_syn(SynArgs a) {
   constexpr int ROWS = PACKED ? 2 : 1;   // pixel rows per thread
   constexpr int NO = PACKED ? 2 * QXP : 2 * QXS;   // pixels per row
   extern __shared__ float smem[];
