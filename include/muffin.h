@@ -184,6 +184,15 @@ typedef struct {
 MUFFIN_API muffin_status muffin_plan_autotune(muffin_plan plan, const char *cache_path,
                                               muffin_tune_info *info);
 
+/* Spectral step kernel for plans with 64 bands: 1 (default for L = 64) runs
+ * it on the tcgen05 tensor cores (tensor-memory accumulators, operands in
+ * shared memory), 0 on the warp-level mma.sync kernel used for other band
+ * counts.  Both compute the same 3xTF32 products; their FP32 rounding order
+ * differs, so results agree to FP32 accuracy, not bit for bit.  Drops
+ * captured graphs and the iterate state.  Errors: EINVAL (NULL plan, or 1
+ * with L != 64). */
+MUFFIN_API muffin_status muffin_plan_set_spectral_kernel(muffin_plan plan, int32_t tcgen05);
+
 /* Sets the variants directly (syn_packed in 0..3, dct_ctas_per_sm >= 0);
  * drops captured graphs.  Errors: EINVAL. */
 MUFFIN_API muffin_status muffin_plan_set_tuning(muffin_plan plan, int32_t syn_packed,

@@ -151,6 +151,11 @@ class Plan:
         native.check(self._lib.muffin_plan_autotune(self._h, path, ctypes.byref(info)))
         return info
 
+    def set_spectral_kernel(self, tcgen05: bool) -> None:
+        """Spectral step on the tcgen05 tensor cores (64-band plans) or on
+        the mma.sync kernel."""
+        native.check(self._lib.muffin_plan_set_spectral_kernel(self._h, int(bool(tcgen05))))
+
     def set_tuning(self, syn_packed: int = 0, dct_ctas_per_sm: int = 0) -> None:
         native.check(self._lib.muffin_plan_set_tuning(self._h, int(syn_packed),
                                                       int(dct_ctas_per_sm)))

@@ -487,6 +487,7 @@ cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st) {
   a.a1hi = d.chi; a.a1lo = d.clo; a.a2hi = d.cthi; a.a2lo = d.ctlo;
   a.alpha = d.alpha; a.sc = d.sc; a.ctas_per_sm = d.ctas_per_sm;
   a.xt = gr.xt; a.x = gr.x; a.v = gr.v; a.t = gr.t;
+  if (d.tc && d.L == 64 && d.Lp == 64) return dct_dual_tc(d, gr, d.err, st);
   if (d.Lp <= 64) {
     if (gr.C == 3) return launch_dct_small<3>(a, st, d.prof);
     return launch_dct_small<1>(a, st, d.prof);

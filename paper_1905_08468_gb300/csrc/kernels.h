@@ -219,11 +219,15 @@ struct DctArgs {
   const float *alpha;      // [B][n*n] pixel weights
   const DevScalars *sc;    // [B]
   int ctas_per_sm;         // persistent spectral grid: CTAs per SM (0: max resident)
+  int tc;                  // 1: tcgen05 kernel (L = 64), 0: mma.sync kernel
+  int *err;                // device flag raised when a tensor-core wait gives up
   Prof *prof;              // optional per-kernel timing
 };
 // Spectral dual update and back-projection (Alg. 2 eqs. vt, v, upt and the
 // derivative forms of Algs. 3/4): reads gr.xt, gr.x, gr.v -> gr.v, gr.t.
 cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st);
+// The same step on the tcgen05 tensor cores (dct_tc.cu), L = Lp = 64.
+cudaError_t dct_dual_tc(const DctArgs &d, const Group &gr, int *err, cudaStream_t st);
 // Operator: out^n = C in^n (inverse = 0) or C^T in^n (inverse = 1).
 cudaError_t dct_op(const DctArgs &d, const float *in, float *out, int inverse,
                    cudaStream_t st);

@@ -260,6 +260,8 @@ muffin_status plan_alloc_init(muffin_plan P, const float *alpha, const float *be
   CK(P->alloc(&P->sc, (size_t)B));
   CK(P->alloc(&P->cube_const, (size_t)4 * B));
   CK(P->alloc(&P->rec_count, 1));
+  CK(P->alloc(&P->kerr, 1));
+  CK(cudaMemsetAsync(P->kerr, 0, sizeof(int), P->ws));
   CK(P->alloc(&P->dred, kRedSure + 65 * (size_t)Lt + 6 * (size_t)(Lt > 4096 ? Lt : 4096)));
   CK(P->alloc(&P->wband, (size_t)Lt));
   CK(P->alloc(&P->S, (size_t)P->Cmax * Lt * nh * n));
@@ -427,7 +429,16 @@ void drop_graphs_and_state(muffin_plan P) {
 muffin_status leave(muffin_plan P, bool sync) {
   CK(cudaEventRecord(P->ev_out, P->ws));
   CK(cudaStreamWaitEvent(P->st, P->ev_out, 0));
-  if (sync) CK(cudaStreamSynchronize(P->ws));
+  if (sync) {
+    CK(cudaStreamSynchronize(P->ws));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, P->kerr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      CK(cudaMemset(P->kerr, 0, sizeof(int)));
+      P->prof.resolve();
+      return fail(MUFFIN_ETIMEOUT, "spectral kernel: a bounded tensor-core wait gave up");
+    }
+  }
   P->prof.resolve();
   return MUFFIN_OK;
 }
@@ -548,12 +559,12 @@ size_t estimate_bytes(const muffin_params *p) {
   else
     for (int j = 1; j < p->levels; ++j) ll += C * Lt * K * (n >> j) * (n >> j);
   size_t b = 3 * NL * 16 + Lt * nh * n * 4 + (size_t)fft32_table_len((int)n) * 8 + n * 16 +
-             4 * Lp * Lp * 4 + B * N * 4 + Lt * 4 + B * sizeof(DevScalars) + B * 32 + 4 +
+             4 * Lp * Lp * 4 + B * N * 4 + Lt * 4 + B * sizeof(DevScalars) + B * 32 + 4 + 4 +
              (kRedSure + 65 * Lt + 6 * (Lt > 4096 ? Lt : 4096)) * 8 + Lt * 8 +
              C * Lt * nh * n * 8 + (ll ? ll : 1) * 4 + 3 * NL * 4 +
              C * NL * (5 + K) * 4;
   if (p->sure) b += 3 * NL * (5 + K) * 4 + 2 * NL * 4;
-  return b + (p->sure ? 36 : 28) * 16;   // 16 bytes of slack per allocation
+  return b + (p->sure ? 37 : 29) * 16;   // 16 bytes of slack per allocation
 }
 
 muffin_status create(const muffin_params *p, const float *psf, const float *alpha,
@@ -572,6 +583,7 @@ muffin_status create(const muffin_params *p, const float *psf, const float *alph
   P->p = *p;
   P->n = p->n; P->L = p->nbands; P->J = p->levels;
   P->dict = p->dictionary;
+  P->dct_tc = p->nbands == 64 ? 1 : 0;
   P->K = P->dict == 1 ? p->levels + 1 : p->n_wavelets;
   P->wsn2 = P->dict == 1 ? iuwt_norm2(p->n, p->levels) : (double)p->n_wavelets;
   P->B = p->batch; P->Lt = P->B * P->L;

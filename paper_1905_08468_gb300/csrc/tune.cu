@@ -149,6 +149,16 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
 
 extern "C" {
 
+muffin_status muffin_plan_set_spectral_kernel(muffin_plan P, int32_t tcgen05) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  if (tcgen05 != 0 && tcgen05 != 1) return fail(MUFFIN_EINVAL, "tcgen05 must be 0 or 1");
+  if (tcgen05 && P->L != 64)
+    return fail(MUFFIN_EINVAL, "the tcgen05 spectral kernel needs 64 bands (plan has %d)", P->L);
+  muffin::pi::drop_graphs_and_state(P);
+  P->dct_tc = tcgen05;
+  return MUFFIN_OK;
+}
+
 muffin_status muffin_plan_set_tuning(muffin_plan P, int32_t syn_packed, int32_t dct_ctas_per_sm) {
   if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
   if (syn_packed < 0 || syn_packed > 3)
