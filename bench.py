@@ -205,7 +205,7 @@ def workload_config(args, oracle=False) -> dict:
            "window": args.window,
            "wavelets": ("IUWT (starlet), 3 scales" if getattr(args, "dictionary", "daubechies") == "iuwt"
                         else "db1..db8, 3 levels"),
-           "spectral": "DCT-II (3xTF32 tensor cores)", "chains": 6,
+           "spectral": "DCT-II, 3xTF32 products on the tensor cores (tcgen05 for 64 bands, else mma.sync)", "chains": 6,
            "theta0": list(THETA0), "eta": list(ETA),
            "l2": "inputs larger than L2 (state ~26 GB per cube)"}
     if oracle:
@@ -478,6 +478,7 @@ def main() -> None:
     elif not args.no_autotune:
         ti = plan.autotune()            # launch variants for this shape (results unchanged)
         tuning = {"syn_packed": ti.syn_packed, "dct_ctas_per_sm": ti.dct_ctas_per_sm,
+                  "spectral_tcgen05": ti.spectral_tcgen05,
                   "candidates": ti.candidates, "iter_ms_default": ti.ms_default,
                   "iter_ms_tuned": ti.ms_best}
     kw = dict(window=args.window, eta=ETA, eps=eps)

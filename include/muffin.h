@@ -154,8 +154,10 @@ MUFFIN_API muffin_status muffin_plan_weights_from_x0(muffin_plan plan, const flo
 
 /* ---- per-shape tuning (launch variants of the hot kernels)
  *
- * Two launch choices change speed but not results (every variant computes
- * the same sums in the same order, so outputs are bit-identical):
+ * For 64-band plans the tuner also times the two spectral kernels (tcgen05
+ * and mma.sync), whose results agree to FP32 accuracy.  Two further launch
+ * choices change speed but not results (every variant computes the same
+ * sums in the same order, so outputs are bit-identical):
  *   syn_packed       bit 0: coarse wavelet synthesis levels, bit 1: level 1;
  *                    0 = scalar row pass (one pixel row per thread),
  *                    1 = packed row pass (two rows per fma.rn.f32x2);
@@ -164,7 +166,9 @@ MUFFIN_API muffin_status muffin_plan_weights_from_x0(muffin_plan plan, const flo
  * Which is fastest depends on the cube shape and the GPU. */
 typedef struct {
   int32_t syn_packed;      /* chosen synthesis variant bits */
-  int32_t dct_ctas_per_sm; /* chosen spectral grid (0 = all resident) */
+  int32_t dct_ctas_per_sm; /* chosen grid of the mma.sync spectral kernel (0 = all resident) */
+  int32_t spectral_tcgen05;/* 1: spectral step on tcgen05 (64-band plans, see
+                              muffin_plan_set_spectral_kernel) */
   int32_t from_cache;      /* 1: taken from the in-process or file cache */
   int32_t candidates;      /* configurations timed (0 when cached) */
   double ms_default;       /* one iteration of every chain group, default */
@@ -176,8 +180,8 @@ typedef struct {
  * with sure = 1, one plain group otherwise), keeps the fastest and caches it
  * per shape (n, bands, batch, chains, levels, bases, SM count, device name):
  * in process, and in the text file `cache_path` when it is not NULL (read
- * first, one line appended per new shape; lines that do not parse are
- * ignored).  The timing iterations overwrite the plan's iterate state: a
+ * first, one line "muffin-tune-2 <key> <syn_packed> <dct_ctas> <tcgen05>"
+ * appended per new shape; lines that do not parse are ignored).  The timing iterations overwrite the plan's iterate state: a
  * following solve or sure_tune must start cold (warm = 0; a warm call
  * returns MUFFIN_ESTATE), and captured graphs are rebuilt.  info may be NULL.
  * Errors: EINVAL (plan NULL), ECUDA. */

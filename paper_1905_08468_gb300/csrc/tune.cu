@@ -21,6 +21,7 @@ using muffin::fail;
 struct Choice {
   int syn_packed = 0;
   int dct_ctas = 0;
+  int dct_tc = 0;      // spectral step on tcgen05 (64-band plans)
 };
 
 std::mutex g_mu;
@@ -42,19 +43,20 @@ std::string shape_key(muffin_plan P) {
   return buf;
 }
 
-// the last line "muffin-tune-1 <key> <syn_packed> <dct_ctas>" with this key
+// the last line "muffin-tune-2 <key> <syn_packed> <dct_ctas> <dct_tc>" with this key
 bool file_lookup(const char *path, const std::string &key, Choice *c) {
   FILE *f = std::fopen(path, "r");
   if (!f) return false;
   char line[512], tag[32], k[400];
   bool found = false;
   while (std::fgets(line, sizeof line, f)) {
-    int a = 0, b = 0;
-    if (std::sscanf(line, "%31s %399s %d %d", tag, k, &a, &b) != 4) continue;
-    if (std::strcmp(tag, "muffin-tune-1") != 0 || key != k) continue;
-    if (a < 0 || a > 3 || b < 0) continue;
+    int a = 0, b = 0, t = 0;
+    if (std::sscanf(line, "%31s %399s %d %d %d", tag, k, &a, &b, &t) != 5) continue;
+    if (std::strcmp(tag, "muffin-tune-2") != 0 || key != k) continue;
+    if (a < 0 || a > 3 || b < 0 || t < 0 || t > 1) continue;
     c->syn_packed = a;
     c->dct_ctas = b;
+    c->dct_tc = t;
     found = true;
   }
   std::fclose(f);
@@ -64,13 +66,14 @@ bool file_lookup(const char *path, const std::string &key, Choice *c) {
 void file_append(const char *path, const std::string &key, const Choice &c) {
   FILE *f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "muffin-tune-1 %s %d %d\n", key.c_str(), c.syn_packed, c.dct_ctas);
+  std::fprintf(f, "muffin-tune-2 %s %d %d %d\n", key.c_str(), c.syn_packed, c.dct_ctas, c.dct_tc);
   std::fclose(f);
 }
 
 void apply(muffin_plan P, const Choice &c) {
   P->syn_packed = c.syn_packed;
   P->dct_ctas = c.dct_ctas;
+  P->dct_tc = P->L == 64 ? c.dct_tc : 0;
 }
 
 // mean time of one iteration of every chain group with choice c
@@ -109,6 +112,7 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
   const double vox = (double)P->NL * P->Cmax * (P->p.sure ? 2 : 1);
   const int reps = vox >= 2e7 ? 3 : (vox >= 1e6 ? 5 : 10);
   Choice cur{};
+  cur.dct_tc = P->L == 64 ? 1 : 0;       // the default kernel for 64 bands
   double t_def = 0.0, t_best = 0.0;
   int cand = 0;
   if (s == MUFFIN_OK) s = time_choice(P, cur, reps, e0, e1, &t_def);
@@ -124,7 +128,15 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
     ++cand;
     if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
   }
-  for (int k = 1; k <= 2 && s == MUFFIN_OK; ++k) {
+  if (P->L == 64 && s == MUFFIN_OK) {     // the other spectral kernel
+    Choice c = *best;
+    c.dct_tc = 0;
+    double t = 0.0;
+    s = time_choice(P, c, reps, e0, e1, &t);
+    ++cand;
+    if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
+  }
+  for (int k = 1; k <= 2 && s == MUFFIN_OK && !best->dct_tc; ++k) {
     Choice c = *best;
     c.dct_ctas = k;
     double t = 0.0;
@@ -193,6 +205,7 @@ muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin
     if (info) {
       info->syn_packed = c.syn_packed;
       info->dct_ctas_per_sm = c.dct_ctas;
+      info->spectral_tcgen05 = P->dct_tc;
       info->from_cache = 1;
     }
     return MUFFIN_OK;
@@ -210,6 +223,7 @@ muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin
   if (info) {
     info->syn_packed = c.syn_packed;
     info->dct_ctas_per_sm = c.dct_ctas;
+    info->spectral_tcgen05 = P->dct_tc;
     info->from_cache = 0;
   }
   return MUFFIN_OK;

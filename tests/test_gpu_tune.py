@@ -74,7 +74,7 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         p.solve(dev(c.dirty, torch), x, 13, 1e-2, 2e-2)
         assert torch.equal(x, ref)
     lines = [ln.split() for ln in cache.read_text().splitlines()]
-    assert len(lines) == 1 and lines[0][0] == "muffin-tune-1" and "n=64,L=8" in lines[0][1]
+    assert len(lines) == 1 and lines[0][0] == "muffin-tune-2" and "n=64,L=8" in lines[0][1]
     # the same shape again: in-process cache
     with pkg.Plan(64, 8, c.psf) as p:
         again = p.autotune(str(cache))
@@ -82,7 +82,8 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         assert (again.syn_packed, again.dct_ctas_per_sm) == (info.syn_packed, info.dct_ctas_per_sm)
     # a shape only the file knows (written by hand), beside lines to ignore
     key = lines[0][1].replace("n=64,L=8", "n=16,L=8")
-    cache.write_text("garbage line\nmuffin-tune-1 %s 9 1\nmuffin-tune-1 %s 2 1\n" % (key, key))
+    cache.write_text("garbage line\nmuffin-tune-2 %s 9 1 0\nmuffin-tune-1 %s 3 2\n"
+                     "muffin-tune-2 %s 2 1 0\n" % (key, key, key))
     c16 = make_cube(16, 8, 4, 1, 480, seed=841)
     with pkg.Plan(16, 8, c16.psf) as p:
         got = p.autotune(str(cache))
