@@ -197,6 +197,17 @@ MUFFIN_API muffin_status muffin_plan_autotune(muffin_plan plan, const char *cach
  * with L != 64). */
 MUFFIN_API muffin_status muffin_plan_set_spectral_kernel(muffin_plan plan, int32_t tcgen05);
 
+/* Failure-path test hook (the paper has no counterpart).  on = 1 makes the
+ * tcgen05 spectral kernel skip its tensor-core products, so its bounded
+ * waits on their completion run out: the kernel raises the plan's error
+ * flag, frees its tensor memory and returns, and the next call that
+ * synchronises (solve, sure_tune, ...) returns MUFFIN_ETIMEOUT; the results
+ * of that call are unspecified and the plan stays usable.  Only plans whose
+ * spectral step runs on tcgen05 (64 bands) wait on the device at all.
+ * on = 0 restores normal operation.  Drops captured graphs and the iterate
+ * state.  Errors: EINVAL (NULL plan). */
+MUFFIN_API muffin_status muffin_plan_inject_timeout(muffin_plan plan, int32_t on);
+
 /* Sets the variants directly (syn_packed in 0..3, dct_ctas_per_sm >= 0);
  * drops captured graphs.  Errors: EINVAL. */
 MUFFIN_API muffin_status muffin_plan_set_tuning(muffin_plan plan, int32_t syn_packed,

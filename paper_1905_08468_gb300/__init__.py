@@ -156,6 +156,10 @@ class Plan:
         the mma.sync kernel."""
         native.check(self._lib.muffin_plan_set_spectral_kernel(self._h, int(bool(tcgen05))))
 
+    def inject_timeout(self, on: bool) -> None:
+        """Test hook: make the tensor-core waits of the next calls run out."""
+        native.check(self._lib.muffin_plan_inject_timeout(self._h, int(bool(on))))
+
     def set_tuning(self, syn_packed: int = 0, dct_ctas_per_sm: int = 0) -> None:
         native.check(self._lib.muffin_plan_set_tuning(self._h, int(syn_packed),
                                                       int(dct_ctas_per_sm)))

@@ -22,7 +22,9 @@
 // own their A tiles, 128 tensor-memory columns and mbarrier, so one group's
 // global traffic overlaps the other's MMAs.  Waits on the mbarriers are
 // bounded: on time-out the kernel raises an error flag, waits once more and
-// frees its tensor memory.
+// frees its tensor memory; the host turns the flag into MUFFIN_ETIMEOUT.  A
+// host-side test hook makes the kernel skip its products so that this path
+// runs without any fault.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,6 +43,7 @@ constexpr uint32_t CMAT_B = TL * TL * 4;         // one C table (16 KB)
 constexpr size_t SMEM = 4 * (size_t)CMAT_B + (size_t)NG * 2 * TILE_B + 1024;
 constexpr uint32_t TMEM_COLS = 256;              // two groups x (64 + 64) FP32 columns
 constexpr long kSpin = 1L << 24;                 // polls of an mbarrier before giving up
+constexpr long kSpinInjected = 1L << 12;         // shorter bound when a time-out is injected
 // instruction descriptor: D FP32, A and B TF32, both K-major, N = 64, M = 128
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) |
                            ((uint32_t)(TL >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
@@ -54,6 +57,8 @@ struct TcArgs {
   const float *xt, *x;         // [C][B*L][n*n]
   float *v, *t;
   int *err;                    // set to 1 when a wait gives up
+  int inject;                  // test hook: issue no products, so the waits run out
+  long spin;                   // polls of an mbarrier before giving up
 };
 
 // byte offset of element (row, k) of a K-major operand with 64 columns
@@ -133,9 +138,9 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
 }
 
 // bounded wait for the phase `ph` of an mbarrier; true when it completed
-__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t ph) {
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t ph, long spin) {
   uint32_t done = 0;
-  for (long it = 0; it < kSpin && !done; ++it)
+  for (long it = 0; it < spin && !done; ++it)
     asm volatile("{\n\t.reg .pred q;\n\tmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n\t"
                  "selp.u32 %0, 1, 0, q;\n\t}" : "=r"(done) : "r"(mbar), "r"(ph) : "memory");
   return done != 0;
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       group_sync(g);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (gt == 0) {
+      if (gt == 0 && !a.inject) {
         issue_product(dg1, sa_hi, sa_lo, sc_hi, sc_lo);
         commit(mb);
       }
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
       float vo[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) vo[j] = valid ? a.v[c * CS + pix + (size_t)j * N] : 0.f;
-      if (!wait_phase(mb, ph)) bail[g] = 1;
+      if (!wait_phase(mb, ph, a.spin)) bail[g] = 1;
       ph ^= 1u;
       group_sync(g);
       if (bail[g]) { ok = false; break; }
@@ -312,11 +317,11 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       group_sync(g);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (gt == 0) {
+      if (gt == 0 && !a.inject) {
         issue_product(dg2, sa_hi, sa_lo, sct_hi, sct_lo);
         commit(mb);
       }
-      if (!wait_phase(mb, ph)) bail[g] = 1;
+      if (!wait_phase(mb, ph, a.spin)) bail[g] = 1;
       ph ^= 1u;
       group_sync(g);
       if (bail[g]) { ok = false; break; }
@@ -332,7 +337,7 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
   }
   if (!ok) {
     if (gt == 0) atomicExch(a.err, 1);
-    wait_phase(mb, ph);          // let an MMA still in flight finish before freeing
+    wait_phase(mb, ph, a.spin);  // let an MMA still in flight finish before freeing
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -372,6 +377,8 @@ cudaError_t dct_dual_tc(const DctArgs &d, const Group &gr, int *err, cudaStream_
   a.chi = d.chi; a.clo = d.clo; a.cthi = d.cthi; a.ctlo = d.ctlo;
   a.alpha = d.alpha; a.sc = d.sc;
   a.xt = gr.xt; a.x = gr.x; a.v = gr.v; a.t = gr.t; a.err = err;
+  a.inject = d.inject_timeout;
+  a.spin = d.inject_timeout ? kSpinInjected : kSpin;
   if (gr.C == 3) return launch_tc<3>(a, st, d.prof);
   return launch_tc<1>(a, st, d.prof);
 }

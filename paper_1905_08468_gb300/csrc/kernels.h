@@ -221,6 +221,7 @@ struct DctArgs {
   int ctas_per_sm;         // persistent spectral grid: CTAs per SM (0: max resident)
   int tc;                  // 1: tcgen05 kernel (L = 64), 0: mma.sync kernel
   int *err;                // device flag raised when a tensor-core wait gives up
+  int inject_timeout;      // test hook: the tcgen05 kernel issues no products
   Prof *prof;              // optional per-kernel timing
 };
 // Spectral dual update and back-projection (Alg. 2 eqs. vt, v, upt and the

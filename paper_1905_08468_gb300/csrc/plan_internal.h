@@ -74,6 +74,7 @@ struct muffin_plan_s {
   int syn_packed = 0;     // synthesis variant bits (see WaveArgs::syn_packed)
   int dct_ctas = 0;       // spectral kernel CTAs per SM (0: all resident)
   int dct_tc = 0;         // spectral step on tcgen05 (L = 64)
+  int inject_timeout = 0; // test hook (muffin_plan_inject_timeout)
   int *kerr = nullptr;    // device flag: a bounded tensor-core wait gave up
   std::map<std::pair<int, int>, cudaGraphExec_t> gplain;   // (parity, cubes)
   cudaGraphExec_t gsure[2] = {nullptr, nullptr};
@@ -121,7 +122,7 @@ struct muffin_plan_s {
     d.chi = chi; d.clo = clo; d.cthi = cthi; d.ctlo = ctlo;
     d.alpha = alpha; d.sc = sc;
     d.ctas_per_sm = dct_ctas;
-    d.tc = dct_tc; d.err = kerr;
+    d.tc = dct_tc; d.err = kerr; d.inject_timeout = inject_timeout;
     d.prof = pp();
     return d;
   }

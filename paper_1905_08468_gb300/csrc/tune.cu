@@ -171,6 +171,13 @@ muffin_status muffin_plan_set_spectral_kernel(muffin_plan P, int32_t tcgen05) {
   return MUFFIN_OK;
 }
 
+muffin_status muffin_plan_inject_timeout(muffin_plan P, int32_t on) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  muffin::pi::drop_graphs_and_state(P);
+  P->inject_timeout = on ? 1 : 0;
+  return MUFFIN_OK;
+}
+
 muffin_status muffin_plan_set_tuning(muffin_plan P, int32_t syn_packed, int32_t dct_ctas_per_sm) {
   if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
   if (syn_packed < 0 || syn_packed > 3)

@@ -79,6 +79,7 @@ SIGNATURES = {
     "muffin_plan_autotune": (c_int32, [c_void_p, ctypes.c_char_p, ctypes.POINTER(TuneInfo)]),
     "muffin_plan_set_tuning": (c_int32, [c_void_p, c_int32, c_int32]),
     "muffin_plan_set_spectral_kernel": (c_int32, [c_void_p, c_int32]),
+    "muffin_plan_inject_timeout": (c_int32, [c_void_p, c_int32]),
     "muffin_sure_params_default": (None, [ctypes.POINTER(SureParams)]),
     "muffin_sure_tune": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p,
                                    ctypes.POINTER(SureParams), c_void_p,

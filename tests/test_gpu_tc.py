@@ -81,3 +81,24 @@ def test_tcgen05_needs_64_bands():
             p.set_spectral_kernel(True)
         assert e.value.status == 1
         p.set_spectral_kernel(False)
+
+
+def test_bounded_wait_times_out_without_fault_and_plan_recovers():
+    """The products are skipped on purpose (host-side hook), so the kernel's
+    bounded waits run out: the call reports MUFFIN_ETIMEOUT, the context and
+    the plan stay usable, and a normal call afterwards matches a fresh plan."""
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    c = make_cube(16, 64, 4, 1, 480, seed=1700)
+    ref = _solve(pkg, torch, c, True, 12)
+    x = torch.zeros_like(ref)
+    with pkg.Plan(16, 64, c.psf) as p:
+        p.inject_timeout(True)
+        with pytest.raises(pkg.MuffinError) as e:
+            p.solve(dev(c.dirty, torch), x, 3, 1e-2, 2e-2)
+        assert e.value.status == 4
+        p.inject_timeout(False)
+        x.zero_()
+        p.solve(dev(c.dirty, torch), x, 12, 1e-2, 2e-2)
+    torch.cuda.synchronize()
+    assert torch.equal(x, ref)
