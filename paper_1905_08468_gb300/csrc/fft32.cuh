@@ -119,8 +119,16 @@ __device__ __forceinline__ void fft_stage(float2 *d, int pitch, int nthr,
       const int w = tid + g * nthr;
       const int s = w / q, j = w % q, k = j & (NS - 1);
       const float2 *src = d + s * pitch;
+      if constexpr (q % 16 == 0) {
+        // j + r q and j share their position within a 16-run: one base
+        // address, constant offsets
+        const float2 *b = src + fpad(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[g * R + r] = src[fpad(j + r * q)];
+        for (int r = 0; r < R; ++r) v[g * R + r] = b[r * (q + q / 16)];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[g * R + r] = src[fpad(j + r * q)];
+      }
       if (NS > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r)
@@ -137,8 +145,16 @@ __device__ __forceinline__ void fft_stage(float2 *d, int pitch, int nthr,
       const int s = w / q, j = w % q, k = j & (NS - 1);
       float2 *dst = d + s * pitch;
       const int o = (j - k) * R + k;
+      if constexpr (NS % 16 == 0 || (NS == 1 && (R == 16 || N <= 16))) {
+        // o + r NS stays in o's 16-run (NS = 1: o is a multiple of R = 16,
+        // or o = 0 for N <= 16) or moves by whole runs (NS a multiple of 16)
+        float2 *b = dst + fpad(o);
 #pragma unroll
-      for (int r = 0; r < R; ++r) dst[fpad(o + r * NS)] = v[g * R + out_slot<R>(r)];
+        for (int r = 0; r < R; ++r) b[r * (NS + NS / 16)] = v[g * R + out_slot<R>(r)];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[fpad(o + r * NS)] = v[g * R + out_slot<R>(r)];
+      }
     }
   }
   __syncthreads();

@@ -26,7 +26,9 @@ namespace {
 constexpr int kThreads = 256;
 
 // sequences per CTA so that every thread owns fft_vpt(n) values per stage
-inline int seqs_per_cta(int n) { return kThreads * fft_vpt(n) / n; }
+constexpr int seqs_per_cta(int n) { return kThreads * fft_vpt(n) / n; }
+// complex (row-pair) sequences per CTA of the row passes: 2 * nq real rows
+constexpr int row_pairs(int n) { return seqs_per_cta(n) < n / 2 ? seqs_per_cta(n) : n / 2; }
 
 // stage the twiddle tables (tlen entries) into shared memory
 __device__ __forceinline__ void load_tw(float2 *dst, const float2 *__restrict__ src, int tlen) {
@@ -35,13 +37,14 @@ __device__ __forceinline__ void load_tw(float2 *dst, const float2 *__restrict__ 
 
 template <int NN>
 __global__ void __launch_bounds__(kThreads)
-k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S, int n, int RB,
+k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S,
            const float2 *__restrict__ tw, int tlen) {
+  // sizes are compile-time so that the index splits below are shifts
+  constexpr int n = NN, nq = row_pairs(NN), nh = (NN >> 1) + 1;
+  constexpr int pitch = n + (n >> 4);
   extern __shared__ float2 sm2[];
   const int img = blockIdx.y;
-  const int y0 = blockIdx.x * RB;
-  const int nq = RB >> 1, nh = (n >> 1) + 1;
-  const int pitch = n + (n >> 4);
+  const int y0 = blockIdx.x * 2 * nq;
   float2 *d = sm2, *tws = sm2 + nq * pitch;
   load_tw(tws, tw, tlen);
   const float *xi = x + (size_t)img * n * n + (size_t)y0 * n;
@@ -82,14 +85,14 @@ k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S, int n, int RB,
 
 template <int NN>
 __global__ void __launch_bounds__(kThreads)
-k_cols(float2 *__restrict__ S, const float *__restrict__ kspec, int n, int L,
-       int CB, const float2 *__restrict__ tw, int tlen) {
+k_cols(float2 *__restrict__ S, const float *__restrict__ kspec, int L,
+       const float2 *__restrict__ tw, int tlen) {
+  constexpr int n = NN, nh = (NN >> 1) + 1, CB = seqs_per_cta(NN);
+  constexpr int pitch = n + (n >> 4);
   extern __shared__ float2 sm2[];
   const int img = blockIdx.y, band = img % L;
-  const int nh = (n >> 1) + 1;
   const int k0 = blockIdx.x * CB;
   const int ncol = min(CB, nh - k0);
-  const int pitch = n + (n >> 4);
   float2 *d = sm2, *tws = sm2 + CB * pitch;
   load_tw(tws, tw, tlen);
   float2 *Si = S + ((size_t)img * nh + k0) * n;
@@ -141,13 +144,13 @@ k_cols(float2 *__restrict__ S, const float *__restrict__ kspec, int n, int L,
 template <int NN>
 __global__ void __launch_bounds__(kThreads)
 k_rows_inv(const float2 *__restrict__ S, float *__restrict__ g,
-           const float *__restrict__ bdata, int n, int L, int RB,
+           const float *__restrict__ bdata, int L,
            const float2 *__restrict__ tw, int tlen) {
+  constexpr int n = NN, nq = row_pairs(NN), nh = (NN >> 1) + 1, half = NN >> 1;
+  constexpr int pitch = n + (n >> 4);
   extern __shared__ float2 sm2[];
   const int img = blockIdx.y, band = img % L;
-  const int y0 = blockIdx.x * RB;
-  const int nq = RB >> 1, nh = (n >> 1) + 1, half = n >> 1;
-  const int pitch = n + (n >> 4);
+  const int y0 = blockIdx.x * 2 * nq;
   float2 *d = sm2, *tws = sm2 + nq * pitch;
   load_tw(tws, tw, tlen);
   const float4 *Si = reinterpret_cast<const float4 *>(S + (size_t)img * nh * n);
@@ -256,9 +259,8 @@ cudaError_t gradient_n(const float *x, float *g, const float *b, float2 *S,
                        cudaStream_t st, Prof *prof) {
   constexpr int n = NN;
   const int nimg = C * L;
-  const int nb = seqs_per_cta(n);
-  const int RB = 2 * nb < n ? 2 * nb : n;          // real rows per CTA (even)
-  const int CB = nb;                                // columns per CTA
+  const int RB = 2 * row_pairs(n);                  // real rows per CTA (even)
+  const int CB = seqs_per_cta(n);                   // columns per CTA
   const int nh = (n >> 1) + 1;
   const int pitch = n + (n >> 4);
   const int tlen = fft_table_len(n);
@@ -276,18 +278,18 @@ cudaError_t gradient_n(const float *x, float *g, const float *b, float2 *S,
   {
     ProfScope ps(prof, "grad_rows_fwd", nimg * (img * 4.0 + spec),
                  nimg * (n / 2.0) * fft, st);
-    k_rows_fwd<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(x, S, n, RB, tw, tlen);
+    k_rows_fwd<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(x, S, tw, tlen);
   }
   {
     ProfScope ps(prof, "grad_cols", nimg * 2.0 * spec + (double)L * nh * n * 4.0,
                  nimg * (double)nh * 2.0 * fft, st);
-    k_cols<NN><<<dim3((nh + CB - 1) / CB, nimg), kThreads, smc, st>>>(S, kspec, n, L, CB, tw, tlen);
+    k_cols<NN><<<dim3((nh + CB - 1) / CB, nimg), kThreads, smc, st>>>(S, kspec, L, tw, tlen);
   }
   {
     ProfScope ps(prof, "grad_rows_inv",
                  nimg * (spec + img * 4.0) + (b ? (double)L * img * 4.0 : 0.0),
                  nimg * (n / 2.0) * fft, st);
-    k_rows_inv<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(S, g, b, n, L, RB, tw, tlen);
+    k_rows_inv<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(S, g, b, L, tw, tlen);
   }
   return cudaGetLastError();
 }
