@@ -26,9 +26,9 @@ namespace {
 constexpr int kThreads = 256;
 
 // sequences per CTA so that every thread owns fft_vpt(n) values per stage
-constexpr int seqs_per_cta(int n) { return kThreads * fft_vpt(n) / n; }
+__host__ __device__ constexpr int seqs_per_cta(int n) { return kThreads * fft_vpt(n) / n; }
 // complex (row-pair) sequences per CTA of the row passes: 2 * nq real rows
-constexpr int row_pairs(int n) { return seqs_per_cta(n) < n / 2 ? seqs_per_cta(n) : n / 2; }
+__host__ __device__ constexpr int row_pairs(int n) { return seqs_per_cta(n) < n / 2 ? seqs_per_cta(n) : n / 2; }
 
 // stage the twiddle tables (tlen entries) into shared memory
 __device__ __forceinline__ void load_tw(float2 *dst, const float2 *__restrict__ src, int tlen) {
@@ -47,25 +47,24 @@ k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S,
   const int y0 = blockIdx.x * 2 * nq;
   float2 *d = sm2, *tws = sm2 + nq * pitch;
   load_tw(tws, tw, tlen);
-  const float *xi = x + (size_t)img * n * n + (size_t)y0 * n;
-  // every thread owns at most VPT row-pair elements: all loads first
+  // element u of the thread is i = tid + 256 u of the [nq][n] row pairs:
+  // pair tid / n + 256 u / n, column tid % n + (256 u) % n, so every index
+  // is a per-thread base plus a compile-time offset
+  const int tid = threadIdx.x;
+  const float *xi = x + (size_t)img * n * n + (size_t)(y0 + 2 * (tid / n)) * n + tid % n;
+  const int sb = (tid / n) * pitch + fpad(tid % n);
   constexpr int VPT = fft_vpt(NN);
   float2 v[VPT];
 #pragma unroll
   for (int u = 0; u < VPT; ++u) {
-    const int i = threadIdx.x + u * kThreads;
-    if (i < nq * n) {
-      const int q = i / n, col = i - q * n;
-      v[u] = make_float2(xi[(2 * q) * n + col], xi[(2 * q + 1) * n + col]);
-    }
+    const int q = (kThreads * u) / n, c = (kThreads * u) % n;
+    if (tid + u * kThreads < nq * n)
+      v[u] = make_float2(xi[2 * q * n + c], xi[(2 * q + 1) * n + c]);
   }
 #pragma unroll
   for (int u = 0; u < VPT; ++u) {
-    const int i = threadIdx.x + u * kThreads;
-    if (i < nq * n) {
-      const int q = i / n, col = i - q * n;
-      d[q * pitch + fpad(col)] = v[u];
-    }
+    const int q = (kThreads * u) / n, c = (kThreads * u) % n;
+    if (tid + u * kThreads < nq * n) d[sb + q * pitch + fpad(c)] = v[u];
   }
   __syncthreads();
   fft_inplace<NN, false>(d, nq, pitch, tws);
@@ -95,50 +94,44 @@ k_cols(float2 *__restrict__ S, const float *__restrict__ kspec, int L,
   const int ncol = min(CB, nh - k0);
   float2 *d = sm2, *tws = sm2 + CB * pitch;
   load_tw(tws, tw, tlen);
-  float2 *Si = S + ((size_t)img * nh + k0) * n;
-  const float *Ki = kspec + ((size_t)band * nh + k0) * n;
+  // element u of the thread is i = tid + 256 u of the CTA's [CB][n] block:
+  // column c0 + 256 u / n, row tid % n + (256 u) % n (see k_rows_fwd)
+  const int tid = threadIdx.x;
+  const int c0 = tid / n, sb = c0 * pitch + fpad(tid % n);
+  float2 *Si = S + ((size_t)img * nh + k0) * n + tid;
+  const float *Ki = kspec + ((size_t)band * nh + k0) * n + tid;
   // every thread owns at most KPT multiplier entries: prefetch them now
   constexpr int KPT = NN < 16 ? NN : 16;
   float kr[KPT];
 #pragma unroll
-  for (int u = 0; u < KPT; ++u) {
-    const int i = threadIdx.x + u * kThreads;
-    kr[u] = i < ncol * n ? __ldg(Ki + i) : 0.f;
-  }
+  for (int u = 0; u < KPT; ++u)
+    kr[u] = c0 + (kThreads * u) / n < ncol ? __ldg(Ki + kThreads * u) : 0.f;
   {
     float2 v[KPT];
 #pragma unroll
-    for (int u = 0; u < KPT; ++u) {
-      const int i = threadIdx.x + u * kThreads;
-      if (i < ncol * n) v[u] = Si[i];
-    }
+    for (int u = 0; u < KPT; ++u)
+      if (c0 + (kThreads * u) / n < ncol) v[u] = Si[kThreads * u];
 #pragma unroll
-    for (int u = 0; u < KPT; ++u) {
-      const int i = threadIdx.x + u * kThreads;
-      if (i < ncol * n) {
-        const int c = i / n, y = i - c * n;
-        d[c * pitch + fpad(y)] = v[u];
-      }
-    }
+    for (int u = 0; u < KPT; ++u)
+      if (c0 + (kThreads * u) / n < ncol)
+        d[sb + ((kThreads * u) / n) * pitch + fpad((kThreads * u) % n)] = v[u];
   }
   __syncthreads();
   fft_inplace<NN, false>(d, ncol, pitch, tws);
 #pragma unroll
   for (int u = 0; u < KPT; ++u) {
-    const int i = threadIdx.x + u * kThreads;
-    if (i < ncol * n) {
-      const int c = i / n, y = i - c * n;
-      float2 &z = d[c * pitch + fpad(y)];
+    if (c0 + (kThreads * u) / n < ncol) {
+      float2 &z = d[sb + ((kThreads * u) / n) * pitch + fpad((kThreads * u) % n)];
       z.x *= kr[u];
       z.y *= kr[u];
     }
   }
   __syncthreads();
   fft_inplace<NN, true>(d, ncol, pitch, tws);
-  for (int i = threadIdx.x; i < ncol * n; i += blockDim.x) {
-    const int c = i / n, y = i - c * n;
-    Si[i] = d[c * pitch + fpad(y)];
-  }
+#pragma unroll
+  for (int u = 0; u < KPT; ++u)
+    if (c0 + (kThreads * u) / n < ncol)
+      Si[kThreads * u] = d[sb + ((kThreads * u) / n) * pitch + fpad((kThreads * u) % n)];
 }
 
 template <int NN>
@@ -165,18 +158,25 @@ k_rows_inv(const float2 *__restrict__ S, float *__restrict__ g,
   __syncthreads();
   fft_inplace<NN, true>(d, nq, pitch, tws);
   const bool sub = (bdata != nullptr) && (img < L);
-  float *gi = g + (size_t)img * n * n + (size_t)y0 * n;
-  const float *bi = sub ? bdata + (size_t)band * n * n + (size_t)y0 * n : nullptr;
-  for (int i = threadIdx.x; i < nq * n; i += blockDim.x) {
-    const int q = i / n, col = i - q * n;
-    const float2 z = d[q * pitch + fpad(col)];
+  // element u of the thread: row pair tid / n + 256 u / n (see k_rows_fwd)
+  const int tid = threadIdx.x;
+  const size_t o0 = (size_t)(y0 + 2 * (tid / n)) * n + tid % n;
+  float *gi = g + (size_t)img * n * n + o0;
+  const float *bi = sub ? bdata + (size_t)band * n * n + o0 : nullptr;
+  const int sb = (tid / n) * pitch + fpad(tid % n);
+  constexpr int VPT = fft_vpt(NN);
+#pragma unroll
+  for (int u = 0; u < VPT; ++u) {
+    if (tid + u * kThreads >= nq * n) continue;
+    const int q = (kThreads * u) / n, c = (kThreads * u) % n;
+    const float2 z = d[sb + q * pitch + fpad(c)];
     float v0 = z.x, v1 = z.y;
     if (sub) {
-      v0 -= __ldg(bi + (2 * q) * n + col);
-      v1 -= __ldg(bi + (2 * q + 1) * n + col);
+      v0 -= __ldg(bi + 2 * q * n + c);
+      v1 -= __ldg(bi + (2 * q + 1) * n + c);
     }
-    gi[(2 * q) * n + col] = v0;
-    gi[(2 * q + 1) * n + col] = v1;
+    gi[2 * q * n + c] = v0;
+    gi[(2 * q + 1) * n + c] = v1;
   }
 }
 
