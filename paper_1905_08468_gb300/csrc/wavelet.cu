@@ -393,29 +393,50 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
-// issue the copies of the four subband tiles of (basis bb, chain c): rows
-// ky0-8 .. ky0+TY-1 and columns kx0-8 .. kx0+TX-1 (mod the level size h).
-// With h >= 8 every aligned group of 4 columns is contiguous in memory (the
-// wrap point is a multiple of 4), so whole groups move with 16-byte copies.
-__device__ __forceinline__ void syn_issue(const SynArgs &a, float *cf, int l,
-                                          int bb, int c, int kx0, int ky0) {
+// copies of the four subband tiles of a (basis, chain) step: rows ky0-8 ..
+// ky0+TY-1 and columns kx0-8 .. kx0+TX-1 (mod the level size h).  With
+// h >= 8 every aligned group of 4 columns is contiguous in memory (the wrap
+// point is a multiple of 4), so whole groups move with 16-byte copies and a
+// thread owns at most one group; its offsets are the same in every step and
+// are set once.
+struct SynSrc {
+  int o;          // shared-memory offset of the group in a subband tile (-1: none)
+  int ll;         // offset of the LL group in the step's LL source image
+  int dy, dx, hh; // offsets of the DY, DX, HH groups in the step's U image
+};
+
+__device__ __forceinline__ SynSrc syn_src(const SynArgs &a, int kx0, int ky0) {
+  const int h = a.M >> 1, hm = h - 1;
+  constexpr int G4 = S_CP / 4;
+  SynSrc sr;
+  const int it = threadIdx.x;
+  if (it >= S_CH * G4) { sr.o = -1; sr.ll = sr.dy = sr.dx = sr.hh = 0; return sr; }
+  const int r = it / G4, cc = (it - r * G4) * 4;
+  const int ky = (ky0 - S_HALO + r) & hm, kx = (kx0 - S_HALO + cc) & hm;
+  sr.o = r * S_CP + cc;
+  sr.ll = a.top ? ky * a.n + kx : ky * h + kx;
+  sr.dy = (h + ky) * a.n + kx;
+  sr.dx = ky * a.n + h + kx;
+  sr.hh = (h + ky) * a.n + h + kx;
+  return sr;
+}
+static_assert(S_CH * (S_CP / 4) <= NT, "one 16-byte group per thread");
+
+__device__ __forceinline__ void syn_issue(const SynArgs &a, const SynSrc &sr, float *cf,
+                                          int l, int bb, int c) {
   const int h = a.M >> 1, hm = h - 1;
   const size_t NN = (size_t)a.n * a.n;
-  const float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * NN;
-  const float *lp = a.top ? nullptr
-                          : a.ll_in + ((size_t)(c * a.L + l) * a.K + bb) * h * h;
+  const size_t img = (size_t)(c * a.L + l) * a.K + bb;
+  const float *up = a.u + img * NN;
+  const float *lp = a.top ? up : a.ll_in + img * h * h;
   if (h >= 8) {
-    constexpr int G4 = S_CP / 4;
-    for (int it = threadIdx.x; it < S_CH * G4; it += NT) {
-      const int r = it / G4, cc = (it - r * G4) * 4;
-      const int ky = (ky0 - S_HALO + r) & hm, kx = (kx0 - S_HALO + cc) & hm;
-      const int o = r * S_CP + cc;
-      cp_async16(cf + o, a.top ? up + (size_t)ky * a.n + kx : lp + (size_t)ky * h + kx);
-      cp_async16(cf + SUB + o, up + (size_t)(h + ky) * a.n + kx);          // DY
-      cp_async16(cf + 2 * SUB + o, up + (size_t)ky * a.n + h + kx);        // DX
-      cp_async16(cf + 3 * SUB + o, up + (size_t)(h + ky) * a.n + h + kx);  // HH
-    }
+    if (sr.o < 0) return;
+    cp_async16(cf + sr.o, lp + sr.ll);
+    cp_async16(cf + SUB + sr.o, up + sr.dy);
+    cp_async16(cf + 2 * SUB + sr.o, up + sr.dx);
+    cp_async16(cf + 3 * SUB + sr.o, up + sr.hh);
   } else {
+    const int kx0 = 0, ky0 = 0;   // h < 8: a single tile covers the level
     for (int it = threadIdx.x; it < S_CH * S_CP; it += NT) {
       const int r = it / S_CP, cc = it - r * S_CP;
       const int ky = (ky0 - S_HALO + r) & hm, kx = (kx0 - S_HALO + cc) & hm;
@@ -522,23 +543,25 @@ __device__ __forceinline__ void syn_step_s(const float *cf, float *lo_s, float *
       vDX[i] = cf[2 * SUB + base + i * S_CP];
       vHH[i] = cf[3 * SUB + base + i * S_CP];
     }
+    // both output rows 2k + e of a coefficient row in the lanes of one
+    // packed FMA: (h_2s, h_2s+1) * (c, c), same sums in the same order as
+    // one scalar FMA per lane
 #pragma unroll
     for (int qq = 0; qq < QYP; ++qq) {
+      float2 lo = make_float2(0.f, 0.f), hi = lo;
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        float lo = 0.f, hi = 0.f;
-#pragma unroll
-        for (int s = 0; s < P; ++s) {
-          const int ci = qq + P - 1 - s;
-          lo = fmaf(c_h[P - 1][2 * s + e], vLL[ci], lo);
-          lo = fmaf(c_g[P - 1][2 * s + e], vDY[ci], lo);
-          hi = fmaf(c_h[P - 1][2 * s + e], vDX[ci], hi);
-          hi = fmaf(c_g[P - 1][2 * s + e], vHH[ci], hi);
-        }
-        const int my = 2 * (QYP * sy + qq) + e;
-        lo_s[my * SLP + kc] = lo;
-        hi_s[my * SLP + kc] = hi;
+      for (int s = 0; s < P; ++s) {
+        const int ci = qq + P - 1 - s;
+        lo = ffma2(c_hp[P - 1][s], make_float2(vLL[ci], vLL[ci]), lo);
+        lo = ffma2(c_gp[P - 1][s], make_float2(vDY[ci], vDY[ci]), lo);
+        hi = ffma2(c_hp[P - 1][s], make_float2(vDX[ci], vDX[ci]), hi);
+        hi = ffma2(c_gp[P - 1][s], make_float2(vHH[ci], vHH[ci]), hi);
       }
+      const int my = 2 * (QYP * sy + qq);
+      lo_s[my * SLP + kc] = lo.x;
+      lo_s[(my + 1) * SLP + kc] = lo.y;
+      hi_s[my * SLP + kc] = hi.x;
+      hi_s[(my + 1) * SLP + kc] = hi.y;
     }
   }
   __syncthreads();
@@ -552,17 +575,15 @@ __device__ __forceinline__ void syn_step_s(const float *cf, float *lo_s, float *
   for (int i = 0; i < NWR; ++i) { vl[i] = pl[i]; vh[i] = ph[i]; }
 #pragma unroll
   for (int qq = 0; qq < QXS; ++qq) {
+    float2 v = make_float2(0.f, 0.f);   // pixels 2k, 2k + 1
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      float v = 0.f;
-#pragma unroll
-      for (int s = 0; s < P; ++s) {
-        const int ci = qq + P - 1 - s;
-        v = fmaf(c_h[P - 1][2 * s + e], vl[ci], v);
-        v = fmaf(c_g[P - 1][2 * s + e], vh[ci], v);
-      }
-      o[0][2 * qq + e] = v;
+    for (int s = 0; s < P; ++s) {
+      const int ci = qq + P - 1 - s;
+      v = ffma2(c_hp[P - 1][s], make_float2(vl[ci], vl[ci]), v);
+      v = ffma2(c_gp[P - 1][s], make_float2(vh[ci], vh[ci]), v);
     }
+    o[0][2 * qq] = v.x;
+    o[0][2 * qq + 1] = v.y;
   }
 }
 
@@ -635,13 +656,14 @@ __global__ void __launch_bounds__(NT, 4) k_syn(SynArgs a) {
       for (int e = 0; e < NO; ++e) acc[c][j][e] = 0.f;
   // (basis, chain) steps; coarser levels write each basis' LL_{j-1}
   const int nsteps = a.K * CH;
-  syn_issue(a, cf0, l, 0, 0, kx0, ky0);
+  const SynSrc sr = syn_src(a, kx0, ky0);
+  syn_issue(a, sr, cf0, l, 0, 0);
   cp_commit();
   for (int i = 0; i < nsteps; ++i) {
     const int bb = i / CH, c = i % CH;
     float *cf = cf0 + (i & 1) * 4 * SUB;
     if (i + 1 < nsteps) {
-      syn_issue(a, cf0 + ((i + 1) & 1) * 4 * SUB, l, (i + 1) / CH, (i + 1) % CH, kx0, ky0);
+      syn_issue(a, sr, cf0 + ((i + 1) & 1) * 4 * SUB, l, (i + 1) / CH, (i + 1) % CH);
       cp_commit();
       cp_wait<1>();
     } else {
