@@ -528,12 +528,12 @@ template <int P>
 __device__ __forceinline__ void syn_step_s(const float *cf, float *lo_s, float *hi_s,
                                            float (&o)[1][2 * QXS]) {
   constexpr int SLP = S_LP;
-  constexpr int NCOL = TX + P - 1;
   constexpr int NSY = TY / QYP;
   constexpr int NWC = QYP + P - 1;
   constexpr int OFF = S_HALO - (P - 1);     // window offset of this basis' halo
-  for (int it = threadIdx.x; it < NSY * NCOL; it += NT) {
-    const int kc = it % NCOL, sy = it / NCOL;
+  static_assert(NSY * 32 == NT, "one warp per coefficient row group");
+  // column item (column kc of the window, coefficient row group sy)
+  auto item = [&](int kc, int sy) {
     const int base = (QYP * sy + OFF) * S_CP + kc + OFF;
     float vLL[NWC], vDY[NWC], vDX[NWC], vHH[NWC];
 #pragma unroll
@@ -563,6 +563,14 @@ __device__ __forceinline__ void syn_step_s(const float *cf, float *lo_s, float *
       hi_s[my * SLP + kc] = hi.x;
       hi_s[(my + 1) * SLP + kc] = hi.y;
     }
+  };
+  // warp w takes row group w and the tile's own TX columns (lane = column,
+  // so a warp touches consecutive shared addresses); the P - 1 halo columns
+  // of every group follow as a short second round
+  item(P - 1 + (threadIdx.x & 31), threadIdx.x >> 5);
+  if (P > 1 && threadIdx.x < NSY * (P - 1)) {
+    const int sy = threadIdx.x / (P > 1 ? P - 1 : 1);
+    item(threadIdx.x - sy * (P - 1), sy);
   }
   __syncthreads();
   constexpr int NWR = QXS + P - 1;
