@@ -655,23 +655,104 @@ __global__ void __launch_bounds__(NT, 4) k_syn(SynArgs a) {
     const int sx = threadIdx.x % (TX / QXS), my = threadIdx.x / (TX / QXS);
     r0 = my; dr = 0; xx0 = 2 * kx0 + NO * sx;
   }
-  float acc[CH][ROWS][NO];
+  // Steps run chain-major (all bases of chain 0, then chain 1, ...), so a
+  // thread holds the running sum of one chain plus chain 0's finished sum:
+  // by linearity the d/dmu chain's synthesis of (u + mu u'_mu) is
+  // W^T u + mu W^T u'_mu.  When a chain's last basis is in, its prox runs.
+  float sum[ROWS][NO], s0[ROWS][NO];
 #pragma unroll
-  for (int c = 0; c < CH; ++c)
+  for (int j = 0; j < ROWS; ++j)
 #pragma unroll
-    for (int j = 0; j < ROWS; ++j)
+    for (int e = 0; e < NO; ++e) { sum[j][e] = 0.f; s0[j][e] = 0.f; }
+  uint32_t keep = 0;                  // chain 0's prox mask, bit j * NO + e
+  const size_t NN = (size_t)a.n * a.n;
+  const bool own = LEVEL1 && xx0 < a.n;   // the thread has pixels of the level-1 output
+  // vector path: the thread's NO pixels of a row are inside it and aligned
+  const bool vec = (a.n % NO) == 0 && xx0 + NO <= a.n;
+  // chain c's output from its synthesis t: the operator's W^T u, or the
+  // primal step x~ = prox(x - tau (grad + scale t + t_spec))
+  auto finish = [&](int c, const float (&t)[ROWS][NO]) {
+    if (MODE == WAVE_TRANSFORM) {
 #pragma unroll
-      for (int e = 0; e < NO; ++e) acc[c][j][e] = 0.f;
-  // (basis, chain) steps; coarser levels write each basis' LL_{j-1}
+      for (int j = 0; j < ROWS; ++j) {
+        const int yy = 2 * ky0 + r0 + dr * j;
+        if (yy >= a.n) continue;
+        float *dst = a.out + (size_t)l * NN + (size_t)yy * a.n + xx0;
+        if (xx0 + NO <= a.n && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+          for (int q = 0; q < NO; q += 4)
+            *reinterpret_cast<float4 *>(dst + q) = make_float4(t[j][q], t[j][q + 1], t[j][q + 2], t[j][q + 3]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < NO; ++e)
+            if (xx0 + e < a.n) dst[e] = t[j][e];
+        }
+      }
+      return;
+    }
+    const float tau = (float)a.sc[l / a.Lc].tau;
+    const float bl = a.beta[l];
+    const size_t CS = (size_t)a.L * NN;
+    const float sc = (CH == 3 && c == 1) ? bl : bl * mu;   // mu_l, beta_l, mu_l
+#pragma unroll
+    for (int j = 0; j < ROWS; ++j) {
+      const int yy = 2 * ky0 + r0 + dr * j;
+      if (yy >= a.n) continue;
+      const size_t i0 = (size_t)l * NN + (size_t)yy * a.n + xx0 + c * CS;
+      // four pixels at a time keep the loads' registers few
+#pragma unroll
+      for (int q = 0; q < NO; q += 4) {
+        float xv[4], gv[4], tv[4];
+        if (vec) {
+          const float4 x4 = *reinterpret_cast<const float4 *>(a.x + i0 + q);
+          const float4 g4 = *reinterpret_cast<const float4 *>(a.g + i0 + q);
+          const float4 t4 = *reinterpret_cast<const float4 *>(a.t + i0 + q);
+          xv[0] = x4.x; xv[1] = x4.y; xv[2] = x4.z; xv[3] = x4.w;
+          gv[0] = g4.x; gv[1] = g4.y; gv[2] = g4.z; gv[3] = g4.w;
+          tv[0] = t4.x; tv[1] = t4.y; tv[2] = t4.z; tv[3] = t4.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const bool ok = xx0 + q + e < a.n;
+            xv[e] = ok ? a.x[i0 + q + e] : 0.f;
+            gv[e] = ok ? a.g[i0 + q + e] : 0.f;
+            tv[e] = ok ? a.t[i0 + q + e] : 0.f;
+          }
+        }
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float m = xv[e] - tau * (gv[e] + sc * t[j][q + e] + tv[e]);
+          const uint32_t bit = 1u << (j * NO + q + e);
+          if (c == 0) {
+            const bool k = !a.positivity || m > 0.f;
+            if (k) keep |= bit;
+            o[e] = k ? m : 0.f;
+          } else {
+            o[e] = (keep & bit) ? m : 0.f;
+          }
+        }
+        if (vec) {
+          *reinterpret_cast<float4 *>(a.xt + i0 + q) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (xx0 + q + e < a.n) a.xt[i0 + q + e] = o[e];
+        }
+      }
+    }
+  };
+  // (chain, basis) steps; coarser levels write each basis' LL_{j-1}
   const int nsteps = a.K * CH;
   const SynSrc sr = syn_src(a, kx0, ky0);
   syn_issue(a, sr, cf0, l, 0, 0);
   cp_commit();
   for (int i = 0; i < nsteps; ++i) {
-    const int bb = i / CH, c = i % CH;
+    const int c = i / a.K, bb = i - c * a.K;
     float *cf = cf0 + (i & 1) * 4 * SUB;
     if (i + 1 < nsteps) {
-      syn_issue(a, sr, cf0 + ((i + 1) & 1) * 4 * SUB, l, (i + 1) / CH, (i + 1) % CH);
+      const int c1 = (i + 1) / a.K;
+      syn_issue(a, sr, cf0 + ((i + 1) & 1) * 4 * SUB, l, i + 1 - c1 * a.K, c1);
       cp_commit();
       cp_wait<1>();
     } else {
@@ -684,15 +765,26 @@ __global__ void __launch_bounds__(NT, 4) k_syn(SynArgs a) {
 #pragma unroll
       for (int j = 0; j < ROWS; ++j)
 #pragma unroll
-        for (int e = 0; e < NO; ++e) {
-          if (CH == 3) {
-            if (c == 0) { acc[0][j][e] += o[j][e]; acc[1][j][e] += o[j][e]; }
-            else if (c == 1) acc[1][j][e] = fmaf(mu, o[j][e], acc[1][j][e]);
-            else acc[2][j][e] += o[j][e];
-          } else {
-            acc[0][j][e] += o[j][e];
-          }
+        for (int e = 0; e < NO; ++e) sum[j][e] += o[j][e];
+      if (bb == a.K - 1) {                 // chain c is complete
+        if (CH == 3 && c == 0) {
+#pragma unroll
+          for (int j = 0; j < ROWS; ++j)
+#pragma unroll
+            for (int e = 0; e < NO; ++e) s0[j][e] = sum[j][e];
         }
+        if (CH == 3 && c == 1) {
+#pragma unroll
+          for (int j = 0; j < ROWS; ++j)
+#pragma unroll
+            for (int e = 0; e < NO; ++e) sum[j][e] = fmaf(mu, sum[j][e], s0[j][e]);
+        }
+        if (own) finish(c, sum);
+#pragma unroll
+        for (int j = 0; j < ROWS; ++j)
+#pragma unroll
+          for (int e = 0; e < NO; ++e) sum[j][e] = 0.f;
+      }
     } else {
 #pragma unroll
       for (int j = 0; j < ROWS; ++j) {
@@ -712,86 +804,6 @@ __global__ void __launch_bounds__(NT, 4) k_syn(SynArgs a) {
       }
     }
     __syncthreads();
-  }
-  if (!LEVEL1 || xx0 >= a.n) return;
-  const size_t NN = (size_t)a.n * a.n;
-  if (MODE == WAVE_TRANSFORM) {
-#pragma unroll
-    for (int j = 0; j < ROWS; ++j) {
-      const int yy = 2 * ky0 + r0 + dr * j;
-      if (yy >= a.n) continue;
-      float *dst = a.out + (size_t)l * NN + (size_t)yy * a.n + xx0;
-      if (xx0 + NO <= a.n && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-#pragma unroll
-        for (int q = 0; q < NO; q += 4)
-          *reinterpret_cast<float4 *>(dst + q) =
-              make_float4(acc[0][j][q], acc[0][j][q + 1], acc[0][j][q + 2], acc[0][j][q + 3]);
-      } else {
-#pragma unroll
-        for (int e = 0; e < NO; ++e)
-          if (xx0 + e < a.n) dst[e] = acc[0][j][e];
-      }
-    }
-    return;
-  }
-  const float tau = (float)a.sc[l / a.Lc].tau;
-  const float bl = a.beta[l];
-  const size_t CS = (size_t)a.L * NN;
-  // vector path: the thread's NO pixels of a row are inside it and aligned
-  const bool vec = (a.n % NO) == 0 && xx0 + NO <= a.n;
-#pragma unroll
-  for (int j = 0; j < ROWS; ++j) {
-    const int yy = 2 * ky0 + r0 + dr * j;
-    if (yy >= a.n) continue;
-    const size_t row = (size_t)l * NN + (size_t)yy * a.n;
-    // chains in order; each loads its x, grad, t first, then stores x-tilde
-    uint32_t keep = 0;
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const float sc = (CH == 3 && c == 1) ? bl : bl * mu;   // mu_l, beta_l, mu_l
-      const size_t i0 = row + xx0 + c * CS;
-      float xv[NO], gv[NO], tv[NO];
-      if (vec) {
-#pragma unroll
-        for (int q = 0; q < NO; q += 4) {
-          const float4 x4 = *reinterpret_cast<const float4 *>(a.x + i0 + q);
-          const float4 g4 = *reinterpret_cast<const float4 *>(a.g + i0 + q);
-          const float4 t4 = *reinterpret_cast<const float4 *>(a.t + i0 + q);
-          xv[q] = x4.x; xv[q + 1] = x4.y; xv[q + 2] = x4.z; xv[q + 3] = x4.w;
-          gv[q] = g4.x; gv[q + 1] = g4.y; gv[q + 2] = g4.z; gv[q + 3] = g4.w;
-          tv[q] = t4.x; tv[q + 1] = t4.y; tv[q + 2] = t4.z; tv[q + 3] = t4.w;
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < NO; ++e) {
-          const bool ok = xx0 + e < a.n;
-          xv[e] = ok ? a.x[i0 + e] : 0.f;
-          gv[e] = ok ? a.g[i0 + e] : 0.f;
-          tv[e] = ok ? a.t[i0 + e] : 0.f;
-        }
-      }
-      float o[NO];
-#pragma unroll
-      for (int e = 0; e < NO; ++e) {
-        const float m = xv[e] - tau * (gv[e] + sc * acc[c][j][e] + tv[e]);
-        if (c == 0) {
-          const bool k = !a.positivity || m > 0.f;
-          if (k) keep |= 1u << e;
-          o[e] = k ? m : 0.f;
-        } else {
-          o[e] = (keep >> e) & 1u ? m : 0.f;
-        }
-      }
-      if (vec) {
-#pragma unroll
-        for (int q = 0; q < NO; q += 4)
-          *reinterpret_cast<float4 *>(a.xt + i0 + q) = make_float4(o[q], o[q + 1], o[q + 2], o[q + 3]);
-      } else {
-#pragma unroll
-        for (int e = 0; e < NO; ++e)
-          if (xx0 + e < a.n) a.xt[i0 + e] = o[e];
-      }
-    }
   }
 }
 
