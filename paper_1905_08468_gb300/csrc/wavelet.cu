@@ -535,33 +535,32 @@ __device__ __forceinline__ void syn_step_s(const float *cf, float *lo_s, float *
   // column item (column kc of the window, coefficient row group sy)
   auto item = [&](int kc, int sy) {
     const int base = (QYP * sy + OFF) * S_CP + kc + OFF;
-    float vLL[NWC], vDY[NWC], vDX[NWC], vHH[NWC];
+    // lo (from LL, DY) and hi (from DX, HH) one after the other, so only
+    // two coefficient windows are live at a time
 #pragma unroll
-    for (int i = 0; i < NWC; ++i) {
-      vLL[i] = cf[base + i * S_CP];
-      vDY[i] = cf[SUB + base + i * S_CP];
-      vDX[i] = cf[2 * SUB + base + i * S_CP];
-      vHH[i] = cf[3 * SUB + base + i * S_CP];
-    }
-    // both output rows 2k + e of a coefficient row in the lanes of one
-    // packed FMA: (h_2s, h_2s+1) * (c, c), same sums in the same order as
-    // one scalar FMA per lane
+    for (int half = 0; half < 2; ++half) {
+      const float *ca = cf + (half ? 2 * SUB : 0) + base;     // LL or DX
+      const float *cb = cf + (half ? 3 * SUB : SUB) + base;   // DY or HH
+      float *dst = half ? hi_s : lo_s;
+      float va[NWC], vb[NWC];
 #pragma unroll
-    for (int qq = 0; qq < QYP; ++qq) {
-      float2 lo = make_float2(0.f, 0.f), hi = lo;
+      for (int i = 0; i < NWC; ++i) { va[i] = ca[i * S_CP]; vb[i] = cb[i * S_CP]; }
+      // both output rows 2k + e of a coefficient row in the lanes of one
+      // packed FMA: (h_2s, h_2s+1) * (c, c), same sums in the same order as
+      // one scalar FMA per lane
 #pragma unroll
-      for (int s = 0; s < P; ++s) {
-        const int ci = qq + P - 1 - s;
-        lo = ffma2(c_hp[P - 1][s], make_float2(vLL[ci], vLL[ci]), lo);
-        lo = ffma2(c_gp[P - 1][s], make_float2(vDY[ci], vDY[ci]), lo);
-        hi = ffma2(c_hp[P - 1][s], make_float2(vDX[ci], vDX[ci]), hi);
-        hi = ffma2(c_gp[P - 1][s], make_float2(vHH[ci], vHH[ci]), hi);
+      for (int qq = 0; qq < QYP; ++qq) {
+        float2 v = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int s = 0; s < P; ++s) {
+          const int ci = qq + P - 1 - s;
+          v = ffma2(c_hp[P - 1][s], make_float2(va[ci], va[ci]), v);
+          v = ffma2(c_gp[P - 1][s], make_float2(vb[ci], vb[ci]), v);
+        }
+        const int my = 2 * (QYP * sy + qq);
+        dst[my * SLP + kc] = v.x;
+        dst[(my + 1) * SLP + kc] = v.y;
       }
-      const int my = 2 * (QYP * sy + qq);
-      lo_s[my * SLP + kc] = lo.x;
-      lo_s[(my + 1) * SLP + kc] = lo.y;
-      hi_s[my * SLP + kc] = hi.x;
-      hi_s[(my + 1) * SLP + kc] = hi.y;
     }
   };
   // warp w takes row group w and the tile's own TX columns (lane = column,
@@ -656,14 +655,14 @@ __global__ void __launch_bounds__(NT, 4) k_syn(SynArgs a) {
     r0 = my; dr = 0; xx0 = 2 * kx0 + NO * sx;
   }
   // Steps run chain-major (all bases of chain 0, then chain 1, ...), so a
-  // thread holds the running sum of one chain plus chain 0's finished sum:
-  // by linearity the d/dmu chain's synthesis of (u + mu u'_mu) is
-  // W^T u + mu W^T u'_mu.  When a chain's last basis is in, its prox runs.
-  float sum[ROWS][NO], s0[ROWS][NO];
+  // thread holds one running sum: by linearity the d/dmu chain's synthesis
+  // of (u + mu u'_mu) is W^T u + mu W^T u'_mu, so chain 1 continues from
+  // chain 0's finished sum.  When a chain's last basis is in, its prox runs.
+  float sum[ROWS][NO];
 #pragma unroll
   for (int j = 0; j < ROWS; ++j)
 #pragma unroll
-    for (int e = 0; e < NO; ++e) { sum[j][e] = 0.f; s0[j][e] = 0.f; }
+    for (int e = 0; e < NO; ++e) sum[j][e] = 0.f;
   uint32_t keep = 0;                  // chain 0's prox mask, bit j * NO + e
   const size_t NN = (size_t)a.n * a.n;
   const bool own = LEVEL1 && xx0 < a.n;   // the thread has pixels of the level-1 output
@@ -747,11 +746,13 @@ __global__ void __launch_bounds__(NT, 4) k_syn(SynArgs a) {
   const SynSrc sr = syn_src(a, kx0, ky0);
   syn_issue(a, sr, cf0, l, 0, 0);
   cp_commit();
+  // i / K as a multiply-shift (exact for i <= 3K + 1, K <= 8)
+  const uint32_t kmag = (65536u + (uint32_t)a.K - 1u) / (uint32_t)a.K;
   for (int i = 0; i < nsteps; ++i) {
-    const int c = i / a.K, bb = i - c * a.K;
+    const int c = (int)(((uint32_t)i * kmag) >> 16), bb = i - c * a.K;
     float *cf = cf0 + (i & 1) * 4 * SUB;
     if (i + 1 < nsteps) {
-      const int c1 = (i + 1) / a.K;
+      const int c1 = (int)(((uint32_t)(i + 1) * kmag) >> 16);
       syn_issue(a, sr, cf0 + ((i + 1) & 1) * 4 * SUB, l, i + 1 - c1 * a.K, c1);
       cp_commit();
       cp_wait<1>();
@@ -762,28 +763,19 @@ __global__ void __launch_bounds__(NT, 4) k_syn(SynArgs a) {
     float o[ROWS][NO];
     syn_dispatch<PACKED>(bb + 1, cf, lo, o);
     if (LEVEL1) {
+      const float w = (CH == 3 && c == 1) ? mu : 1.f;
 #pragma unroll
       for (int j = 0; j < ROWS; ++j)
 #pragma unroll
-        for (int e = 0; e < NO; ++e) sum[j][e] += o[j][e];
+        for (int e = 0; e < NO; ++e) sum[j][e] = fmaf(w, o[j][e], sum[j][e]);
       if (bb == a.K - 1) {                 // chain c is complete
-        if (CH == 3 && c == 0) {
-#pragma unroll
-          for (int j = 0; j < ROWS; ++j)
-#pragma unroll
-            for (int e = 0; e < NO; ++e) s0[j][e] = sum[j][e];
-        }
-        if (CH == 3 && c == 1) {
-#pragma unroll
-          for (int j = 0; j < ROWS; ++j)
-#pragma unroll
-            for (int e = 0; e < NO; ++e) sum[j][e] = fmaf(mu, sum[j][e], s0[j][e]);
-        }
         if (own) finish(c, sum);
+        if (!(CH == 3 && c == 0)) {        // chain 1 continues from chain 0's sum
 #pragma unroll
-        for (int j = 0; j < ROWS; ++j)
+          for (int j = 0; j < ROWS; ++j)
 #pragma unroll
-          for (int e = 0; e < NO; ++e) sum[j][e] = 0.f;
+            for (int e = 0; e < NO; ++e) sum[j][e] = 0.f;
+        }
       }
     } else {
 #pragma unroll
