@@ -216,17 +216,18 @@ __device__ __forceinline__ void ana_cols_dispatch(int p, const float2 *lo_s,
 
 // U values the thread's column item updates in step (bb, c): subbands DX
 // (low y, high x), DY, HH and, at the last level, LL
-template <int MODE>
+template <int MODE, int NS, bool L1>
 __device__ __forceinline__ void ana_prefetch(const AnaArgs &a, int l, int bb, int c,
                                              int kx0, int ky0, float (&pre)[4][QY]) {
-  const int h = a.M >> 1, hn = h * a.n;
+  const int n = NS ? NS : a.n, M = (NS && L1) ? NS : a.M;
+  const int h = M >> 1, hn = h * n;
   const int kx = threadIdx.x % TX, s = threadIdx.x / TX;
   const int kxg = kx0 + kx;
-  const float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * ((size_t)a.n * a.n);
+  const float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * ((size_t)n * n);
 #pragma unroll
   for (int qq = 0; qq < QY; ++qq) {
     const int ky = ky0 + QY * s + qq;
-    const int o = ky * a.n + kxg;
+    const int o = ky * n + kxg;
     const bool act = MODE == WAVE_ITERATE && ky < h && kxg < h;
     pre[0][qq] = act ? up[o + h] : 0.f;
     pre[1][qq] = act ? up[o + hn] : 0.f;
@@ -237,15 +238,16 @@ __device__ __forceinline__ void ana_prefetch(const AnaArgs &a, int l, int bb, in
 
 // dual update p = u + q w, u = sat(p) (or the mask of channel 0) and the
 // stores of step (bb, c)
-template <int MODE>
+template <int MODE, int NS, bool L1>
 __device__ __forceinline__ void ana_emit_step(const AnaArgs &a, int l, int bb, int c,
                                               int kx0, int ky0, float q,
                                               const float (&cf)[4][QY],
                                               const float (&pre)[4][QY], uint32_t &keep) {
-  const int h = a.M >> 1, hn = h * a.n;
+  const int n = NS ? NS : a.n, M = (NS && L1) ? NS : a.M;
+  const int h = M >> 1, hn = h * n;
   const int kx = threadIdx.x % TX, s = threadIdx.x / TX;
   const int kxg = kx0 + kx;
-  float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * ((size_t)a.n * a.n);
+  float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * ((size_t)n * n);
   float *llp = a.last ? nullptr : a.ll_out + ((size_t)(c * a.L + l) * a.K + bb) * h * h;
   const int sbo[4] = {h, hn, hn + h, 0};
   if (c == 0) keep = 0;
@@ -253,7 +255,7 @@ __device__ __forceinline__ void ana_emit_step(const AnaArgs &a, int l, int bb, i
   for (int qq = 0; qq < QY; ++qq) {
     const int ky = ky0 + QY * s + qq;
     if (ky >= h || kxg >= h) continue;
-    const int o = ky * a.n + kxg;
+    const int o = ky * n + kxg;
     const int nsb = a.last ? 4 : 3;
 #pragma unroll
     for (int sb = 0; sb < 4; ++sb) {
@@ -277,20 +279,23 @@ __device__ __forceinline__ void ana_emit_step(const AnaArgs &a, int l, int bb, i
   }
 }
 
-template <int CH, int MODE, bool LEVEL1>
+// NS > 0: the image side n fixed at compile time (level 1 of the common
+// sizes), so every U offset of the dual update is an immediate
+template <int CH, int MODE, bool LEVEL1, int NS>
 __global__ void __launch_bounds__(NT, 4) k_ana(AnaArgs a) {
   extern __shared__ float2 smem2[];
   float2 *in_s = smem2;                     // [CH][A_RP][A_IP] row pairs
   float2 *lohi = in_s + CH * A_RP * A_IP;   // [A_RP][A_LP] lo, then hi
-  const int h = a.M >> 1;
+  const int n = NS ? NS : a.n, M = (NS && LEVEL1) ? NS : a.M;
+  const int h = M >> 1;
   const int ntx = (h + TX - 1) / TX;
   const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
   const int l = LEVEL1 ? blockIdx.y : blockIdx.y / a.K;
   const int b = LEVEL1 ? 0 : blockIdx.y % a.K;
   const int P = LEVEL1 ? a.K : b + 1;
   const int RP = TY + P - 1, RW = 2 * TX + 2 * P - 2;
-  const int Mm = a.M - 1;
-  const size_t NN = (size_t)a.n * a.n;
+  const int Mm = M - 1;
+  const size_t NN = (size_t)n * n;
   const size_t CS = (size_t)a.L * NN;   // channel stride of images
   float mu = 0.f, sbl = 1.f;
   if (MODE == WAVE_ITERATE) {
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(NT, 4) k_ana(AnaArgs a) {
     for (int e = 0; e < 2; ++e) {
       const int yy = (2 * ky0 + 2 * rp + e) & Mm;
       if (LEVEL1) {
-        const size_t pix = (size_t)l * NN + (size_t)yy * a.n + xx;
+        const size_t pix = (size_t)l * NN + (size_t)yy * n + xx;
         if (MODE == WAVE_TRANSFORM) {
           w[e][0] = a.in[pix];
         } else {
@@ -321,7 +326,7 @@ __global__ void __launch_bounds__(NT, 4) k_ana(AnaArgs a) {
       } else {
 #pragma unroll
         for (int c = 0; c < CH; ++c)
-          w[e][c] = a.in[(((size_t)(c * a.L + l) * a.K + b) * a.M + yy) * a.M + xx];
+          w[e][c] = a.in[(((size_t)(c * a.L + l) * a.K + b) * M + yy) * M + xx];
       }
     }
   };
@@ -351,14 +356,14 @@ __global__ void __launch_bounds__(NT, 4) k_ana(AnaArgs a) {
   for (int s = 0; s < nsteps; ++s) {
     const int bb = b0 + s / CH, c = s % CH;
     float pre[4][QY];
-    ana_prefetch<MODE>(a, l, bb, c, kx0, ky0, pre);
+    ana_prefetch<MODE, NS, LEVEL1>(a, l, bb, c, kx0, ky0, pre);
     ana_rows_dispatch(bb + 1, in_s + c * A_RP * A_IP, lohi, lohi + LH);
     __syncthreads();
     float cf[4][QY];
     ana_cols_dispatch(bb + 1, lohi, lohi + LH, cf);
     // dual step scale: sigma mu_l (primal, d/dgamma), sigma beta_l (d/dmu)
     const float qc = MODE == WAVE_ITERATE ? (c == 1 ? sbl : sbl * mu) : 1.f;
-    ana_emit_step<MODE>(a, l, bb, c, kx0, ky0, qc, cf, pre, keep);
+    ana_emit_step<MODE, NS, LEVEL1>(a, l, bb, c, kx0, ky0, qc, cf, pre, keep);
     __syncthreads();
   }
 }
@@ -872,7 +877,7 @@ inline double level_flops(int CH, int L, int K, int h) {
   return (double)CH * L * 32.0 * (K * (K + 1) / 2) * (double)h * h;
 }
 
-template <int CH, int MODE, bool L1>
+template <int CH, int MODE, bool L1, int NS = 0>
 cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st, Prof *prof) {
   const double h = a.M >> 1, rw = MODE == WAVE_ITERATE ? 2.0 : 1.0;
   const double in = L1 ? (double)CH * a.L * a.M * a.M * (MODE == WAVE_ITERATE ? 8.0 : 4.0)
@@ -883,11 +888,11 @@ cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st, Prof *prof
                level_flops(CH, a.L, L1 ? a.K : a.K, (int)h), st);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_ana<CH, MODE, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_ana<CH, MODE, L1, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)ana_smem(CH));
     attr = true;
   }
-  k_ana<CH, MODE, L1><<<dim3(tiles(a.M >> 1), nblk_y), NT, ana_smem(CH), st>>>(a);
+  k_ana<CH, MODE, L1, NS><<<dim3(tiles(a.M >> 1), nblk_y), NT, ana_smem(CH), st>>>(a);
   return cudaGetLastError();
 }
 
@@ -957,7 +962,9 @@ cudaError_t analysis_all(const WaveArgs &w, const AnaArgs &base, cudaStream_t st
   a.M = w.n;
   a.last = (w.J == 1);
   a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[1];
-  cudaError_t e = launch_ana<CH, MODE, true>(a, w.L, st, w.prof);
+  cudaError_t e = w.n == 1024 ? launch_ana<CH, MODE, true, 1024>(a, w.L, st, w.prof)
+                  : w.n == 512 ? launch_ana<CH, MODE, true, 512>(a, w.L, st, w.prof)
+                               : launch_ana<CH, MODE, true>(a, w.L, st, w.prof);
   for (int j = 2; j <= w.J && e == cudaSuccess; ++j) {
     a.M = w.n >> (j - 1);
     a.in = w.scratch + w.lvl_off[j - 1];
