@@ -113,7 +113,10 @@ __global__ void k_axpy(const float *__restrict__ y, const float *__restrict__ d,
     out[i] = y[i] + eps * d[i];
 }
 
-// grid (blocks_per_band, L)
+// grid (blocks_per_band, L).  Four pixels per step: the six products of
+// each pixel in FP32 (the differences of the two groups' FP32 iterates are
+// exact when they are close), the four pixels' sums in FP32, then every
+// further sum in FP64 in a fixed order (deterministic).
 __global__ void k_sure_stats(SureStatsArgs a, double *__restrict__ part) {
   const size_t N = (size_t)a.n * a.n;
   const size_t CL = (size_t)a.L * N;   // stride between chains of a group
@@ -121,20 +124,54 @@ __global__ void k_sure_stats(SureStatsArgs a, double *__restrict__ part) {
   const double w = a.wband[l];
   const size_t base = (size_t)l * N;
   double v[6] = {0, 0, 0, 0, 0, 0};
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < N;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const size_t j = base + i;
-    const double gr = a.grad[j];
-    const double hd = a.htd[j];
-    const double xm = a.x[CL + j], xg = a.x[2 * CL + j];
-    const double xbm = a.xb[CL + j], xbg = a.xb[2 * CL + j];
-    const double x0 = a.x[j], xb0 = a.xb[j];
-    v[0] += gr * xm;
-    v[1] += gr * xg;
-    v[2] += (xbm - xm) * hd;
-    v[3] += (xbg - xg) * hd;
-    v[4] += x0 * (gr - (double)a.b[j]);
-    v[5] += (xb0 - x0) * hd;
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  if ((N & 3) == 0) {
+    const float4 *gr4 = reinterpret_cast<const float4 *>(a.grad + base);
+    const float4 *hd4 = reinterpret_cast<const float4 *>(a.htd + base);
+    const float4 *b4 = reinterpret_cast<const float4 *>(a.b + base);
+    const float4 *x04 = reinterpret_cast<const float4 *>(a.x + base);
+    const float4 *xm4 = reinterpret_cast<const float4 *>(a.x + CL + base);
+    const float4 *xg4 = reinterpret_cast<const float4 *>(a.x + 2 * CL + base);
+    const float4 *y04 = reinterpret_cast<const float4 *>(a.xb + base);
+    const float4 *ym4 = reinterpret_cast<const float4 *>(a.xb + CL + base);
+    const float4 *yg4 = reinterpret_cast<const float4 *>(a.xb + 2 * CL + base);
+    for (size_t q = t0; q < (N >> 2); q += stride) {
+      const float4 gr = gr4[q], hd = hd4[q], bb = b4[q];
+      const float4 x0 = x04[q], xm = xm4[q], xg = xg4[q];
+      const float4 y0 = y04[q], ym = ym4[q], yg = yg4[q];
+      float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      auto one = [&](float g, float h, float b, float p0, float pm, float pg, float q0,
+                     float qm, float qg) {
+        s[0] = fmaf(g, pm, s[0]);
+        s[1] = fmaf(g, pg, s[1]);
+        s[2] = fmaf(qm - pm, h, s[2]);
+        s[3] = fmaf(qg - pg, h, s[3]);
+        s[4] = fmaf(p0, g - b, s[4]);
+        s[5] = fmaf(q0 - p0, h, s[5]);
+      };
+      one(gr.x, hd.x, bb.x, x0.x, xm.x, xg.x, y0.x, ym.x, yg.x);
+      one(gr.y, hd.y, bb.y, x0.y, xm.y, xg.y, y0.y, ym.y, yg.y);
+      one(gr.z, hd.z, bb.z, x0.z, xm.z, xg.z, y0.z, ym.z, yg.z);
+      one(gr.w, hd.w, bb.w, x0.w, xm.w, xg.w, y0.w, ym.w, yg.w);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[k] += (double)s[k];
+    }
+  } else {
+    for (size_t i = t0; i < N; i += stride) {
+      const size_t j = base + i;
+      const double gr = a.grad[j];
+      const double hd = a.htd[j];
+      const double xm = a.x[CL + j], xg = a.x[2 * CL + j];
+      const double xbm = a.xb[CL + j], xbg = a.xb[2 * CL + j];
+      const double x0 = a.x[j], xb0 = a.xb[j];
+      v[0] += gr * xm;
+      v[1] += gr * xg;
+      v[2] += (xbm - xm) * hd;
+      v[3] += (xbg - xg) * hd;
+      v[4] += x0 * (gr - (double)a.b[j]);
+      v[5] += (xb0 - x0) * hd;
+    }
   }
   v[2] *= w; v[3] *= w; v[5] *= w;
   __shared__ double sh[32 * 6];

@@ -216,10 +216,10 @@ __device__ __forceinline__ void ana_cols_dispatch(int p, const float2 *lo_s,
 
 // U values the thread's column item updates in step (bb, c): subbands DX
 // (low y, high x), DY, HH and, at the last level, LL
-template <int MODE, int NS, bool L1>
+template <int MODE, int NS, int MS>
 __device__ __forceinline__ void ana_prefetch(const AnaArgs &a, int l, int bb, int c,
                                              int kx0, int ky0, float (&pre)[4][QY]) {
-  const int n = NS ? NS : a.n, M = (NS && L1) ? NS : a.M;
+  const int n = NS ? NS : a.n, M = MS ? MS : a.M;
   const int h = M >> 1, hn = h * n;
   const int kx = threadIdx.x % TX, s = threadIdx.x / TX;
   const int kxg = kx0 + kx;
@@ -238,12 +238,12 @@ __device__ __forceinline__ void ana_prefetch(const AnaArgs &a, int l, int bb, in
 
 // dual update p = u + q w, u = sat(p) (or the mask of channel 0) and the
 // stores of step (bb, c)
-template <int MODE, int NS, bool L1>
+template <int MODE, int NS, int MS>
 __device__ __forceinline__ void ana_emit_step(const AnaArgs &a, int l, int bb, int c,
                                               int kx0, int ky0, float q,
                                               const float (&cf)[4][QY],
                                               const float (&pre)[4][QY], uint32_t &keep) {
-  const int n = NS ? NS : a.n, M = (NS && L1) ? NS : a.M;
+  const int n = NS ? NS : a.n, M = MS ? MS : a.M;
   const int h = M >> 1, hn = h * n;
   const int kx = threadIdx.x % TX, s = threadIdx.x / TX;
   const int kxg = kx0 + kx;
@@ -279,14 +279,15 @@ __device__ __forceinline__ void ana_emit_step(const AnaArgs &a, int l, int bb, i
   }
 }
 
-// NS > 0: the image side n fixed at compile time (level 1 of the common
-// sizes), so every U offset of the dual update is an immediate
-template <int CH, int MODE, bool LEVEL1, int NS>
+// NS, MS > 0: the image side n and the level's input side M fixed at
+// compile time (levels 1 and 2 of the common sizes), so every U offset of
+// the dual update is an immediate
+template <int CH, int MODE, bool LEVEL1, int NS, int MS>
 __global__ void __launch_bounds__(NT, 4) k_ana(AnaArgs a) {
   extern __shared__ float2 smem2[];
   float2 *in_s = smem2;                     // [CH][A_RP][A_IP] row pairs
   float2 *lohi = in_s + CH * A_RP * A_IP;   // [A_RP][A_LP] lo, then hi
-  const int n = NS ? NS : a.n, M = (NS && LEVEL1) ? NS : a.M;
+  const int n = NS ? NS : a.n, M = MS ? MS : a.M;
   const int h = M >> 1;
   const int ntx = (h + TX - 1) / TX;
   const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
@@ -356,14 +357,14 @@ __global__ void __launch_bounds__(NT, 4) k_ana(AnaArgs a) {
   for (int s = 0; s < nsteps; ++s) {
     const int bb = b0 + s / CH, c = s % CH;
     float pre[4][QY];
-    ana_prefetch<MODE, NS, LEVEL1>(a, l, bb, c, kx0, ky0, pre);
+    ana_prefetch<MODE, NS, MS>(a, l, bb, c, kx0, ky0, pre);
     ana_rows_dispatch(bb + 1, in_s + c * A_RP * A_IP, lohi, lohi + LH);
     __syncthreads();
     float cf[4][QY];
     ana_cols_dispatch(bb + 1, lohi, lohi + LH, cf);
     // dual step scale: sigma mu_l (primal, d/dgamma), sigma beta_l (d/dmu)
     const float qc = MODE == WAVE_ITERATE ? (c == 1 ? sbl : sbl * mu) : 1.f;
-    ana_emit_step<MODE, NS, LEVEL1>(a, l, bb, c, kx0, ky0, qc, cf, pre, keep);
+    ana_emit_step<MODE, NS, MS>(a, l, bb, c, kx0, ky0, qc, cf, pre, keep);
     __syncthreads();
   }
 }
@@ -877,7 +878,7 @@ inline double level_flops(int CH, int L, int K, int h) {
   return (double)CH * L * 32.0 * (K * (K + 1) / 2) * (double)h * h;
 }
 
-template <int CH, int MODE, bool L1, int NS = 0>
+template <int CH, int MODE, bool L1, int NS = 0, int MS = 0>
 cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st, Prof *prof) {
   const double h = a.M >> 1, rw = MODE == WAVE_ITERATE ? 2.0 : 1.0;
   const double in = L1 ? (double)CH * a.L * a.M * a.M * (MODE == WAVE_ITERATE ? 8.0 : 4.0)
@@ -888,11 +889,11 @@ cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st, Prof *prof
                level_flops(CH, a.L, L1 ? a.K : a.K, (int)h), st);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_ana<CH, MODE, L1, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_ana<CH, MODE, L1, NS, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)ana_smem(CH));
     attr = true;
   }
-  k_ana<CH, MODE, L1, NS><<<dim3(tiles(a.M >> 1), nblk_y), NT, ana_smem(CH), st>>>(a);
+  k_ana<CH, MODE, L1, NS, MS><<<dim3(tiles(a.M >> 1), nblk_y), NT, ana_smem(CH), st>>>(a);
   return cudaGetLastError();
 }
 
@@ -962,15 +963,17 @@ cudaError_t analysis_all(const WaveArgs &w, const AnaArgs &base, cudaStream_t st
   a.M = w.n;
   a.last = (w.J == 1);
   a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[1];
-  cudaError_t e = w.n == 1024 ? launch_ana<CH, MODE, true, 1024>(a, w.L, st, w.prof)
-                  : w.n == 512 ? launch_ana<CH, MODE, true, 512>(a, w.L, st, w.prof)
+  cudaError_t e = w.n == 1024 ? launch_ana<CH, MODE, true, 1024, 1024>(a, w.L, st, w.prof)
+                  : w.n == 512 ? launch_ana<CH, MODE, true, 512, 512>(a, w.L, st, w.prof)
                                : launch_ana<CH, MODE, true>(a, w.L, st, w.prof);
   for (int j = 2; j <= w.J && e == cudaSuccess; ++j) {
     a.M = w.n >> (j - 1);
     a.in = w.scratch + w.lvl_off[j - 1];
     a.last = (j == w.J);
     a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[j];
-    e = launch_ana<CH, MODE, false>(a, w.L * w.K, st, w.prof);
+    if (j == 2 && w.n == 1024) e = launch_ana<CH, MODE, false, 1024, 512>(a, w.L * w.K, st, w.prof);
+    else if (j == 2 && w.n == 512) e = launch_ana<CH, MODE, false, 512, 256>(a, w.L * w.K, st, w.prof);
+    else e = launch_ana<CH, MODE, false>(a, w.L * w.K, st, w.prof);
   }
   return e;
 }
