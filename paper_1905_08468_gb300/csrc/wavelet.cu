@@ -232,7 +232,7 @@ __device__ __forceinline__ void ana_prefetch(const AnaArgs &a, int l, int bb, in
     pre[0][qq] = act ? up[o + h] : 0.f;
     pre[1][qq] = act ? up[o + hn] : 0.f;
     pre[2][qq] = act ? up[o + hn + h] : 0.f;
-    pre[3][qq] = (act && a.last) ? up[o] : 0.f;
+    pre[3][qq] = (act && !NS && a.last) ? up[o] : 0.f;
   }
 }
 
@@ -248,7 +248,8 @@ __device__ __forceinline__ void ana_emit_step(const AnaArgs &a, int l, int bb, i
   const int kx = threadIdx.x % TX, s = threadIdx.x / TX;
   const int kxg = kx0 + kx;
   float *up = a.u + ((size_t)(c * a.L + l) * a.K + bb) * ((size_t)n * n);
-  float *llp = a.last ? nullptr : a.ll_out + ((size_t)(c * a.L + l) * a.K + bb) * h * h;
+  const bool last = !NS && a.last;   // specialised sizes never run the last level
+  float *llp = last ? nullptr : a.ll_out + ((size_t)(c * a.L + l) * a.K + bb) * h * h;
   const int sbo[4] = {h, hn, hn + h, 0};
   if (c == 0) keep = 0;
 #pragma unroll
@@ -256,7 +257,7 @@ __device__ __forceinline__ void ana_emit_step(const AnaArgs &a, int l, int bb, i
     const int ky = ky0 + QY * s + qq;
     if (ky >= h || kxg >= h) continue;
     const int o = ky * n + kxg;
-    const int nsb = a.last ? 4 : 3;
+    const int nsb = last ? 4 : 3;
 #pragma unroll
     for (int sb = 0; sb < 4; ++sb) {
       if (sb >= nsb) break;
@@ -275,7 +276,7 @@ __device__ __forceinline__ void ana_emit_step(const AnaArgs &a, int l, int bb, i
       }
       up[o + sbo[sb]] = val;
     }
-    if (!a.last) llp[ky * h + kxg] = cf[3][qq];
+    if (!last) llp[ky * h + kxg] = cf[3][qq];
   }
 }
 
@@ -963,16 +964,17 @@ cudaError_t analysis_all(const WaveArgs &w, const AnaArgs &base, cudaStream_t st
   a.M = w.n;
   a.last = (w.J == 1);
   a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[1];
-  cudaError_t e = w.n == 1024 ? launch_ana<CH, MODE, true, 1024, 1024>(a, w.L, st, w.prof)
-                  : w.n == 512 ? launch_ana<CH, MODE, true, 512, 512>(a, w.L, st, w.prof)
-                               : launch_ana<CH, MODE, true>(a, w.L, st, w.prof);
+  // the size-specialised kernels assume a level below (J > level)
+  cudaError_t e = (w.n == 1024 && w.J > 1) ? launch_ana<CH, MODE, true, 1024, 1024>(a, w.L, st, w.prof)
+                  : (w.n == 512 && w.J > 1) ? launch_ana<CH, MODE, true, 512, 512>(a, w.L, st, w.prof)
+                                            : launch_ana<CH, MODE, true>(a, w.L, st, w.prof);
   for (int j = 2; j <= w.J && e == cudaSuccess; ++j) {
     a.M = w.n >> (j - 1);
     a.in = w.scratch + w.lvl_off[j - 1];
     a.last = (j == w.J);
     a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[j];
-    if (j == 2 && w.n == 1024) e = launch_ana<CH, MODE, false, 1024, 512>(a, w.L * w.K, st, w.prof);
-    else if (j == 2 && w.n == 512) e = launch_ana<CH, MODE, false, 512, 256>(a, w.L * w.K, st, w.prof);
+    if (j == 2 && w.J > 2 && w.n == 1024) e = launch_ana<CH, MODE, false, 1024, 512>(a, w.L * w.K, st, w.prof);
+    else if (j == 2 && w.J > 2 && w.n == 512) e = launch_ana<CH, MODE, false, 512, 256>(a, w.L * w.K, st, w.prof);
     else e = launch_ana<CH, MODE, false>(a, w.L * w.K, st, w.prof);
   }
   return e;
