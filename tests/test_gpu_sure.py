@@ -69,6 +69,36 @@ def test_sure_crop_of_the_tuning_workload():
     check(c, (1e-2, 1e-2), 20, 10, (2e-5, 2e-5))
 
 
+def test_sure_512_size_specialised_kernels():
+    """512^2 x 2: the analysis kernels compiled for a 512 px side (levels 1
+    and 2) against the oracle, one window of two iterations."""
+    c = make_cube(512, 2, 30, 2, 3000, seed=31)
+    check(c, (1e-2, 1e-2), 2, 2, (5e-5, 5e-5))
+
+
+def test_full_size_eta_zero_primal_equals_plain_solve():
+    """1024^2 x 64 (the tuning workload's shape, size-specialised kernels):
+    with eta = 0 the ADA-PT primal chain is the plain iteration, bit for bit
+    (the plain iteration at this size is checked against the oracle in
+    test_gpu_muffin)."""
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    n, L = 1024, 64
+    c = make_cube(n, L, 2000, 100, 200000, seed=3)
+    eps = fdmc_eps(c.noise_var)
+    d = dev(c.dirty, torch)
+    xs = torch.zeros_like(d)
+    with pkg.Plan(n, L, c.psf, sure=True) as plan:
+        th, _, _ = plan.sure_tune(d, dev(c.delta, torch), c.noise_var, xs, (1e-2, 1e-2), 4,
+                                  window=2, eta=(0.0, 0.0), eps=eps)
+    assert tuple(th) == (1e-2, 1e-2)
+    x = torch.zeros_like(d)
+    with pkg.Plan(n, L, c.psf) as plan:
+        plan.solve(d, x, 4, 1e-2, 1e-2)
+    torch.cuda.synchronize()
+    assert torch.equal(xs, x)
+
+
 def test_eta_zero_primal_equals_plain_solve():
     torch = cuda()
     import paper_1905_08468_gb300 as pkg
