@@ -88,15 +88,13 @@ void release_pool(muffin_server_s *S, size_t i) {
 
 // a pool for (n, L) with a free slot, creating one within the budget; -1: none now
 int find_pool(muffin_server_s *S, int n, int L, muffin_status *err) {
-  bool exists = false;
   for (size_t i = 0; i < S->pools.size(); ++i) {
     Pool &pl = S->pools[i];
     if (pl.n != n || pl.L != L) continue;
-    exists = true;
     for (int64_t r : pl.slot_req)
       if (r < 0) return (int)i;
   }
-  (void)exists;   // every pool of this shape is full: open another if it fits
+  // no pool of this shape has a free slot: open another if it fits
   muffin_params p = pool_params(S, n, L);
   size_t need = 0;
   *err = muffin_plan_estimate_bytes(&p, &need);
