@@ -41,7 +41,10 @@ constexpr int CTA_T = NG * GT;
 constexpr uint32_t TILE_B = TM * TL * 4;         // one A tile (32 KB)
 constexpr uint32_t CMAT_B = TL * TL * 4;         // one C table (16 KB)
 constexpr size_t SMEM = 4 * (size_t)CMAT_B + (size_t)NG * 2 * TILE_B + 1024;
-constexpr uint32_t TMEM_COLS = 256;              // two groups x (64 + 64) FP32 columns
+// tensor-memory columns per group: 64 per product accumulator; with three
+// chains chain 0's two accumulators are kept for chain 2 (see k_dct_tc)
+constexpr uint32_t group_cols(int ch) { return ch == 3 ? 256u : 128u; }
+constexpr uint32_t tmem_cols(int ch) { return NG * group_cols(ch); }   // 512 or 256
 constexpr long kSpin = 1L << 24;                 // polls of an mbarrier before giving up
 constexpr long kSpinInjected = 1L << 12;         // shorter bound when a time-out is injected
 // instruction descriptor: D FP32, A and B TF32, both K-major, N = 64, M = 128
@@ -113,15 +116,16 @@ __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(GT) : "memory");
 }
 
-// 3 x 8 MMAs of one TF32-split product into tensor-memory columns d
+// 3 x 8 MMAs of one TF32-split product into tensor-memory columns d; with
+// acc the product is added to what d holds
 __device__ __forceinline__ void issue_product(uint32_t d, uint32_t ahi, uint32_t alo,
-                                              uint32_t bhi, uint32_t blo) {
+                                              uint32_t bhi, uint32_t blo, bool acc) {
 #pragma unroll 1
   for (int ks = 0; ks < TL / 8; ++ks) {
     const uint32_t ko = (uint32_t)ks * 256u;   // two core matrices along K
     const uint64_t dah = sdesc(ahi + ko), dal = sdesc(alo + ko);
     const uint64_t dbh = sdesc(bhi + ko), dbl = sdesc(blo + ko);
-    const uint32_t first = ks == 0;
+    const uint32_t first = ks == 0 && !acc;
     asm volatile("{\n\t.reg .pred p;\n\tsetp.eq.u32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
                  ::"r"(d), "l"(dal), "l"(dbh), "r"(IDESC), "r"(first) : "memory");
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
   if (tid < 32) {
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(dst), "r"(TMEM_COLS) : "memory");
+                 ::"r"(dst), "r"(tmem_cols(CH)) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -215,9 +219,14 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
 
   const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar[g]);
   const uint32_t quad = (uint32_t)(wg & 3), h = (uint32_t)(wg >> 2);
-  const uint32_t d1 = tmem_base + ((quad * 32u) << 16) + (uint32_t)g * 128u;   // this warp's lanes
-  const uint32_t d2 = d1 + 64u;
-  const uint32_t dg1 = tmem_base + (uint32_t)g * 128u, dg2 = dg1 + 64u;       // MMA destinations
+  // accumulators of the group: [0, 64) first product of chains 0 and 2,
+  // [64, 128) second product of chains 0 and 2 (one chain: nothing else);
+  // three chains add [128, 192), [192, 256) for chain 1.  Chain 2 (d/dgamma)
+  // multiplies gamma z'_gamma + z and gamma v'_gamma + v (Algorithm 4): its
+  // products are accumulated onto chain 0's, C (gamma z') + C z, so chain
+  // 0's tiles are neither staged nor reloaded again.
+  const uint32_t lanes = tmem_base + ((quad * 32u) << 16) + (uint32_t)g * group_cols(CH);
+  const uint32_t gcol = tmem_base + (uint32_t)g * group_cols(CH);   // MMA destinations
   const uint32_t sa_hi = (uint32_t)__cvta_generic_to_shared(ahi);
   const uint32_t sa_lo = (uint32_t)__cvta_generic_to_shared(alo);
   const uint32_t sc_hi = (uint32_t)__cvta_generic_to_shared(cth[0]);
@@ -242,8 +251,11 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
     uint32_t keep = 0;
 #pragma unroll 1
     for (int c = 0; c < CH && ok; ++c) {
-      // ---- first product: z = 2x~ - x (and Algorithm 4's mix for d/dgamma);
-      // the raw tiles are staged through the A buffers, free at this point
+      const bool mix = CH == 3 && c == 2;          // accumulate onto chain 0's products
+      const uint32_t off1 = (CH == 3 && c == 1) ? 128u : 0u, off2 = off1 + 64u;
+      // ---- first product: z = 2x~ - x (gamma z' for d/dgamma, whose + z is
+      // chain 0's product already in tensor memory); the raw tiles are staged
+      // through the A buffers, free at this point
       const size_t tile_base = (size_t)cube * TL * N;
       const size_t p0 = p - row;
       float z[32];
@@ -256,18 +268,9 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
         z[j] = 2.f * *reinterpret_cast<const float *>(ahi + o) -
                *reinterpret_cast<const float *>(alo + o);
       }
-      if (CH == 3 && c == 2) {
-        group_sync(g);                     // every thread has read chain 2's tiles
-        stage_raw(a.xt, a.x, tile_base, N, p0, gt, ahi, alo);
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        group_sync(g);
+      if (mix) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int o = ((32 * (int)h + j) * TM + row) * 4;
-          const float z0 = 2.f * *reinterpret_cast<const float *>(ahi + o) -
-                           *reinterpret_cast<const float *>(alo + o);
-          z[j] = fmaf(gamma, z[j], z0);
-        }
+        for (int j = 0; j < 32; ++j) z[j] *= gamma;
       }
       group_sync(g);                       // staging reads done before the split overwrites it
       store_split(ahi, alo, row, (int)h, z);
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
       group_sync(g);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (gt == 0 && !a.inject) {
-        issue_product(dg1, sa_hi, sa_lo, sc_hi, sc_lo);
+        issue_product(gcol + off1, sa_hi, sa_lo, sc_hi, sc_lo, mix);
         commit(mb);
       }
       // old duals while the product runs
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
       if (bail[g]) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float acc[32];
-      tmem_row32(d1 + 32u * h, acc);
+      tmem_row32(lanes + off1 + 32u * h, acc);
       // ---- dual update (chain 0 sets the masks Pi(v~) used by the others)
       const float sg = (c == 2 ? sigma : sigma * gamma) * al;
 #pragma unroll
@@ -306,10 +309,9 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
         else a.v[c * CS + pix + (size_t)j * N] = vn;
         z[j] = vn;
       }
-      if (CH == 3 && c == 2) {             // gamma v'_gamma + v (Algorithm 4)
+      if (mix) {                           // gamma v'_gamma (+ v: chain 0's product)
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          z[j] = valid ? fmaf(gamma, z[j], a.v[pix + (size_t)j * N]) : 0.f;
+        for (int j = 0; j < 32; ++j) z[j] *= gamma;
       }
       // ---- second product: t = gamma_n C^T v
       store_split(ahi, alo, row, (int)h, z);
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
       group_sync(g);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (gt == 0 && !a.inject) {
-        issue_product(dg2, sa_hi, sa_lo, sct_hi, sct_lo);
+        issue_product(gcol + off2, sa_hi, sa_lo, sct_hi, sct_lo, mix);
         commit(mb);
       }
       if (!wait_phase(mb, ph, a.spin)) bail[g] = 1;
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
       group_sync(g);
       if (bail[g]) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      tmem_row32(d2 + 32u * h, acc);
+      tmem_row32(lanes + off2 + 32u * h, acc);
       const float s2 = (c == 2) ? al : gamma * al;
       if (valid) {
 #pragma unroll
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (tid < 32)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
-                 ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+                 ::"r"(tmem_base), "r"(tmem_cols(CH)) : "memory");
 }
 
 template <int CH>
