@@ -21,10 +21,12 @@
 // The analysis filters run on packed pairs (fma.rn.f32x2): the row pass
 // filters two image rows at once (the tile is stored as row pairs) and the
 // column pass splits each output into its even- and odd-tap halves.  The
-// synthesis column pass is scalar (its inputs arrive by cp.async in the
-// coefficient layout) and stores row pairs, so the synthesis row pass is
-// packed too.  Filters live in constant memory and every pass keeps a
-// sliding window of taps' inputs in registers.
+// synthesis has two variants with identical sums: the default keeps the
+// coefficient layout its cp.async copies deliver and packs both passes over
+// the output parity, (x[2k], x[2k+1]) += (h_2s, h_2s+1) * (c, c); the other
+// stores the column pass as row pairs and packs the row pass over two rows.
+// Filters live in constant memory and every pass keeps a sliding window of
+// taps' inputs in registers.
 //
 // Chains: a launch advances C = 1 (plain) or C = 3 chains {x, dx/dmu,
 // dx/dgamma} of one ADA-PT group.  The derivative channels use the masks of
@@ -375,11 +377,11 @@ __global__ void __launch_bounds__(NT, 4) k_ana(AnaArgs a) {
 // rows.  x[2k+e] = sum_s h[2s+e] a[k-s] + g[2s+e] d[k-s] (transpose of the
 // analysis, indices mod the level size).
 //
-// A CTA walks (basis, chain) steps; the coefficient tiles of the next step
-// are copied global->shared with cp.async while the current step computes
-// (double buffer).  Steps are pure per chain: by linearity the d/dmu chain's
-// synthesis of (u + mu u'_mu) (Algorithm 3) is accumulated as
-// W^T u + mu W^T u'_mu from the chain-0 and chain-1 steps.
+// A CTA walks (chain, basis) steps, chain-major; the coefficient tiles of the
+// next step are copied global->shared with cp.async while the current step
+// computes (double buffer).  Steps are pure per chain: by linearity the
+// d/dmu chain's synthesis of (u + mu u'_mu) (Algorithm 3) is accumulated as
+// W^T u + mu W^T u'_mu, continuing from chain 0's finished sum.
 
 __device__ __forceinline__ void cp_async4(float *dst, const float *src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -400,7 +402,7 @@ __device__ __forceinline__ void cp_async16(float *dst, const float *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 
-// copies of the four subband tiles of a (basis, chain) step: rows ky0-8 ..
+// copies of the four subband tiles of a (chain, basis) step: rows ky0-8 ..
 // ky0+TY-1 and columns kx0-8 .. kx0+TX-1 (mod the level size h).  With
 // h >= 8 every aligned group of 4 columns is contiguous in memory (the wrap
 // point is a multiple of 4), so whole groups move with 16-byte copies and a
