@@ -19,8 +19,9 @@
 // (free before the split), so the whole 64 KB is in flight at once.
 //
 // A CTA runs two independent groups of 8 warps that share the C tables but
-// own their A tiles, 128 tensor-memory columns and mbarrier, so one group's
-// global traffic overlaps the other's MMAs.  Waits on the mbarriers are
+// own their A tiles, tensor-memory columns (128, or 256 with three chains,
+// where the d/dgamma chain accumulates onto chain 0's products) and
+// mbarrier, so one group's global traffic overlaps the other's MMAs.  Waits on the mbarriers are
 // bounded: on time-out the kernel raises an error flag, waits once more and
 // frees its tensor memory; the host turns the flag into MUFFIN_ETIMEOUT.  A
 // host-side test hook makes the kernel skip its products so that this path
