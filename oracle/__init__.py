@@ -28,6 +28,5 @@ Parity pins: every function is checked by ``tests/test_oracle_*.py`` against
 closed forms, dense brute force, library special cases, finite differences
 and Monte-Carlo expectations.  The values the paper prints for its own
 datasets (tuned parameters, SNR, WMSE, Sec. 4.2.1) need data that is not
-available, so none of them is reproduced: against the paper's printed numbers
-the oracle is "parity unpinned"; against the mathematics it is pinned.
+available, so no pin uses a printed number.
 """
