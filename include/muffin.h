@@ -220,7 +220,68 @@ typedef struct {
   double lipschitz;   /* beta */
   double mu, gamma;   /* regularisation weights at the end of the call */
   int32_t records;    /* ADA-PT trace records written by this call */
+  int32_t checks;     /* convergence-monitor checks made by this call */
+  int32_t stopped_early; /* 1: the monitor's rel_tol ended the call early */
+  double rel_change;  /* last check, cube 0: ||X^k - X^{k-1}|| / ||X^{k-1}||
+                         (NaN without checks) */
+  double objective;   /* last check, cube 0: the objective (NaN if not asked) */
 } muffin_info;
+
+/* ---- convergence monitor (Sec. 2.1: the iteration has no closed form and
+ * is run until it settles; Sec. 3.3 monitors the iterates the same way)
+ *
+ * Every call of muffin_solve / muffin_sure_tune ends with an FP64 scan of the
+ * restored cube for NaN/Inf: if one is found the call returns
+ * MUFFIN_ENUMERIC, the caller's x holds the non-finite cube, and the plan
+ * forgets its iterate state (the next call must start cold, which works
+ * normally).  With monitoring on, the plan also checks the iterates of the
+ * primal chain on y after every `every` iterations (at the first window end
+ * at or after it for muffin_sure_tune), in FP64:
+ *   rel_change = ||X^k - X^{k-1}||_2 / ||X^{k-1}||_2 (inf when X^{k-1} = 0
+ *                and X^k != 0; 0 when both are 0),
+ *   objective  = sum_l 1/2 ||y_l - H_l x_l||^2 + sum_l mu_l ||W_s x_l||_1
+ *                + sum_n gamma_n ||W_lambda x^n||_1   (Eqs. probopt, RegAll;
+ *                X >= 0 always holds for the iterates), with the call's
+ *                (mu, gamma) (for ADA-PT the values after that window's
+ *                update), the residual from an FP64 convolution,
+ *   and the NaN/Inf scan (MUFFIN_ENUMERIC as above, at once).
+ * A check synchronises the plan's stream.  With rel_tol > 0 the call stops
+ * after the first check at which every cube has rel_change <= rel_tol
+ * (info->stopped_early = 1, info->iters_done = the iterations run). */
+typedef struct {
+  int32_t every;      /* K >= 1: check every K iterations; 0: end scan only */
+  int32_t objective;  /* 1: evaluate the objective at each check (keeps a
+                         device copy of the dirty cube, loaded by the next
+                         call that passes one) */
+  double rel_tol;     /* > 0: early exit as above; 0: fixed iteration count */
+} muffin_monitor_params;
+
+typedef struct {
+  int32_t k;          /* iterations completed by the call at the check */
+  int32_t cube;       /* cube index b < B */
+  double rel_change;  /* as above */
+  double objective;   /* as above, NaN when not evaluated */
+  int64_t nonfinite;  /* NaN/Inf entries of X^k */
+} muffin_monitor_record;
+
+/* mp = NULL switches monitoring off (the end-of-call scan stays).
+ * Errors: EINVAL (every < 0, rel_tol < 0 or not finite), ENOMEM, ECUDA. */
+MUFFIN_API muffin_status muffin_plan_set_monitor(muffin_plan plan,
+                                                 const muffin_monitor_params *mp);
+/* The last call's check records (per check, per cube, in order): copies up
+ * to capacity, *count = the number recorded.  Errors: EINVAL. */
+MUFFIN_API muffin_status muffin_plan_monitor_read(muffin_plan plan,
+                                                  muffin_monitor_record *out,
+                                                  int32_t capacity, int32_t *count);
+/* Objective (Eqs. probopt, RegAll) of a cube x [B][L][n][n] for the dirty
+ * cubes [B][L][n][n] (both host or device) and per-cube weights mu[B],
+ * gamma[B] (host), with the plan's PSFs and weights alpha_n, beta_l:
+ * f[b] (host, B values); +inf for a cube with a negative entry when the plan
+ * projects on the positive orthant.  FP64 sums, FP32 transforms.
+ * Errors: EINVAL (NULL argument, negative weights), ENOMEM, ECUDA. */
+MUFFIN_API muffin_status muffin_objective(muffin_plan plan, const float *dirty,
+                                          const float *x, const double *mu,
+                                          const double *gamma, double *f);
 
 #define MUFFIN_WARM 1 /* continue from the plan's current state (x ignored
                          on input; dirty may be NULL to keep the last one) */
@@ -292,6 +353,27 @@ MUFFIN_API muffin_status muffin_sure_tune(muffin_plan plan, const float *dirty,
                                double *theta, muffin_sure_record *trace,
                                int32_t flags, muffin_info *info);
 
+/* Global SUGAR descent with n_c chosen by the rule of Sec. 3.3 (after Eq.
+ * globalgrad): at every outer step, MUFFIN and the derivative chains run
+ * from the initial cube with theta fixed, and k -> ||grad R_{0:k}(theta)||
+ * (the SUGAR pair, derivatives carried from k = 0) is evaluated every
+ * `check` iterations; n_c is the first k >= 2 check with
+ *   | ||grad R_{0:k}|| - ||grad R_{0:k-check}|| | <= tol ||grad R_{0:k}||
+ * for every cube, or sp->iters (the cap) if that comes first; then
+ * theta <- max(theta - eta grad R_{0:n_c}, theta_min).  The cap sp->iters must
+ * be a multiple of check.  With tol = 0 the rule never fires and the result
+ * is muffin_sure_global's with n_c = sp->iters, up to the rounding of tau
+ * (recomputed on the device at every check).  Arguments as
+ * muffin_sure_global; trace record i of cube b (at [b][outer]) has k = the
+ * n_c used.  Errors: EINVAL (check < 1, tol < 0, cap not a multiple of
+ * check, ...), ESTATE, ENOMEM, ECUDA. */
+MUFFIN_API muffin_status muffin_sure_global_auto(muffin_plan plan, const float *dirty,
+                                                 const float *delta, const double *noise_var,
+                                                 const muffin_sure_params *sp, int32_t outer,
+                                                 int32_t check, double tol, float *x,
+                                                 double *theta, muffin_sure_record *trace,
+                                                 muffin_info *info);
+
 /* Global SUGAR descent (Eq. globalgrad): `outer` steps of
  *   theta <- max(theta - eta * SUGAR_{0:n_c}(theta), theta_min)
  * where every step restarts both primal chains from the same initial cube
@@ -311,7 +393,18 @@ MUFFIN_API muffin_status muffin_sure_global(muffin_plan plan, const float *dirty
 /* ---- checkpoint / resume ------------------------------------------------
  * The state blob holds the iterates (X, U, V, T of every chain), the
  * dirty-cube terms and theta; importing it into a plan created with the
- * same parameters and PSF continues bit-identically (MUFFIN_WARM calls). */
+ * same parameters and PSF continues bit-identically (MUFFIN_WARM calls).
+ * Blob layout (native byte order), so that the iterates can be inspected:
+ *   56-byte header: char magic[8]; int32 n, L, K, J, sure, B; int64 k_done;
+ *                   int32 have_b, have_state, have_sure_state, dictionary;
+ *   per cube: double {psure constant, mu, gamma};
+ *   per chain group g (g = 0 on y; with sure = 1 also g = 1 on
+ *   y + eps delta), each of C chains (C = 3 with sure = 1: primal, dX/dmu,
+ *   dX/dgamma (Algorithms 3/4); else C = 1), float32 arrays in the order
+ *     X [C][B*L][n][n], U [C][B*L][K][n][n], V [C][B*L][n][n], T [C][B*L][n][n];
+ *   H^T y [B*L][n][n] float32; with sure = 1 also H^T y_bar and H^T delta;
+ *   the per-cube device scalars (4 doubles each: mu, gamma, tau, sigma);
+ *   per band 2 sigma_l^2 / eps (double). */
 MUFFIN_API muffin_status muffin_state_size(muffin_plan plan, size_t *bytes);
 MUFFIN_API muffin_status muffin_state_export(muffin_plan plan, void *host_buf,
                                   size_t bytes);
@@ -398,8 +491,9 @@ MUFFIN_API muffin_status muffin_server_stats(muffin_server s, size_t *device_byt
  * memory-pool callback).
  *
  * u = W_s x, exactly what muffin_op_analysis computes, with no plan: x
- * [nbands][n][n] and u [nbands][n_wavelets][n][n] are device arrays owned by
- * the caller; the work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ * [nbands][n][n] and u [nbands][n_wavelets][n][n] are non-overlapping arrays
+ * owned by the caller, in device memory of the current device (or managed
+ * memory); the work is enqueued on `stream` (a cudaStream_t, NULL = legacy
  * default stream) and the call returns without synchronising.  Levels 2..J
  * use a fixed file-scope device scratch of 4 Mi floats (16 MiB), which every
  * GPU that loads the library keeps until the process exits; a cube needing
@@ -408,12 +502,15 @@ MUFFIN_API muffin_status muffin_server_stats(muffin_server s, size_t *device_byt
  * cudaMalloc/cudaFree, no library allocation).  The first call on a device
  * does a one-time set-up with that device current (it looks up the
  * scratch's device address and uploads the filter taps); make that first
- * call before any stream capture.  All calls share the one scratch array and
+ * call before any stream capture.  The set-up is redone when the device's
+ * context has changed since (after cudaDeviceReset), so the first call after
+ * a reset must also come before any capture.  All calls share the one scratch array and
  * it keeps the previous call's contents (every level writes the LL values it
  * later reads, so nothing needs clearing); calls whose work overlaps on the
  * GPU (different streams, or different threads) race on it and must be
  * ordered by the caller.
- * Errors: EINVAL (NULL or host arrays, bad shape, scratch too small), ECUDA. */
+ * Errors: EINVAL (NULL or host arrays, arrays of another device, x and u
+ * overlapping, bad shape, scratch too small), ECUDA. */
 MUFFIN_API muffin_status muffin_op_analysis_noalloc(const float *x, float *u,
                                                     int32_t n, int32_t nbands,
                                                     int32_t n_wavelets,

@@ -9,6 +9,11 @@
   used to initialise the algorithm (Sec. 2.1).  The paper leaves eps open;
   it is an input here, one value for the alphas and one for the betas.
 * Eq. (globalgrad), Sec. 3.3: theta^(i+1) = theta^(i) - eta grad R_{0:n_c},
+  where n_c is either given or, as the paragraph after Eq. (globalgrad)
+  suggests, found by watching k -> ||grad R_{0:k}(theta^(i))||: reading
+  taken, n_c is the first multiple k >= 2 check of the check interval at
+  which that norm changed by at most tol times itself since k - check (or
+  the cap, if reached first);
   where grad R_{0:n_c} is SUGAR after running MUFFIN and its derivative
   iterates for n_c iterations from the same initialisation with theta^(i)
   held fixed.  One such outer step is ADA-PT (Algorithm 5) with a single
@@ -63,4 +68,36 @@ def global_descent(prob: Problem, delta, eps: float, noise_var, theta0, outer: i
                    safety=safety)
         records.append(r.trace[-1])
         theta, x = r.theta, r.x
+    return x, theta, records
+
+
+def global_descent_auto(prob: Problem, delta, eps: float, noise_var, theta0, outer: int,
+                        check: int, tol: float, n_cap: int, eta=(1e-3, 1e-3),
+                        theta_min: float = 1e-8, step_rule: int = 0, safety: float = 0.99):
+    """Eq. (globalgrad) with n_c chosen by the rule above.  Each outer step
+    runs MUFFIN and the derivative chains from the zero initialisation with
+    theta fixed, ``check`` iterations at a time (derivatives carried, so each
+    window end gives grad R_{0:k}), stops at n_c and takes the descent step.
+    Returns (x of the last run, theta, records), records holding the theta
+    used, SUGAR, PSURE, tau and k = n_c of every step."""
+    theta = np.array(theta0, np.float64)
+    eta = np.asarray(eta, np.float64)
+    records, x = [], None
+    for _ in range(outer):
+        states, prev, k, last = None, None, 0, None
+        while True:
+            r = ada_pt(prob, delta, eps, noise_var, theta, check, Delta=check, eta=(0.0, 0.0),
+                       theta_min=theta_min, reset=False, step_rule=step_rule, safety=safety,
+                       states=states)
+            states, k, last = r.states, k + check, r.trace[-1]
+            nrm = float(np.linalg.norm(last["sugar"]))
+            settled = prev is not None and k >= 2 * check and abs(nrm - prev) <= tol * nrm
+            prev = nrm
+            if settled or k >= n_cap:
+                break
+        rec = dict(last)
+        rec["k"] = k
+        records.append(rec)
+        theta = np.maximum(theta - eta * rec["sugar"], theta_min)
+        x = states[0].x
     return x, theta, records

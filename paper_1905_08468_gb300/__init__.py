@@ -248,6 +248,69 @@ class Plan:
         return ([(th[2 * c], th[2 * c + 1]) for c in range(B)],
                 [cube_trace(c) for c in range(B)], info)
 
+    def sure_global_auto(self, dirty, delta, noise_var, x, theta, n_cap: int, outer: int, *,
+                         check: int, tol: float, eta=(1e-3, 1e-3), theta_min: float = 1e-8,
+                         eps: float):
+        """Global SUGAR descent with n_c chosen by watching ||SUGAR_{0:k}||
+        every `check` iterations (``muffin_sure_global_auto``); the trace
+        records' k is the n_c of each step."""
+        keep = []
+        sp = native.SureParams()
+        self._lib.muffin_sure_params_default(ctypes.byref(sp))
+        sp.iters, sp.window = int(n_cap), int(check)
+        sp.eta_mu, sp.eta_gamma = float(eta[0]), float(eta[1])
+        sp.theta_min, sp.eps = theta_min, float(eps)
+        B = self.B
+        th_in = np.broadcast_to(np.asarray(theta, dtype=np.float64).reshape(-1, 2), (B, 2))
+        th = (ctypes.c_double * (2 * B))(*th_in.ravel())
+        cap = max(1, int(outer))
+        rec = (SureRecord * (cap * B))()
+        nv_arr = np.ascontiguousarray(noise_var, dtype=np.float64)
+        keep.append(nv_arr)
+        info = native.Info()
+        native.check(self._lib.muffin_sure_global_auto(
+            self._h, _ptr(dirty, keep), _ptr(delta, keep), ctypes.c_void_p(nv_arr.ctypes.data),
+            ctypes.byref(sp), int(outer), int(check), float(tol), _ptr(x, keep), th, rec,
+            ctypes.byref(info)))
+        def cube_trace(c):
+            return [dict(k=r.k, mu=r.mu, gamma=r.gamma, sugar_mu=r.sugar_mu,
+                         sugar_gamma=r.sugar_gamma, psure=r.psure, tau=r.tau)
+                    for r in rec[c * cap: c * cap + info.records]]
+        if B == 1:
+            return (th[0], th[1]), cube_trace(0), info
+        return ([(th[2 * c], th[2 * c + 1]) for c in range(B)],
+                [cube_trace(c) for c in range(B)], info)
+
+    # -- convergence monitor
+    def set_monitor(self, every: int = 0, objective: bool = False, rel_tol: float = 0.0,
+                    off: bool = False) -> None:
+        """Check the iterates every `every` iterations (``muffin_plan_set_monitor``)."""
+        if off:
+            native.check(self._lib.muffin_plan_set_monitor(self._h, None))
+            return
+        mp = native.MonitorParams(int(every), int(bool(objective)), float(rel_tol))
+        native.check(self._lib.muffin_plan_set_monitor(self._h, ctypes.byref(mp)))
+
+    def monitor_records(self) -> list:
+        cnt = ctypes.c_int32()
+        native.check(self._lib.muffin_plan_monitor_read(self._h, None, 0, ctypes.byref(cnt)))
+        arr = (native.MonitorRecord * max(1, cnt.value))()
+        native.check(self._lib.muffin_plan_monitor_read(self._h, arr, cnt.value,
+                                                        ctypes.byref(cnt)))
+        return [dict(k=r.k, cube=r.cube, rel_change=r.rel_change, objective=r.objective,
+                     nonfinite=int(r.nonfinite)) for r in arr[: cnt.value]]
+
+    def objective(self, dirty, x, mu, gamma):
+        """Eqs. probopt/RegAll per cube (a float when the plan holds one cube)."""
+        keep = []
+        B = self.B
+        m = (ctypes.c_double * B)(*np.broadcast_to(np.asarray(mu, float), B))
+        g = (ctypes.c_double * B)(*np.broadcast_to(np.asarray(gamma, float), B))
+        f = (ctypes.c_double * B)()
+        native.check(self._lib.muffin_objective(self._h, _ptr(dirty, keep), _ptr(x, keep),
+                                                m, g, f))
+        return f[0] if B == 1 else list(f)
+
     # -- weights (Eq. 2regpar)
     def set_weights(self, alpha=None, beta=None) -> None:
         """alpha [B][n*n] pixel weights, beta [B][L] band weights (None keeps)."""
@@ -291,6 +354,41 @@ class Plan:
         buf = ctypes.create_string_buffer(sz.value)
         native.check(self._lib.muffin_state_export(self._h, buf, sz.value))
         return buf.raw
+
+    def state_arrays(self) -> dict:
+        """The iterates of ``state_export`` as numpy arrays (layout of the
+        blob documented in muffin.h): x, v, t [G][C][B*L][n][n] and u
+        [G][C][B*L][K][n][n] for the G chain groups (G = 2 with ADA-PT: on y
+        and on y + eps delta) of C chains each (primal, d/dmu, d/dgamma),
+        b, and with ADA-PT b_bar and H^T delta [B*L][n][n]; mu, gamma [B]."""
+        blob = self.state_export()
+        hdr = np.frombuffer(blob, dtype=np.int32, count=14)
+        n, L, K, sure, B = (int(v) for v in (hdr[2], hdr[3], hdr[4], hdr[6], hdr[7]))
+        off = 56
+        cub = np.frombuffer(blob, dtype=np.float64, count=3 * B, offset=off).reshape(B, 3)
+        off += 24 * B
+        NL, G = B * L * n * n, 2 if sure else 1
+        C = 3 if sure else 1
+        out = {"mu": cub[:, 1].copy(), "gamma": cub[:, 2].copy()}
+
+        def take(count, shape):
+            nonlocal off
+            a = np.frombuffer(blob, dtype=np.float32, count=count, offset=off).reshape(shape)
+            off += 4 * count
+            return a.copy()
+        cube = (B * L, n, n)
+        parts = {k: [] for k in ("x", "u", "v", "t")}
+        for _ in range(G):
+            parts["x"].append(take(C * NL, (C,) + cube))
+            parts["u"].append(take(C * NL * K, (C, B * L, K, n, n)))
+            parts["v"].append(take(C * NL, (C,) + cube))
+            parts["t"].append(take(C * NL, (C,) + cube))
+        out.update({k: np.stack(v) for k, v in parts.items()})
+        out["b"] = take(NL, cube)
+        if sure:
+            out["bbar"] = take(NL, cube)
+            out["htd"] = take(NL, cube)
+        return out
 
     def state_import(self, blob: bytes) -> None:
         buf = ctypes.create_string_buffer(blob, len(blob))

@@ -169,6 +169,25 @@ struct ThetaUpdateArgs {
 };
 cudaError_t theta_update(const ThetaUpdateArgs &a, cudaStream_t st);
 
+// ------------------------------------------------------------ monitor (monitor.cu)
+// Doubles of scratch the monitor reductions need for L bands: partials
+// [L][16][3], then the outputs state [L][3], residual [L], |W_s x| [L],
+// alpha |W_lambda x| [L].
+size_t monitor_scratch_doubles(int L);
+// out[l][0..2] = {sum (x - xo)^2, sum xo^2 (sum x^2 when xo is NULL), number
+// of NaN/Inf entries of x} over the N values of band l (FP64)
+cudaError_t mon_state(const float *x, const float *xo, int L, size_t N, double *scratch,
+                      double *out, cudaStream_t st);
+// out[l] = sum_i (scale * w[l][i].x - y[l][i])^2 (FP64)
+cudaError_t mon_resid2(const double2 *w, const float *y, double scale, int L, size_t N,
+                       double *scratch, double *out, cudaStream_t st);
+// out[l] = sum_i a_i |u[l][i]| over per_band values, a_i = alpha[(l / Lc) N + i mod N]
+// (or 1 when alpha is NULL)
+cudaError_t mon_abs(const float *u, int L, size_t per_band, const float *alpha, int Lc,
+                    size_t N, double *scratch, double *out, cudaStream_t st);
+// a *= h elementwise (complex FP64)
+cudaError_t mul_c64(double2 *a, const double2 *h, size_t count, cudaStream_t st);
+
 // ------------------------------------------------------------ wavelets (wavelet.cu)
 // Filters db1..db8: h, g taps (g[i] = (-1)^i h[2p-1-i]) uploaded to constant memory.
 cudaError_t upload_filters(const double h[8][16]);

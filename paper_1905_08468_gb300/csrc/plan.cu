@@ -17,6 +17,7 @@
 // CUDA graphs on the plan's own stream and replayed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -231,6 +232,7 @@ muffin_status set_weights(muffin_plan P, const std::vector<float> &a,
     }
   }
   P->Asum = as; P->Amax2 = am; P->Bsum = bs; P->Bmax2 = bm;
+  P->beta_h = bw;
   CK(cudaMemcpyAsync(P->alpha, a.data(), a.size() * 4, cudaMemcpyHostToDevice, P->ws));
   CK(cudaMemcpyAsync(P->beta, bw.data(), bw.size() * 4, cudaMemcpyHostToDevice, P->ws));
   CK(cudaStreamSynchronize(P->ws));
@@ -264,6 +266,7 @@ muffin_status plan_alloc_init(muffin_plan P, const float *alpha, const float *be
   CK(cudaMemsetAsync(P->kerr, 0, sizeof(int), P->ws));
   CK(P->alloc(&P->dred, kRedSure + 65 * (size_t)Lt + 6 * (size_t)(Lt > 4096 ? Lt : 4096)));
   CK(P->alloc(&P->wband, (size_t)Lt));
+  CK(P->alloc(&P->mon, monitor_scratch_doubles(Lt)));
   CK(P->alloc(&P->S, (size_t)P->Cmax * Lt * nh * n));
   size_t off = 0;
   if (P->dict == 1) {
@@ -398,6 +401,120 @@ muffin_status window_end(muffin_plan P, const muffin_sure_params *sp) {
   return MUFFIN_OK;
 }
 
+// Results of one monitor evaluation, per cube.
+struct MonOut {
+  std::vector<double> rel, obj;
+  std::vector<long long> nonfinite;
+  long long nonfinite_total = 0;
+};
+
+// FP64 monitor of a cube of iterates x (device, [B][L][n][n]) against the
+// previous iterates xo (NULL: scan x only); with y (device dirty cubes) also
+// the objective (Eqs. probopt, RegAll) at x with per-cube (mu, gamma):
+// the residual y - H x from an FP64 convolution (the plan's FP64 spectra),
+// ||W_s x_l||_1 and ||W_lambda x^n||_1 from the FP32 transforms, all sums
+// in FP64.  Synchronises the work stream.
+muffin_status monitor_eval(muffin_plan P, const float *x, const float *xo, const float *y,
+                           const std::vector<double> &mu, const std::vector<double> &gamma,
+                           MonOut &r) {
+  const int Lt = P->Lt, L = P->L, B = P->B;
+  const size_t N = P->N;
+  double *part = P->mon;
+  double *o_state = part + 48 * (size_t)Lt, *o_res = o_state + 3 * (size_t)Lt;
+  double *o_u = o_res + Lt, *o_v = o_u + Lt;
+  CK(mon_state(x, xo, Lt, N, part, o_state, P->ws));
+  if (y) {
+    muffin_status s = ensure_op_buffers(P);
+    if (s != MUFFIN_OK) return s;
+    CK(real_to_c64(x, P->w64a, P->NL, P->ws));
+    CK(fft2d_c64(P->w64a, P->w64b, P->n, Lt, false, P->tw64, P->ws));
+    CK(mul_c64(P->w64a, P->hhat, P->NL, P->ws));
+    CK(fft2d_c64(P->w64a, P->w64b, P->n, Lt, true, P->tw64, P->ws));
+    CK(mon_resid2(P->w64a, y, 1.0 / (double)N, Lt, N, part, o_res, P->ws));
+    CK(wavelet_analysis_op(P->wave(1), x, P->op_out, P->ws));
+    CK(mon_abs(P->op_out, Lt, (size_t)P->K * N, nullptr, L, N, part, o_u, P->ws));
+    CK(dct_op(P->dct(1), x, P->op_out, 0, P->ws));
+    CK(mon_abs(P->op_out, Lt, N, P->alpha, L, N, part, o_v, P->ws));
+  }
+  std::vector<double> h(6 * (size_t)Lt);
+  CK(cudaMemcpyAsync(h.data(), o_state, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                     P->ws));
+  CK(cudaStreamSynchronize(P->ws));
+  const double *hs = h.data(), *hr = hs + 3 * Lt, *hu = hr + Lt, *hv = hu + Lt;
+  r.rel.assign(B, 0.0);
+  r.obj.assign(B, std::nan(""));
+  r.nonfinite.assign(B, 0);
+  r.nonfinite_total = 0;
+  for (int c = 0; c < B; ++c) {
+    double d2 = 0, p2 = 0, nf = 0, res = 0, l1u = 0, l1v = 0;
+    for (int l = c * L; l < (c + 1) * L; ++l) {
+      d2 += hs[3 * l]; p2 += hs[3 * l + 1]; nf += hs[3 * l + 2];
+      res += hr[l]; l1u += (double)P->beta_h[l] * hu[l]; l1v += hv[l];
+    }
+    r.rel[c] = p2 > 0 ? std::sqrt(d2 / p2) : (d2 > 0 ? INFINITY : 0.0);
+    r.nonfinite[c] = (long long)nf;
+    r.nonfinite_total += (long long)nf;
+    if (y) r.obj[c] = 0.5 * res + mu[c] * l1u + gamma[c] * l1v;
+  }
+  return MUFFIN_OK;
+}
+
+// a check of the primal chain on y after k iterations of the current call:
+// records, numeric failure, early-exit test (every cube at or below rel_tol)
+muffin_status monitor_check(muffin_plan P, int k, const std::vector<double> &mu,
+                            const std::vector<double> &gamma, bool *converged,
+                            muffin_info *info) {
+  const Group &g = P->grp[0];
+  const bool obj = P->mon_p.objective != 0;
+  if (obj && !P->have_y)
+    return fail(MUFFIN_ESTATE, "the monitor's objective needs the dirty cube: pass it to the call");
+  MonOut r;
+  muffin_status s = monitor_eval(P, g.x, g.xt, obj ? P->ydev : nullptr, mu, gamma, r);
+  if (s != MUFFIN_OK) return s;
+  bool conv = P->mon_p.rel_tol > 0;
+  for (int c = 0; c < P->B; ++c) {
+    muffin_monitor_record rec{};
+    rec.k = k; rec.cube = c; rec.rel_change = r.rel[c]; rec.objective = r.obj[c];
+    rec.nonfinite = r.nonfinite[c];
+    P->mon_rec.push_back(rec);
+    if (!(r.rel[c] <= P->mon_p.rel_tol)) conv = false;
+  }
+  if (info) {
+    info->checks += 1;
+    info->rel_change = r.rel[0];
+    info->objective = r.obj[0];
+  }
+  if (r.nonfinite_total > 0) {
+    P->have_state = P->have_sure_state = false;
+    return fail(MUFFIN_ENUMERIC, "%lld NaN/Inf entries in X after %d iterations",
+                r.nonfinite_total, k);
+  }
+  *converged = conv;
+  return MUFFIN_OK;
+}
+
+// end-of-call scan of the restored cube for NaN/Inf
+muffin_status final_scan(muffin_plan P, int k) {
+  MonOut r;
+  std::vector<double> z(P->B, 0.0);
+  muffin_status s = monitor_eval(P, P->grp[0].x, nullptr, nullptr, z, z, r);
+  if (s != MUFFIN_OK) return s;
+  if (r.nonfinite_total > 0) {
+    P->have_state = P->have_sure_state = false;
+    return fail(MUFFIN_ENUMERIC, "%lld NaN/Inf entries in X after %d iterations",
+                r.nonfinite_total, k);
+  }
+  return MUFFIN_OK;
+}
+
+void info_monitor_defaults(muffin_info *info) {
+  if (!info) return;
+  info->checks = 0;
+  info->stopped_early = 0;
+  info->rel_change = std::nan("");
+  info->objective = std::nan("");
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- internal API
@@ -476,6 +593,11 @@ muffin_status load_dirty(muffin_plan P, int b0, int b1, const float *dirty) {
                    P->w64b + off);
   if (s != MUFFIN_OK) return s;
   CK(c64_real_to_f32(P->w64a + off, P->b + off, 1.0 / ((double)P->n * P->n), cnt, P->ws));
+  if (P->ydev) {
+    CK(cudaMemcpyAsync(P->ydev + off, P->stage_a + off, cnt * sizeof(float),
+                       cudaMemcpyDeviceToDevice, P->ws));
+    if (b0 == 0 && b1 == P->B) P->have_y = true;
+  }
   return MUFFIN_OK;
 }
 
@@ -564,7 +686,8 @@ size_t estimate_bytes(const muffin_params *p) {
              C * Lt * nh * n * 8 + (ll ? ll : 1) * 4 + 3 * NL * 4 +
              C * NL * (5 + K) * 4;
   if (p->sure) b += 3 * NL * (5 + K) * 4 + 2 * NL * 4;
-  return b + (p->sure ? 37 : 29) * 16;   // 16 bytes of slack per allocation
+  b += monitor_scratch_doubles((int)Lt) * 8;
+  return b + (p->sure ? 38 : 30) * 16;   // 16 bytes of slack per allocation
 }
 
 muffin_status create(const muffin_params *p, const float *psf, const float *alpha,
@@ -718,17 +841,46 @@ muffin_status muffin_solve_batch(muffin_plan P, const float *dirty, float *x,
   if (s != MUFFIN_OK) return s;
   P->have_state = true;
   P->have_sure_state = false;
-  s = pi::run_plain(P, iters, P->B);
-  if (s != MUFFIN_OK) return s;
+  if (P->mon_p.objective && !P->have_y)
+    return fail(MUFFIN_ESTATE, "the monitor's objective needs the dirty cube: pass it to the call");
+  muffin_info scratch_info{};
+  muffin_info *inf = info ? info : &scratch_info;
+  info_monitor_defaults(inf);
+  P->mon_rec.clear();
+  const std::vector<double> mv(mu, mu + P->B), gv(gamma, gamma + P->B);
+  const int every = P->mon_p.every;
+  int done = 0;
+  muffin_status numeric = MUFFIN_OK;
+  while (done < iters) {
+    const int seg = every > 0 ? std::min(every, iters - done) : iters - done;
+    s = pi::run_plain(P, seg, P->B);
+    if (s != MUFFIN_OK) return s;
+    done += seg;
+    if (every > 0 && done % every == 0) {
+      bool conv = false;
+      s = monitor_check(P, done, mv, gv, &conv, inf);
+      if (s == MUFFIN_ENUMERIC) { numeric = s; break; }
+      if (s != MUFFIN_OK) return s;
+      if (conv) {
+        inf->stopped_early = done < iters;
+        break;
+      }
+    }
+  }
+  if (numeric == MUFFIN_OK) {
+    s = final_scan(P, done);
+    if (s == MUFFIN_ENUMERIC) numeric = s;
+    else if (s != MUFFIN_OK) return s;
+  }
+  const std::string numeric_msg = numeric != MUFFIN_OK ? muffin_last_error() : "";
   s = pi::fetch_x(P, 0, P->B, x);
   if (s != MUFFIN_OK) return s;
   s = pi::leave(P, true);
   if (s != MUFFIN_OK) return s;
-  if (info) {
-    info->iters_done = iters; info->tau = P->tau_for(0, mu[0], gamma[0]);
-    info->sigma = P->p.sigma; info->lipschitz = P->lips[0];
-    info->mu = mu[0]; info->gamma = gamma[0]; info->records = 0;
-  }
+  inf->iters_done = done; inf->tau = P->tau_for(0, mu[0], gamma[0]);
+  inf->sigma = P->p.sigma; inf->lipschitz = P->lips[0];
+  inf->mu = mu[0]; inf->gamma = gamma[0]; inf->records = 0;
+  if (numeric != MUFFIN_OK) return fail(numeric, "%s", numeric_msg.c_str());
   return MUFFIN_OK;
 }
 
@@ -825,6 +977,31 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
   }
   const bool graphs = P->use_graphs && !P->profiling;
   std::vector<long long> rec_k;
+  if (P->mon_p.objective && !P->have_y)
+    return fail(MUFFIN_ESTATE, "the monitor's objective needs the dirty cube: pass it to the call");
+  muffin_info scratch_info{};
+  muffin_info *inf = info ? info : &scratch_info;
+  info_monitor_defaults(inf);
+  P->mon_rec.clear();
+  muffin_status numeric = MUFFIN_OK;
+  const int every = P->mon_p.every;
+  int next_check = every;
+  // a check at a window end at or after every `every` iterations
+  auto window_check = [&](int done, bool *stop) -> muffin_status {
+    *stop = false;
+    if (every <= 0 || done < next_check) return MUFFIN_OK;
+    while (next_check <= done) next_check += every;
+    std::vector<DevScalars> th(B);
+    CK(cudaMemcpyAsync(th.data(), P->sc, B * sizeof(DevScalars), cudaMemcpyDeviceToHost, P->ws));
+    CK(cudaStreamSynchronize(P->ws));
+    std::vector<double> m(B), g(B);
+    for (int c = 0; c < B; ++c) { m[c] = th[c].mu; g[c] = th[c].gamma; }
+    bool conv = false;
+    muffin_status r = monitor_check(P, done, m, g, &conv, inf);
+    if (r != MUFFIN_OK) return r;
+    if (conv && done < sp->iters) { inf->stopped_early = 1; *stop = true; }
+    return MUFFIN_OK;
+  };
   int it = 0;
   while (it < sp->iters) {
     const bool at_boundary = P->k_done % sp->window == 0;
@@ -852,6 +1029,11 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
       it += sp->window;
       P->k_done += sp->window;
       rec_k.push_back(P->k_done);
+      bool stop = false;
+      s = window_check(it, &stop);
+      if (s == MUFFIN_ENUMERIC) { numeric = s; break; }
+      if (s != MUFFIN_OK) return s;
+      if (stop) break;
       continue;
     }
     s = iterate_group(P, P->grp[0]);
@@ -863,8 +1045,19 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
       s = window_end(P, sp);
       if (s != MUFFIN_OK) return s;
       rec_k.push_back(P->k_done);
+      bool stop = false;
+      s = window_check(it, &stop);
+      if (s == MUFFIN_ENUMERIC) { numeric = s; break; }
+      if (s != MUFFIN_OK) return s;
+      if (stop) break;
     }
   }
+  if (numeric == MUFFIN_OK) {
+    s = final_scan(P, it);
+    if (s == MUFFIN_ENUMERIC) numeric = s;
+    else if (s != MUFFIN_OK) return s;
+  }
+  const std::string numeric_msg = numeric != MUFFIN_OK ? muffin_last_error() : "";
   const int nrec = (int)rec_k.size();
   s = pi::fetch_x(P, 0, B, x);
   if (s != MUFFIN_OK) return s;
@@ -888,11 +1081,15 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
         t.k = (int32_t)rec_k[q]; t.mu = r[1]; t.gamma = r[2];
         t.sugar_mu = r[3]; t.sugar_gamma = r[4]; t.psure = r[5]; t.tau = r[6];
       }
-  if (info) {
-    info->iters_done = sp->iters; info->tau = hs[0].tau; info->sigma = P->p.sigma;
-    info->lipschitz = P->lips[0]; info->mu = hs[0].mu; info->gamma = hs[0].gamma;
-    info->records = nrec;
-  }
+  inf->iters_done = it; inf->tau = hs[0].tau; inf->sigma = P->p.sigma;
+  inf->lipschitz = P->lips[0]; inf->mu = hs[0].mu; inf->gamma = hs[0].gamma;
+  inf->records = nrec;
+  if (numeric != MUFFIN_OK) return fail(numeric, "%s", numeric_msg.c_str());
+  for (int c = 0; c < B; ++c)
+    if (!std::isfinite(theta[2 * c]) || !std::isfinite(theta[2 * c + 1])) {
+      P->have_state = P->have_sure_state = false;
+      return fail(MUFFIN_ENUMERIC, "theta of cube %d is not finite", c);
+    }
   return MUFFIN_OK;
 }
 
@@ -1048,6 +1245,133 @@ muffin_status muffin_sure_global(muffin_plan P, const float *dirty, const float 
     info->iters_done = outer * sp->iters;
     info->records = outer;
   }
+  return MUFFIN_OK;
+}
+
+muffin_status muffin_sure_global_auto(muffin_plan P, const float *dirty, const float *delta,
+                                      const double *noise_var, const muffin_sure_params *sp,
+                                      int32_t outer, int32_t check, double tol, float *x,
+                                      double *theta, muffin_sure_record *trace,
+                                      muffin_info *info) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  if (!P->p.sure) return fail(MUFFIN_ESTATE, "plan was created without the ADA-PT chains (sure=0)");
+  if (!sp || !x || !theta) return fail(MUFFIN_EINVAL, "NULL argument");
+  if (outer < 0 || sp->iters < 1 || check < 1)
+    return fail(MUFFIN_EINVAL, "outer >= 0, iters >= 1 and check >= 1 required");
+  if (!(tol >= 0) || !std::isfinite(tol)) return fail(MUFFIN_EINVAL, "tol must be finite and >= 0");
+  if (sp->iters % check != 0)
+    return fail(MUFFIN_EINVAL, "the cap iters=%d must be a multiple of check=%d", sp->iters, check);
+  const int B = P->B;
+  const size_t NL = P->NL;
+  float *x0 = nullptr;
+  CK(cudaMalloc(&x0, NL * sizeof(float)));
+  struct Guard { float *p; ~Guard() { cudaFree(p); } } guard{x0};
+  CK(cudaMemcpy(x0, x, NL * sizeof(float), cudaMemcpyDefault));
+  // theta fixed within a step: windows of `check` with no update and the
+  // derivative iterates carried, so every window end yields grad R_{0:k}
+  muffin_sure_params q = *sp;
+  q.window = check;
+  q.reset_each_window = 0;
+  q.eta_mu = 0.0;
+  q.eta_gamma = 0.0;
+  std::vector<muffin_sure_record> rec((size_t)B * 2);
+  muffin_info inf{};
+  int total = 0;
+  for (int i = 0; i < outer; ++i) {
+    if (i > 0) CK(cudaMemcpy(x, x0, NL * sizeof(float), cudaMemcpyDefault));
+    std::vector<double> prev(B, -1.0);
+    std::vector<muffin_sure_record> last(B);
+    int k = 0;
+    for (;;) {
+      q.iters = check;
+      const bool warm = k > 0;
+      muffin_status s = muffin_sure_tune(P, warm ? nullptr : dirty, warm ? nullptr : delta,
+                                         warm ? nullptr : noise_var, &q, x, theta, rec.data(),
+                                         warm ? MUFFIN_WARM : 0, &inf);
+      if (s != MUFFIN_OK) return s;
+      k += q.iters;
+      bool settled = k >= 2 * check && inf.records > 0;
+      for (int c = 0; c < B; ++c) {
+        if (inf.records > 0) last[c] = rec[(size_t)c * 2];
+        const double nrm = std::hypot(last[c].sugar_mu, last[c].sugar_gamma);
+        if (!(std::fabs(nrm - prev[c]) <= tol * nrm)) settled = false;
+        prev[c] = nrm;
+      }
+      if (settled || k >= sp->iters) break;
+    }
+    total += k;
+    for (int c = 0; c < B; ++c) {   // Eq. globalgrad
+      muffin_sure_record &r = last[c];
+      r.k = k;
+      theta[2 * c] = std::fmax(std::fma(-sp->eta_mu, r.sugar_mu, r.mu), sp->theta_min);
+      theta[2 * c + 1] = std::fmax(std::fma(-sp->eta_gamma, r.sugar_gamma, r.gamma), sp->theta_min);
+      if (trace) trace[(size_t)c * outer + i] = r;
+    }
+  }
+  if (info) {
+    *info = inf;
+    info->iters_done = total;
+    info->records = outer;
+    info->mu = theta[0];
+    info->gamma = theta[1];
+  }
+  return MUFFIN_OK;
+}
+
+// ---------------------------------------------------------------- monitor
+muffin_status muffin_plan_set_monitor(muffin_plan P, const muffin_monitor_params *mp) {
+  if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
+  if (!mp) {
+    P->mon_p = muffin_monitor_params{};
+    return MUFFIN_OK;
+  }
+  if (mp->every < 0 || !(mp->rel_tol >= 0) || !std::isfinite(mp->rel_tol))
+    return fail(MUFFIN_EINVAL, "every >= 0 and a finite rel_tol >= 0 required");
+  if (mp->objective && !P->ydev) {
+    float *y = nullptr;
+    CK(P->alloc(&y, P->NL));
+    P->ydev = y;
+    P->have_y = false;
+  }
+  P->mon_p = *mp;
+  return MUFFIN_OK;
+}
+
+muffin_status muffin_plan_monitor_read(muffin_plan P, muffin_monitor_record *out,
+                                       int32_t capacity, int32_t *count) {
+  if (!P || !count) return fail(MUFFIN_EINVAL, "NULL argument");
+  *count = (int32_t)P->mon_rec.size();
+  for (int32_t i = 0; i < *count && i < capacity && out; ++i) out[i] = P->mon_rec[i];
+  return MUFFIN_OK;
+}
+
+muffin_status muffin_objective(muffin_plan P, const float *dirty, const float *x,
+                               const double *mu, const double *gamma, double *f) {
+  if (!P || !dirty || !x || !mu || !gamma || !f) return fail(MUFFIN_EINVAL, "NULL argument");
+  for (int c = 0; c < P->B; ++c)
+    if (!(mu[c] >= 0) || !(gamma[c] >= 0))
+      return fail(MUFFIN_EINVAL, "mu and gamma must be >= 0");
+  muffin_status s = pi::enter(P);
+  if (s == MUFFIN_OK) s = fetch(P, dirty, P->stage_a, P->NL);
+  if (s == MUFFIN_OK) s = fetch(P, x, P->stage_b, P->NL);
+  if (s != MUFFIN_OK) return s;
+  MonOut r;
+  const std::vector<double> m(mu, mu + P->B), g(gamma, gamma + P->B);
+  s = monitor_eval(P, P->stage_b, nullptr, P->stage_a, m, g, r);
+  if (s != MUFFIN_OK) return s;
+  // +inf outside the positive orthant (the indicator of Eq. probopt)
+  std::vector<int> neg(P->B, 0);
+  if (P->p.positivity) {
+    std::vector<float> h(P->NL);
+    CK(cudaMemcpyAsync(h.data(), P->stage_b, P->NL * sizeof(float), cudaMemcpyDeviceToHost, P->ws));
+    CK(cudaStreamSynchronize(P->ws));
+    for (int c = 0; c < P->B; ++c)
+      for (size_t i = (size_t)c * P->NLc; i < (size_t)(c + 1) * P->NLc && !neg[c]; ++i)
+        if (h[i] < 0.f) neg[c] = 1;
+  }
+  s = pi::leave(P, true);
+  if (s != MUFFIN_OK) return s;
+  for (int c = 0; c < P->B; ++c) f[c] = neg[c] ? INFINITY : r.obj[c];
   return MUFFIN_OK;
 }
 

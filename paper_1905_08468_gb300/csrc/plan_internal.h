@@ -67,6 +67,12 @@ struct muffin_plan_s {
   float *b = nullptr, *bbar = nullptr, *htd = nullptr;
   float *stage_a = nullptr, *stage_b = nullptr;
   float *op_in = nullptr, *op_out = nullptr, *op_b = nullptr;
+  double *mon = nullptr;              // monitor reduction scratch and outputs
+  float *ydev = nullptr;              // dirty cube kept for the monitor's objective
+  bool have_y = false;
+  std::vector<float> beta_h;          // band weights (host copy)
+  muffin_monitor_params mon_p{};      // convergence monitor settings
+  std::vector<muffin_monitor_record> mon_rec;   // records of the last call
 
   muffin::Prof prof;
   bool profiling = false;

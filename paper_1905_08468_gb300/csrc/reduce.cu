@@ -206,8 +206,10 @@ __global__ void k_theta_update(ThetaUpdateArgs a) {
     rec[4] = sug_ga;
     rec[5] = psure;
     rec[6] = sc->tau;
-    const double nmu = fmax(mu - a.eta_mu * sug_mu, a.theta_min);
-    const double nga = fmax(gamma - a.eta_gamma * sug_ga, a.theta_min);
+    // explicit fused products: the host-side descent (muffin_sure_global_auto)
+    // applies the same rounding
+    const double nmu = fmax(fma(-a.eta_mu, sug_mu, mu), a.theta_min);
+    const double nga = fmax(fma(-a.eta_gamma, sug_ga, gamma), a.theta_min);
     sc->mu = nmu;
     sc->gamma = nga;
     sc->tau = a.safety / (0.5 * cc[1] + sc->sigma * (a.K * nmu * nmu * cc[2] + nga * nga * cc[3]));

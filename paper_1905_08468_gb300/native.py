@@ -23,7 +23,17 @@ class Params(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("iters_done", c_int32), ("tau", c_double), ("sigma", c_double),
                 ("lipschitz", c_double), ("mu", c_double), ("gamma", c_double),
-                ("records", c_int32)]
+                ("records", c_int32), ("checks", c_int32), ("stopped_early", c_int32),
+                ("rel_change", c_double), ("objective", c_double)]
+
+
+class MonitorParams(ctypes.Structure):
+    _fields_ = [("every", c_int32), ("objective", c_int32), ("rel_tol", c_double)]
+
+
+class MonitorRecord(ctypes.Structure):
+    _fields_ = [("k", c_int32), ("cube", c_int32), ("rel_change", c_double),
+                ("objective", c_double), ("nonfinite", ctypes.c_int64)]
 
 
 class SureParams(ctypes.Structure):
@@ -88,6 +98,15 @@ SIGNATURES = {
     "muffin_sure_global": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                                      c_void_p, ctypes.POINTER(c_double),
                                      ctypes.POINTER(SureRecord), ctypes.POINTER(Info)]),
+    "muffin_sure_global_auto": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                          c_int32, c_int32, c_double, c_void_p,
+                                          ctypes.POINTER(c_double), ctypes.POINTER(SureRecord),
+                                          ctypes.POINTER(Info)]),
+    "muffin_plan_set_monitor": (c_int32, [c_void_p, ctypes.POINTER(MonitorParams)]),
+    "muffin_plan_monitor_read": (c_int32, [c_void_p, ctypes.POINTER(MonitorRecord), c_int32,
+                                           ctypes.POINTER(c_int32)]),
+    "muffin_objective": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
+                                   ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
     "muffin_plan_set_weights": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "muffin_plan_weights_from_x0": (c_int32, [c_void_p, c_void_p, c_double, c_double,
                                               c_void_p, c_void_p]),

@@ -100,3 +100,45 @@ def test_iuwt_weights_are_below_parseval():
     const = np.full((2, 16, 16), 3.0)
     _, bc = ow.weights_from_x0(const, J=3, eps_alpha=0.0, eps_beta=0.0, dictionary="iuwt")
     np.testing.assert_allclose(bc, 1.0 / (3.0 * 16), rtol=1e-12)
+
+
+def test_auto_n_c_with_zero_tolerance_is_the_fixed_descent():
+    """tol = 0 never settles: n_c = the cap, as the fixed-n_c descent."""
+    c = make_cube(16, 3, 5, 1, 300, seed=61)
+    prob = om.make_problem(c.dirty, c.psf, n_wavelets=2, J=2)
+    eps = fdmc_eps(c.noise_var)
+    args = (prob, c.delta, eps, c.noise_var, (0.03, 0.02), 2)
+    x, th, recs = ow.global_descent(*args, n_c=12, eta=(1e-4, 1e-4))
+    xa, tha, reca = ow.global_descent_auto(*args, check=4, tol=0.0, n_cap=12, eta=(1e-4, 1e-4))
+    assert [r["k"] for r in reca] == [12, 12]
+    assert np.allclose(xa, x, rtol=0, atol=1e-13 * np.max(np.abs(x)))
+    assert np.allclose(tha, th, rtol=1e-13, atol=0)
+    for a, b in zip(reca, recs):
+        assert np.allclose(a["sugar"], b["sugar"], rtol=1e-10, atol=0)
+
+
+def test_auto_n_c_stops_where_the_norm_settles():
+    """The chosen n_c is the first k >= 2 check where ||SUGAR_{0:k}|| moved by
+    at most tol of itself since k - check, read off one long run of the
+    derivative chains with theta fixed (Algorithm 5 with eta = 0 and the
+    derivatives carried); the step is Eq. globalgrad with that SUGAR."""
+    c = make_cube(16, 3, 5, 1, 300, seed=62)
+    prob = om.make_problem(c.dirty, c.psf, n_wavelets=2, J=2)
+    eps = fdmc_eps(c.noise_var)
+    th0, check, cap, eta = np.array([0.03, 0.02]), 3, 60, np.array([1e-4, 1e-4])
+    long = osu.ada_pt(prob, c.delta, eps, c.noise_var, th0, cap, Delta=check,
+                        eta=(0.0, 0.0), reset=False)
+    norms = [np.linalg.norm(t["sugar"]) for t in long.trace]
+    rel = [abs(norms[i] - norms[i - 1]) / norms[i] for i in range(1, len(norms))]
+    tol = float(np.sort(rel)[len(rel) // 2])           # fires somewhere inside
+    want = next(check * (i + 1) for i in range(1, len(norms)) if rel[i - 1] <= tol)
+    assert want < cap
+    x, th, recs = ow.global_descent_auto(prob, c.delta, eps, c.noise_var, th0, 1, check=check,
+                                         tol=tol, n_cap=cap, eta=eta)
+    assert recs[0]["k"] == want
+    g = long.trace[want // check - 1]["sugar"]
+    assert np.allclose(recs[0]["sugar"], g, rtol=1e-12, atol=0)
+    assert np.allclose(th, np.maximum(th0 - eta * g, 1e-8), rtol=1e-14, atol=0)
+    ref = osu.ada_pt(prob, c.delta, eps, c.noise_var, th0, want, Delta=check,
+                       eta=(0.0, 0.0), reset=False)
+    assert np.allclose(x, ref.x, rtol=0, atol=1e-13 * np.max(np.abs(ref.x)))
