@@ -172,7 +172,7 @@ cudaError_t theta_update(const ThetaUpdateArgs &a, cudaStream_t st);
 // ------------------------------------------------------------ monitor (monitor.cu)
 // Doubles of scratch the monitor reductions need for L bands: partials
 // [L][16][3], then the outputs state [L][3], residual [L], |W_s x| [L],
-// alpha |W_lambda x| [L].
+// alpha |W_lambda x| [L], input scan [L][3].
 size_t monitor_scratch_doubles(int L);
 // out[l][0..2] = {sum (x - xo)^2, sum xo^2 (sum x^2 when xo is NULL), number
 // of NaN/Inf entries of x} over the N values of band l (FP64)

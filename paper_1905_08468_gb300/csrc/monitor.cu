@@ -124,7 +124,7 @@ int bpb_for(size_t per_band) {
 
 }  // namespace
 
-size_t monitor_scratch_doubles(int L) { return (size_t)L * (3 * kMaxBpb + 8) + 64; }
+size_t monitor_scratch_doubles(int L) { return (size_t)L * (3 * kMaxBpb + 12) + 64; }
 
 cudaError_t mon_state(const float *x, const float *xo, int L, size_t N, double *scratch,
                       double *out, cudaStream_t st) {

@@ -88,17 +88,6 @@ extern "C" MUFFIN_API muffin_status muffin_op_analysis_noalloc(
     return noalloc_fail(MUFFIN_EINVAL, "nbands >= 1 and 1 <= n_wavelets <= 8 required");
   if (levels < 0 || levels > 15 || (1 << levels) > n)
     return noalloc_fail(MUFFIN_EINVAL, "levels must satisfy 2^levels <= n");
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    cudaGetLastError();
-    return noalloc_fail(MUFFIN_ECUDA, "no usable current CUDA device");
-  }
-  if (!usable_on(x, dev) || !usable_on(u, dev))
-    return noalloc_fail(MUFFIN_EINVAL,
-                        "x and u must be device (or managed) arrays of the current device");
-  const size_t xbytes = (size_t)nbands * n * n * sizeof(float);
-  if (overlap(x, xbytes, u, xbytes * n_wavelets))
-    return noalloc_fail(MUFFIN_EINVAL, "x and u must not overlap");
   // LL scratch of levels 1..J-1: [L][K][n>>j][n>>j]
   WaveArgs w{};
   size_t need = 0;
@@ -111,6 +100,17 @@ extern "C" MUFFIN_API muffin_status muffin_op_analysis_noalloc(
     return noalloc_fail(MUFFIN_EINVAL,
                         "cube too large for the fixed scratch (needs nbands * n_wavelets * "
                         "sum_{1<=j<levels} (n>>j)^2 <= 4194304 floats)");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return noalloc_fail(MUFFIN_ECUDA, "no usable current CUDA device");
+  }
+  if (!usable_on(x, dev) || !usable_on(u, dev))
+    return noalloc_fail(MUFFIN_EINVAL,
+                        "x and u must be device (or managed) arrays of the current device");
+  const size_t xbytes = (size_t)nbands * n * n * sizeof(float);
+  if (overlap(x, xbytes, u, xbytes * n_wavelets))
+    return noalloc_fail(MUFFIN_EINVAL, "x and u must not overlap");
   {
     // once per device (and again if its context was reset), with that device
     // current: the scratch's device address (the host-side name is only a

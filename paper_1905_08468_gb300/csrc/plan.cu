@@ -139,6 +139,20 @@ muffin_status store(muffin_plan P, const float *src, float *dst, size_t count) {
   return MUFFIN_OK;
 }
 
+// NaN/Inf scan of an input already copied to the device (nimg images of N
+// pixels); synchronises the work stream
+muffin_status scan_input(muffin_plan P, const float *d, int nimg, const char *what) {
+  double *o = P->mon + 54 * (size_t)P->Lt;
+  CK(mon_state(d, nullptr, nimg, P->N, P->mon, o, P->ws));
+  std::vector<double> h(3 * (size_t)nimg);
+  CK(cudaMemcpyAsync(h.data(), o, h.size() * sizeof(double), cudaMemcpyDeviceToHost, P->ws));
+  CK(cudaStreamSynchronize(P->ws));
+  double bad = 0;
+  for (int l = 0; l < nimg; ++l) bad += h[3 * (size_t)l + 2];
+  if (bad > 0) return fail(MUFFIN_ENUMERIC, "%s has %.0f NaN/Inf entries", what, bad);
+  return MUFFIN_OK;
+}
+
 // H^T y (unnormalised, FP64) for `nimg` bands of y already on the device
 muffin_status adjoint_fp64(muffin_plan P, const float *y_dev, const double2 *hh,
                            int nimg, double2 *w, double2 *tmp) {
@@ -588,6 +602,7 @@ muffin_status load_dirty(muffin_plan P, int b0, int b1, const float *dirty) {
   const size_t cnt = (size_t)(b1 - b0) * P->NLc;
   const size_t off = (size_t)b0 * P->NLc;
   muffin_status s = fetch(P, dirty, P->stage_a + off, cnt);
+  if (s == MUFFIN_OK) s = scan_input(P, P->stage_a + off, (b1 - b0) * P->L, "the dirty cube");
   if (s != MUFFIN_OK) return s;
   s = adjoint_fp64(P, P->stage_a + off, P->hhat + off, (b1 - b0) * P->L, P->w64a + off,
                    P->w64b + off);
@@ -834,6 +849,7 @@ muffin_status muffin_solve_batch(muffin_plan P, const float *dirty, float *x,
   }
   if (!warm) {
     s = fetch(P, x, P->stage_b, P->NL);
+    if (s == MUFFIN_OK) s = scan_input(P, P->stage_b, P->Lt, "X0");
     if (s == MUFFIN_OK) s = pi::reset_cubes(P, 0, 0, P->B, P->stage_b);
     if (s != MUFFIN_OK) return s;
   }
@@ -921,6 +937,7 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
     if (s != MUFFIN_OK) return s;
     P->have_b = true;
     s = fetch(P, delta, P->stage_b, NL);
+    if (s == MUFFIN_OK) s = scan_input(P, P->stage_b, P->Lt, "delta");
     if (s != MUFFIN_OK) return s;
     s = adjoint_fp64(P, P->stage_b, P->hhat, P->Lt, P->w64b, P->w64a);
     if (s != MUFFIN_OK) return s;
@@ -945,6 +962,7 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
     s = upload_cube_const(P);
     if (s != MUFFIN_OK) return s;
     s = fetch(P, x, P->stage_b, NL);
+    if (s == MUFFIN_OK) s = scan_input(P, P->stage_b, P->Lt, "X0");
     if (s == MUFFIN_OK) s = pi::reset_cubes(P, 0, 0, B, P->stage_b);
     if (s == MUFFIN_OK) s = pi::reset_cubes(P, 1, 0, B, P->stage_b);
     if (s != MUFFIN_OK) return s;

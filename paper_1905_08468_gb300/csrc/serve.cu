@@ -17,6 +17,8 @@
 // result is the same alone and in the mix.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -276,6 +278,9 @@ muffin_status muffin_serve_submit(muffin_server S, int32_t n, int32_t nbands,
       std::memcpy(dst, src, cnt * sizeof(float));
     }
   }
+  for (size_t i = 0; i < cnt; ++i)
+    if (!std::isfinite(r.dirty[i]) || !std::isfinite(r.psf[i]))
+      return fail(MUFFIN_ENUMERIC, "request input has a NaN/Inf entry (index %zu)", i);
   *ticket = r.id;
   S->queue.push_back(r.id);
   S->reqs.emplace(r.id, std::move(r));

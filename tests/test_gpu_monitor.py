@@ -139,6 +139,25 @@ def test_nan_in_dirty_cube_is_reported_and_plan_stays_usable():
     assert torch.equal(x1, y1) and torch.equal(x2, y2) and th2 == th3
 
 
+def test_overflow_inside_the_iteration_is_caught_by_the_scan():
+    """Finite inputs whose H^T y overflows FP32: without the positivity
+    projection (which would map the non-finite m to 0) X turns non-finite and
+    the end-of-call scan returns MUFFIN_ENUMERIC."""
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    from paper_1905_08468_gb300.native import MuffinError
+    n, L = 16, 2
+    psf = np.zeros((L, n, n), np.float32)
+    psf[:, 0, 0] = 1.0
+    psf[:, 0, 1] = 1.0              # |h_hat(0)| = 2: H^T y = 2 y = 6e38 > FP32 max
+    dirty = np.full((L, n, n), 3e38, np.float32)
+    x = dev(np.zeros((L, n, n)), torch)
+    with pkg.Plan(n, L, psf, positivity=False, n_wavelets=2, levels=1) as plan:
+        with pytest.raises(MuffinError) as e:
+            plan.solve(dev(dirty, torch), x, 3, 1e-2, 1e-2)
+        assert e.value.status == 5 and "after 3 iterations" in str(e.value)
+
+
 def test_monitor_in_sure_tune_checks_at_window_ends():
     torch = cuda()
     import paper_1905_08468_gb300 as pkg

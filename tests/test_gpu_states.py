@@ -8,12 +8,14 @@ of both.  Each is compared with the oracle's, element by element, as a
 relative L2 error over the whole array:
 
 * primal iterates X, X_bar and their U, V, T: <= 1e-5 (the cube tolerance);
-* derivative iterates: <= DERIV_TOL = 1e-5 as well.  They are linear
-  recursions driven by the primal's masks U(m), Pi(p), Pi(v~) (Sec. 3.2);
-  FP32 and FP64 could decide a mask differently at a near-tie, which would
-  move one coefficient of a derivative by its whole value, but no such flip
-  shows in these runs (measured on a GB300: every derivative iterate within
-  7e-7 of the oracle's at 32^2 x 8).
+* derivative iterates: <= DERIV_TOL = 1e-4.  They are linear recursions
+  driven by the primal's masks U(m), Pi(p), Pi(v~) (Sec. 3.2); FP32 and
+  FP64 decide a mask differently at a near-tie, which moves the coefficients
+  it gates by their whole value.  Measured on a GB300: within 2e-6 of the
+  oracle's at 32^2 x 8 and 64^2 x 64; at 1024^2 x 2 (2 M pixels, 16 M
+  coefficients per chain) three derivative arrays show such flips at
+  6e-5.  Where an error exceeds the cube tolerance, the differing entries
+  must be few (isolated mask flips, not a wrong term).
 
 The runs are chosen so that theta stays well above theta_min in both
 components (the clamp would make the theta comparison vacuous), and the
@@ -29,7 +31,7 @@ from tests.gpu_util import cuda, dev, rel_l2
 pytestmark = pytest.mark.gpu
 
 PRIMAL_TOL = 1e-5
-DERIV_TOL = 1e-5
+DERIV_TOL = 1e-4
 THETA_TOL = 1e-3
 THETA_MIN = 1e-8
 
@@ -63,6 +65,14 @@ def compare_states(states, st, label):
     for name, e in errs.items():
         tol = PRIMAL_TOL if name.split(".")[0] in ("X", "X_bar") else DERIV_TOL
         assert e <= tol, (name, e)
+        if e > PRIMAL_TOL:
+            i = [k for k, v in NAMES.items() if v == name.split(".")[0]][0]
+            g, ch = STATE_MAP[i]
+            ref = getattr(states[i], name.split(".")[1])
+            d = np.abs(st[name.split(".")[1]][g, ch] - ref)
+            big = int(np.sum(d > 1e-3 * np.max(np.abs(ref))))
+            print(f"  {name}: {big} of {d.size} entries differ by > 1e-3 max|ref|")
+            assert big <= max(8, d.size // 100000), (name, big)
     # the derivative iterates are live (not just reset) at the end of the run
     for i in (2, 3, 4, 5):
         assert np.linalg.norm(states[i].x) > 0, NAMES[i]
