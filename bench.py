@@ -33,8 +33,12 @@ if ROOT not in sys.path:
 METRIC = "voxel-iters/s (px x bands x iters) at 1024^2 x 64, ADA-PT'ed MUFFIN"
 UNIT = "voxel-iters/s"
 THETA0 = (1e-2, 1e-2)
-ETA = (1e-12, 1e-12)
-CROP = dict(n=256, L=8, iters=3)      # oracle sample: top-left 256^2 x 8 bands
+# gradient steps that move theta by about 1 % (mu) and 2 % (gamma) per window
+# at 1024^2 x 64 (SUGAR there is ~2e4 for mu and ~3e3 for gamma at the start)
+ETA = (5e-9, 5e-8)
+# oracle sample: the top-left 128^2 pixels of all 64 bands (the per-pixel DCT
+# step keeps its share of the work), two ADA-PT iterations
+CROP = dict(n=128, L=64, iters=2)
 
 # DRAM bytes (read + write) per chain-voxel of a kernel, from a committed
 # ncu capture (profiles/), valid only while the kernel's source file is the
@@ -133,30 +137,66 @@ def parse_clocks(text: str) -> dict:
 
 
 # ------------------------------------------------------------------ oracle leg
+# The oracle runs in a subprocess of its own (no CUDA, its own BLAS settings)
+# on a crop saved once by the parent; `parallel` selects the band-parallel
+# form (Sec. 2.3 split) on all cores.
 ORACLE_SAMPLE = r"""
-import json, sys, time
+import json, os, sys, time
 sys.path.insert(0, {root!r})
 import numpy as np
-from synth import make_workload, fdmc_eps
-from oracle import muffin as om, sure as osure
-c = make_workload({name!r})
-n, L, iters = {n}, {L}, {iters}
-sl = (slice(0, L), slice(0, n), slice(0, n))
-prob = om.make_problem(c.dirty[sl], c.psf[sl])
-nv = c.noise_var[:L]
-t0 = time.perf_counter()
-osure.ada_pt(prob, c.delta[sl], fdmc_eps(nv), nv, {theta0!r}, iters, Delta=10, eta=(0.0, 0.0))
-dt = time.perf_counter() - t0
-print(json.dumps(dict(seconds=dt, voxels=n * n * L, iters=iters)))
+from synth import fdmc_eps
+from oracle import muffin as om, sure as osure, parallel as opar
+if __name__ == "__main__":
+    z = np.load({crop!r})
+    iters = {iters}
+    prob = om.make_problem(z["dirty"], z["psf"])
+    nv = z["noise_var"]
+    eps = fdmc_eps(nv)
+    workers = opar.default_workers() if {parallel!r} else 1
+    t0 = time.perf_counter()
+    if {parallel!r}:
+        opar.ada_pt(prob, z["delta"], eps, nv, {theta0!r}, iters, Delta=10, eta=(0.0, 0.0),
+                    workers=workers)
+    else:
+        osure.ada_pt(prob, z["delta"], eps, nv, {theta0!r}, iters, Delta=10, eta=(0.0, 0.0))
+    dt = time.perf_counter() - t0
+    print(json.dumps(dict(seconds=dt, voxels=int(z["dirty"].size), iters=iters, cores=workers)))
 """
 
+_CROP_FILE = None
 
-def oracle_sample(name: str) -> dict:
+
+def crop_file(name: str, cube=None) -> str:
+    """The oracle's sample: the top-left CROP['n']^2 pixels of the first
+    CROP['L'] bands of the workload, saved once per process."""
+    global _CROP_FILE
+    if _CROP_FILE is None:
+        import numpy as np
+        if cube is None:
+            from synth import make_workload
+            cube = make_workload(name)
+        n, L = CROP["n"], CROP["L"]
+        sl = (slice(0, L), slice(0, n), slice(0, n))
+        fd, path = tempfile.mkstemp(suffix=".npz")
+        os.close(fd)
+        np.savez(path, dirty=cube.dirty[sl], psf=cube.psf[sl], delta=cube.delta[sl],
+                 noise_var=cube.noise_var[:L])
+        _CROP_FILE = path
+    return _CROP_FILE
+
+
+def oracle_sample(name: str, parallel: bool, cube=None) -> dict:
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
                MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
-    code = ORACLE_SAMPLE.format(root=ROOT, name=name, theta0=THETA0, **CROP)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
-                       env=env, timeout=900)
+    code = ORACLE_SAMPLE.format(root=ROOT, crop=crop_file(name, cube), theta0=THETA0,
+                                parallel=parallel, iters=CROP["iters"])
+    with tempfile.NamedTemporaryFile("w", suffix=".py", delete=False) as f:
+        f.write(code)       # a file, so that spawned workers can re-import it
+    try:
+        r = subprocess.run([sys.executable, f.name], capture_output=True, text=True,
+                           env=env, timeout=900)
+    finally:
+        os.unlink(f.name)
     if r.returncode != 0:
         raise RuntimeError(f"oracle sample failed: {r.stderr[-2000:]}")
     d = json.loads(r.stdout.strip().splitlines()[-1])
@@ -165,10 +205,12 @@ def oracle_sample(name: str) -> dict:
 
 
 def cpu_baseline_obj(d: dict) -> dict:
-    return {"value": d["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 NumPy oracle, {d['iters']} ADA-PT iteration(s) (6 chains) "
-                       f"on the top-left {CROP['n']}x{CROP['n']} x {CROP['L']}-band crop "
-                       f"of the 1024^2 x 64 cube, 1 thread, {d['seconds']:.1f} s")}
+    form = (f"band-parallel (Sec. 2.3 split), {d['cores']} worker processes"
+            if d["cores"] > 1 else "1 thread")
+    return {"value": d["value"], "unit": UNIT, "cores": d["cores"], "kind": "oracle",
+            "sample": (f"FP64 NumPy oracle, {d['iters']} ADA-PT iterations (6 chains) "
+                       f"on the top-left {CROP['n']}x{CROP['n']} px of all {CROP['L']} bands "
+                       f"of the 1024^2 x 64 cube, {form}, {d['seconds']:.1f} s")}
 
 
 def run_reference(args) -> None:
@@ -176,10 +218,10 @@ def run_reference(args) -> None:
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(args.workload)
+        oracle_sample(args.workload, parallel=True)
     vals, secs = [], 0.0
     for _ in range(args.steps):
-        d = oracle_sample(args.workload)
+        d = oracle_sample(args.workload, parallel=True)
         vals.append(d["value"])
         secs += d["seconds"]
     v = statistics.mean(vals)
@@ -199,15 +241,17 @@ def run_reference(args) -> None:
 def workload_config(args, oracle=False) -> dict:
     from synth import WORKLOADS
     n, L, n_src, n_blob, n_uv, seed = WORKLOADS[args.workload]
-    cfg = {"workload": f"ADA-PT'ed MUFFIN {n}x{n} px x {L} bands",
+    plain = getattr(args, "plain", False)
+    cfg = {"workload": (f"plain MUFFIN {n}x{n} px x {L} bands, mu = gamma = {args.mu:g}" if plain
+                        else f"ADA-PT'ed MUFFIN {n}x{n} px x {L} bands"),
            "n": n, "bands": L, "sources": n_src, "blobs": n_blob, "uv_points": n_uv,
            "snr_db": 20, "seed": seed, "iters_per_step": args.iters,
            "window": args.window,
            "wavelets": ("IUWT (starlet), 3 scales" if getattr(args, "dictionary", "daubechies") == "iuwt"
                         else "db1..db8, 3 levels"),
-           "spectral": "DCT-II, 3xTF32 products on the tensor cores (tcgen05 for 64 bands, else mma.sync)", "chains": 6,
-           "theta0": list(THETA0), "eta": list(ETA),
-           "l2": "inputs larger than L2 (state ~26 GB per cube)"}
+           "spectral": "DCT-II, 3xTF32 products on the tensor cores (tcgen05 for 64 bands, else mma.sync)", "chains": 1 if plain else 6,
+           "theta0": None if plain else list(THETA0), "eta": None if plain else list(ETA),
+           "l2": "inputs larger than L2 (state ~26 GB per cube at 1024^2 x 64 ADA-PT)"}
     if oracle:
         cfg["oracle_sample"] = dict(CROP)
     return cfg
@@ -437,6 +481,13 @@ def main() -> None:
                     help="arrival-stream seed (request i draws its cube from seed 4000 + i)")
     ap.add_argument("--serve-rate", type=float, default=4.0,
                     help="mean arrivals per second (0: all requests at once)")
+    ap.add_argument("--plain", action="store_true",
+                    help="plain MUFFIN (Algorithm 2, fixed mu = gamma = --mu) instead of ADA-PT")
+    ap.add_argument("--mu", type=float, default=1e-2)
+    ap.add_argument("--no-cufft", action="store_true",
+                    help="skip the cuFFT timing reference of the gradient")
+    ap.add_argument("--cufft-reference", action="store_true",
+                    help="cuFFT timing reference of the gradient at 256^2 x 32 and 1024^2 x 64")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -446,12 +497,120 @@ def main() -> None:
     if args.serve:
         run_serve(args)
         return
+    if args.cufft_reference:
+        run_cufft_reference(args)
+        return
     if args.convergence:
         if args.workload == "c3_1024x1024x64":
             args.workload = "c2_256x256x32"
         run_convergence(args)
         return
 
+    run_gpu(args)
+
+
+# Algorithmic bytes per chain-voxel that the path must move (the 86 B / 490 B
+# floor of one plain chain / the six ADA-PT chains, split by kernel) against
+# each kernel's own design bytes (which add the scratch round trips of this
+# multi-pass schedule: LL approximations between levels, FFT spectra, the
+# gradient image).  achieved = floor-attributable bytes / duration.
+ATTRIBUTABLE = {
+    # x~, x read; level-1 U details read and written (the LL_1 write is scratch)
+    "ana_level1_dual": (56.0, 64.0),
+    # level-1 U details, x, t read; x~ written (LL_1 read and the gradient are scratch)
+    "syn_level1_prox": (36.0, 48.0),
+    # x~, x, v read; v, t written
+    "spectral_dual": (20.0, 20.0),
+}
+FLOOR_BYTES = {"adapt": 490.0, "plain": 86.0}
+
+
+def attributable_bytes(name: str, design_bytes: float) -> float:
+    a = ATTRIBUTABLE.get(name)
+    return design_bytes * a[0] / a[1] if a else design_bytes
+
+
+def cufft_gradient_ms(torch, psf, x, b, reps=10):
+    """The gradient H^T H x - b of every image of x ([nimg, n, n], images
+    cycling over the PSFs' bands) with cuFFT (torch.fft) and elementwise
+    torch kernels: a timing reference for the library's own FFT kernels."""
+    nimg, n = x.shape[0], x.shape[-1]
+    L = psf.shape[0]
+    k = (torch.fft.rfft2(psf.double()).abs() ** 2).float()
+    k = k.repeat((nimg + L - 1) // L, 1, 1)[:nimg].contiguous()
+    bb = b.repeat((nimg + L - 1) // L, 1, 1)[:nimg].contiguous()
+
+    def once():
+        return torch.fft.irfft2(torch.fft.rfft2(x) * k, s=(n, n)) - bb
+
+    for _ in range(3):
+        once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def muffin_gradient_ms(stats, nimg_bytes):
+    """Average duration of one gradient launch (the three FFT passes) from a
+    profiled step: the entries of the per-iteration launches (the most
+    frequent of each name)."""
+    tot = 0.0
+    for name in ("grad_rows_fwd", "grad_cols", "grad_rows_inv"):
+        ent = [s for s in stats if s["name"] == name]
+        if not ent:
+            return None
+        e = max(ent, key=lambda s: s["launches"])
+        tot += e["total_ms"] / e["launches"]
+    return tot
+
+
+def run_cufft_reference(args) -> None:
+    """cuFFT timing reference for the gradient at the 256^2 x 32 (plain, one
+    chain) and 1024^2 x 64 (ADA-PT groups of three chains) shapes."""
+    import numpy as np
+    import torch
+    from synth import make_workload
+    import paper_1905_08468_gb300 as pkg
+    torch.cuda.set_device(0)
+    rows = []
+    for wl, chains in (("c2_256x256x32", 1), ("c3_1024x1024x64", 3)):
+        c = make_workload(wl)
+        dev = torch.device("cuda")
+        psf = torch.from_numpy(c.psf).to(dev)
+        dirty = torch.from_numpy(c.dirty).to(dev)
+        with pkg.Plan(c.n, c.L, psf, sure=chains == 3) as plan:
+            x = torch.zeros_like(dirty)
+            plan.profile(True)
+            if chains == 3:
+                plan.sure_tune(dirty, torch.from_numpy(c.delta).to(dev), c.noise_var, x,
+                               THETA0, 20, window=10, eta=(0.0, 0.0),
+                               eps=float(np.sqrt(np.mean(c.noise_var))) * 0.1)
+            else:
+                plan.solve(dirty, x, 20, 1e-2, 1e-2)
+            stats = plan.profile_stats()
+            plan.profile(False)
+        ours = muffin_gradient_ms(stats, None)
+        xs = torch.rand((chains * c.L, c.n, c.n), device=dev)
+        b = torch.rand((c.L, c.n, c.n), device=dev)
+        ref = cufft_gradient_ms(torch, psf, xs, b)
+        rows.append({"workload": wl, "images": chains * c.L, "n": c.n,
+                     "muffin_ms": ours, "cufft_ms": ref,
+                     "speedup_vs_cufft": ref / ours if ours else None})
+        del psf, dirty, x, xs, b
+        torch.cuda.empty_cache()
+    out = {"metric": "gradient H^T(Hx - y) per launch: library FFT kernels vs cuFFT (torch.fft)",
+           "value": rows[-1]["speedup_vs_cufft"], "unit": "x (cuFFT time / library time)",
+           "n_gpus": 1, "steps": 10, "warmup": 3, "higher_is_better": True,
+           "data": "synthetic", "dtype": "f32", "rows": rows}
+    print(json.dumps(out), flush=True)
+
+
+def run_gpu(args) -> None:
     import numpy as np
     import torch
     from synth import fdmc_eps, make_workload
@@ -461,14 +620,14 @@ def main() -> None:
     torch.cuda.set_device(local_rank)
     dist_init("nccl")
     dev = torch.device("cuda", local_rank)
+    mode = "plain" if args.plain else "adapt"
     c = make_workload(args.workload)
-    eps = fdmc_eps(c.noise_var)
     vox = c.voxels
     psf = torch.from_numpy(c.psf).to(dev)
     dirty = torch.from_numpy(c.dirty).to(dev)
-    delta = torch.from_numpy(c.delta).to(dev)
+    delta = torch.from_numpy(c.delta).to(dev) if mode == "adapt" else None
     x = torch.zeros_like(dirty)
-    plan = pkg.Plan(c.n, c.L, psf, sure=True, dictionary=args.dictionary)
+    plan = pkg.Plan(c.n, c.L, psf, sure=mode == "adapt", dictionary=args.dictionary)
     del psf
     tuning = None
     if args.tuning:
@@ -481,18 +640,24 @@ def main() -> None:
                   "spectral_tcgen05": ti.spectral_tcgen05,
                   "candidates": ti.candidates, "iter_ms_default": ti.ms_default,
                   "iter_ms_tuned": ti.ms_best}
-    kw = dict(window=args.window, eta=ETA, eps=eps)
+    if mode == "adapt":
+        eps = fdmc_eps(c.noise_var)
+        kw = dict(window=args.window, eta=ETA, eps=eps)
 
-    def step(xb, d, dl):
-        return plan.sure_tune(d, dl, c.noise_var, xb, THETA0, args.iters, **kw)
+        def step(xb, d, dl):
+            th, _, _ = plan.sure_tune(d, dl, c.noise_var, xb, THETA0, args.iters, **kw)
+            return th
+    else:
+        def step(xb, d, dl):
+            plan.solve(d, xb, args.iters, args.mu, args.mu)
+            return (args.mu, args.mu)
 
     for _ in range(args.warmup):
         x.zero_()
         step(x, dirty, delta)
     torch.cuda.synchronize()
 
-    # ---- device-resident timed region
-    plan.profile(True)
+    # ---- device-resident timed region (captured graphs, no per-launch events)
     sampler = ClockSampler(local_rank) if rank == 0 else None
     barrier()
     torch.cuda.synchronize()
@@ -500,40 +665,64 @@ def main() -> None:
     ev0.record()
     for _ in range(args.steps):
         x.zero_()
-        theta, trace, info = step(x, dirty, delta)
+        theta = step(x, dirty, delta)
     ev1.record()
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop() if sampler else None
     ms = ev0.elapsed_time(ev1)
     ms = max_over_ranks(ms, dev)
-    stats = plan.profile_stats()
-    plan.profile(False)
     secs = ms / 1e3
     value = job_value(vox * args.iters * args.steps, world, secs)
-    launches = sum(s["launches"] for s in stats)
+
+    # ---- one more step with CUDA events around every launch (on the plan's
+    # stream): per-kernel durations, shares and the launch count of a step
+    plan.profile(True)
+    x.zero_()
+    torch.cuda.synchronize()
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record()
+    step(x, dirty, delta)
+    pe1.record()
+    torch.cuda.synchronize()
+    profiled_ms = pe0.elapsed_time(pe1)
+    stats = plan.profile_stats()
+    plan.profile(False)
+    launches = sum(s["launches"] for s in stats) * args.steps
     dom = max(stats, key=lambda s: s["total_ms"])
     tot_ms = sum(s["total_ms"] for s in stats)
     avg_ms = dom["total_ms"] / dom["launches"]
     peak, peak_kind = measured_peak_gbs()
-    achieved = dom["bytes_per_launch"] / (avg_ms / 1e3) / 1e9
+    attr = attributable_bytes(dom["name"], dom["bytes_per_launch"])
+    achieved = attr / (avg_ms / 1e3) / 1e9
+    chains = 3.0 if mode == "adapt" else 1.0
     roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved,
                 "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": achieved / peak,
-                "traffic": captured_traffic(dom["name"], 3.0 * vox),
-                "bytes_per_launch": dom["bytes_per_launch"],
-                "avg_launch_ms": avg_ms, "share": dom["total_ms"] / tot_ms}
+                "traffic": captured_traffic(dom["name"], chains * vox),
+                "bytes_per_launch": attr, "design_bytes_per_launch": dom["bytes_per_launch"],
+                "avg_launch_ms": avg_ms, "share": dom["total_ms"] / tot_ms,
+                "timing": "CUDA events around each launch on the plan's stream, one "
+                          "profiled step after the timed region"}
+    floor = FLOOR_BYTES[mode]
+    iteration_roofline = {"floor_bytes_per_voxel_iter": floor,
+                          "achieved_GBps": floor * value / 1e9,
+                          "frac": floor * value / 1e9 / peak}
     kernels = sorted(({"name": s["name"], "launches": s["launches"],
                        "ms": round(s["total_ms"], 3),
-                       "GBps": round(s["bytes_per_launch"] * s["launches"] /
-                                     (s["total_ms"] / 1e3) / 1e9, 1) if s["total_ms"] else None}
+                       "share": round(s["total_ms"] / tot_ms, 4),
+                       "GBps_design": round(s["bytes_per_launch"] * s["launches"] /
+                                            (s["total_ms"] / 1e3) / 1e9, 1) if s["total_ms"] else None,
+                       "GBps_attributable": round(attributable_bytes(s["name"], s["bytes_per_launch"])
+                                                  * s["launches"] / (s["total_ms"] / 1e3) / 1e9, 1)
+                       if s["total_ms"] else None}
                       for s in stats), key=lambda s: -s["ms"])
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
         hd = torch.from_numpy(c.dirty).pin_memory()
-        hdl = torch.from_numpy(c.delta).pin_memory()
+        hdl = torch.from_numpy(c.delta).pin_memory() if mode == "adapt" else None
         hx = torch.zeros(c.dirty.shape, dtype=torch.float32).pin_memory()
         barrier()
         torch.cuda.synchronize()
@@ -546,23 +735,37 @@ def main() -> None:
         es = max_over_ranks(time.perf_counter() - t0, dev)
         nbytes = c.dirty.nbytes
         e2e = {"value": job_value(vox * args.iters * args.e2e_steps, world, es),
-               "unit": UNIT, "h2d_bytes_per_step": 3 * nbytes,
+               "unit": UNIT, "h2d_bytes_per_step": (3 if mode == "adapt" else 2) * nbytes,
                "d2h_bytes_per_step": nbytes, "steps": args.e2e_steps}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_obj(oracle_sample(args.workload))
+    cufft = None
+    if mode == "adapt" and rank == 0 and not args.no_cufft:
+        ours = muffin_gradient_ms(stats, None)
+        xs = torch.rand((3 * c.L, c.n, c.n), device=dev)
+        ref = cufft_gradient_ms(torch, torch.from_numpy(c.psf).to(dev), xs, dirty)
+        cufft = {"images": 3 * c.L, "n": c.n, "muffin_gradient_ms": ours,
+                 "cufft_gradient_ms": ref, "speedup_vs_cufft": ref / ours if ours else None}
+        del xs
+
+    cpu = cpu1 = None
+    if mode == "adapt" and rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_obj(oracle_sample(args.workload, parallel=True, cube=c))
+        cpu1 = cpu_baseline_obj(oracle_sample(args.workload, parallel=False, cube=c))
 
     if rank == 0:
-        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        metric = METRIC if mode == "adapt" else \
+            f"voxel-iters/s (px x bands x iters) at {c.n}^2 x {c.L}, plain MUFFIN (Algorithm 2)"
+        out = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic", "config": dict(workload_config(args), tuning=tuning),
-               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "roofline": roofline, "iteration_roofline": iteration_roofline,
+               "cpu_baseline": cpu, "cpu_baseline_1core": cpu1, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks,
                "theta": list(theta), "kernels": kernels,
-               "iter_ms": ms / args.steps / args.iters}
+               "iter_ms": ms / args.steps / args.iters,
+               "profiled_step_ms": profiled_ms, "cufft_reference": cufft}
         print(json.dumps(out), flush=True)
     plan.close()
 
