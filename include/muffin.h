@@ -173,6 +173,7 @@ typedef struct {
   int32_t candidates;      /* configurations timed (0 when cached) */
   double ms_default;       /* one iteration of every chain group, default */
   double ms_best;          /* the same with the chosen variants */
+  int32_t grad_chunk;      /* chosen gradient chunking (muffin_schedule) */
 } muffin_tune_info;
 
 /* Times each candidate configuration on this plan's own buffers (a few
@@ -180,7 +181,7 @@ typedef struct {
  * with sure = 1, one plain group otherwise), keeps the fastest and caches it
  * per shape (n, bands, batch, chains, levels, bases, SM count, device name):
  * in process, and in the text file `cache_path` when it is not NULL (read
- * first, one line "muffin-tune-2 <key> <syn_packed> <dct_ctas> <tcgen05>"
+ * first, one line "muffin-tune-3 <key> <syn_packed> <dct_ctas> <tcgen05> <grad_chunk>"
  * appended per new shape; lines that do not parse are ignored).  The timing iterations overwrite the plan's iterate state: a
  * following solve or sure_tune must start cold (warm = 0; a warm call
  * returns MUFFIN_ESTATE), and captured graphs are rebuilt.  info may be NULL.
@@ -212,6 +213,24 @@ MUFFIN_API muffin_status muffin_plan_inject_timeout(muffin_plan plan, int32_t on
  * drops captured graphs.  Errors: EINVAL. */
 MUFFIN_API muffin_status muffin_plan_set_tuning(muffin_plan plan, int32_t syn_packed,
                                                 int32_t dct_ctas_per_sm);
+
+/* Every launch choice of the per-iteration schedule (what the tuner picks).
+ * None changes results except spectral_tcgen05 (FP32 rounding order, see
+ * muffin_plan_set_spectral_kernel). */
+typedef struct {
+  int32_t syn_packed;       /* synthesis row-pass variant bits, 0..3 */
+  int32_t dct_ctas_per_sm;  /* mma.sync spectral grid, 0 = all resident */
+  int32_t spectral_tcgen05; /* 64-band plans: 1 tcgen05, 0 mma.sync */
+  int32_t grad_chunk;       /* images per pass of the gradient's three FFT
+                               passes: 0 = each pass over all images of a
+                               chain group; k > 0 = the three passes run k
+                               images at a time, so the spectra stay in L2 */
+} muffin_schedule;
+
+/* Reads / sets the schedule (set drops captured graphs and the iterate
+ * state).  Errors: EINVAL (NULL, a value out of range). */
+MUFFIN_API muffin_status muffin_plan_get_schedule(muffin_plan plan, muffin_schedule *s);
+MUFFIN_API muffin_status muffin_plan_set_schedule(muffin_plan plan, const muffin_schedule *s);
 
 typedef struct {
   int32_t iters_done; /* iterations run by this call */

@@ -160,6 +160,23 @@ class Plan:
         """Test hook: make the tensor-core waits of the next calls run out."""
         native.check(self._lib.muffin_plan_inject_timeout(self._h, int(bool(on))))
 
+    def schedule(self) -> dict:
+        """The launch choices of the per-iteration schedule (muffin_schedule)."""
+        sc = native.Schedule()
+        native.check(self._lib.muffin_plan_get_schedule(self._h, ctypes.byref(sc)))
+        return {f: getattr(sc, f) for f, _ in native.Schedule._fields_}
+
+    def set_schedule(self, **kw) -> None:
+        """Change some launch choices (keys of ``schedule()``); the next solve
+        starts cold."""
+        cur = self.schedule()
+        unknown = set(kw) - set(cur)
+        if unknown:
+            raise ValueError(f"unknown schedule keys {sorted(unknown)}")
+        cur.update(kw)
+        sc = native.Schedule(**{k: int(v) for k, v in cur.items()})
+        native.check(self._lib.muffin_plan_set_schedule(self._h, ctypes.byref(sc)))
+
     def set_tuning(self, syn_packed: int = 0, dct_ctas_per_sm: int = 0) -> None:
         native.check(self._lib.muffin_plan_set_tuning(self._h, int(syn_packed),
                                                       int(dct_ctas_per_sm)))

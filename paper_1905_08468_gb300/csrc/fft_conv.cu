@@ -38,12 +38,13 @@ __device__ __forceinline__ void load_tw(float2 *dst, const float2 *__restrict__ 
 template <int NN>
 __global__ void __launch_bounds__(kThreads)
 k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S,
-           const float2 *__restrict__ tw, int tlen) {
+           const float2 *__restrict__ tw, int tlen, int img0) {
   // sizes are compile-time so that the index splits below are shifts
   constexpr int n = NN, nq = row_pairs(NN), nh = (NN >> 1) + 1;
   constexpr int pitch = n + (n >> 4);
   extern __shared__ float2 sm2[];
-  const int img = blockIdx.y;
+  const int img = blockIdx.y;           // image of the chunk (its spectrum in S)
+  const int gimg = img0 + img;          // image of the cube
   const int y0 = blockIdx.x * 2 * nq;
   float2 *d = sm2, *tws = sm2 + nq * pitch;
   load_tw(tws, tw, tlen);
@@ -51,7 +52,7 @@ k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S,
   // pair tid / n + 256 u / n, column tid % n + (256 u) % n, so every index
   // is a per-thread base plus a compile-time offset
   const int tid = threadIdx.x;
-  const float *xi = x + (size_t)img * n * n + (size_t)(y0 + 2 * (tid / n)) * n + tid % n;
+  const float *xi = x + (size_t)gimg * n * n + (size_t)(y0 + 2 * (tid / n)) * n + tid % n;
   const int sb = (tid / n) * pitch + fpad(tid % n);
   constexpr int VPT = fft_vpt(NN);
   float2 v[VPT];
@@ -85,11 +86,11 @@ k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S,
 template <int NN>
 __global__ void __launch_bounds__(kThreads)
 k_cols(float2 *__restrict__ S, const float *__restrict__ kspec, int L,
-       const float2 *__restrict__ tw, int tlen) {
+       const float2 *__restrict__ tw, int tlen, int img0) {
   constexpr int n = NN, nh = (NN >> 1) + 1, CB = seqs_per_cta(NN);
   constexpr int pitch = n + (n >> 4);
   extern __shared__ float2 sm2[];
-  const int img = blockIdx.y, band = img % L;
+  const int img = blockIdx.y, band = (img0 + img) % L;
   const int k0 = blockIdx.x * CB;
   const int ncol = min(CB, nh - k0);
   float2 *d = sm2, *tws = sm2 + CB * pitch;
@@ -138,11 +139,11 @@ template <int NN>
 __global__ void __launch_bounds__(kThreads)
 k_rows_inv(const float2 *__restrict__ S, float *__restrict__ g,
            const float *__restrict__ bdata, int L,
-           const float2 *__restrict__ tw, int tlen) {
+           const float2 *__restrict__ tw, int tlen, int img0) {
   constexpr int n = NN, nq = row_pairs(NN), nh = (NN >> 1) + 1, half = NN >> 1;
   constexpr int pitch = n + (n >> 4);
   extern __shared__ float2 sm2[];
-  const int img = blockIdx.y, band = img % L;
+  const int img = blockIdx.y, gimg = img0 + img, band = gimg % L;
   const int y0 = blockIdx.x * 2 * nq;
   float2 *d = sm2, *tws = sm2 + nq * pitch;
   load_tw(tws, tw, tlen);
@@ -157,11 +158,11 @@ k_rows_inv(const float2 *__restrict__ S, float *__restrict__ g,
   }
   __syncthreads();
   fft_inplace<NN, true>(d, nq, pitch, tws);
-  const bool sub = (bdata != nullptr) && (img < L);
+  const bool sub = (bdata != nullptr) && (gimg < L);
   // element u of the thread: row pair tid / n + 256 u / n (see k_rows_fwd)
   const int tid = threadIdx.x;
   const size_t o0 = (size_t)(y0 + 2 * (tid / n)) * n + tid % n;
-  float *gi = g + (size_t)img * n * n + o0;
+  float *gi = g + (size_t)gimg * n * n + o0;
   const float *bi = sub ? bdata + (size_t)band * n * n + o0 : nullptr;
   const int sb = (tid / n) * pitch + fpad(tid % n);
   constexpr int VPT = fft_vpt(NN);
@@ -256,9 +257,9 @@ inline int grid_for(size_t count) {
 template <int NN>
 cudaError_t gradient_n(const float *x, float *g, const float *b, float2 *S,
                        const float *kspec, const float2 *tw, int L, int C,
-                       cudaStream_t st, Prof *prof) {
+                       cudaStream_t st, Prof *prof, int chunk) {
   constexpr int n = NN;
-  const int nimg = C * L;
+  const int ntot = C * L;
   const int RB = 2 * row_pairs(n);                  // real rows per CTA (even)
   const int CB = seqs_per_cta(n);                   // columns per CTA
   const int nh = (n >> 1) + 1;
@@ -275,21 +276,31 @@ cudaError_t gradient_n(const float *x, float *g, const float *b, float2 *S,
   }
   const double img = (double)n * n, spec = (double)nh * n * 8.0;
   const double fft = 5.0 * n * ilog2(n);   // flops of one length-n complex FFT
-  {
-    ProfScope ps(prof, "grad_rows_fwd", nimg * (img * 4.0 + spec),
-                 nimg * (n / 2.0) * fft, st);
-    k_rows_fwd<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(x, S, tw, tlen);
-  }
-  {
-    ProfScope ps(prof, "grad_cols", nimg * 2.0 * spec + (double)L * nh * n * 4.0,
-                 nimg * (double)nh * 2.0 * fft, st);
-    k_cols<NN><<<dim3((nh + CB - 1) / CB, nimg), kThreads, smc, st>>>(S, kspec, L, tw, tlen);
-  }
-  {
-    ProfScope ps(prof, "grad_rows_inv",
-                 nimg * (spec + img * 4.0) + (b ? (double)L * img * 4.0 : 0.0),
-                 nimg * (n / 2.0) * fft, st);
-    k_rows_inv<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(S, g, b, L, tw, tlen);
+  const int step = chunk > 0 && chunk < ntot ? chunk : ntot;
+  // the whole call: x read, g written, b read, |h_hat|^2 read once per
+  // band, the spectra of every image written and read twice
+  ProfScope all(prof, "grad_total",
+                ntot * (img * 8.0 + 4.0 * spec) + (b ? (double)L * img * 4.0 : 0.0) +
+                    (double)L * nh * n * 4.0,
+                ntot * (double)(n + 2 * nh) * fft, st);
+  for (int i0 = 0; i0 < ntot; i0 += step) {
+    const int nimg = step < ntot - i0 ? step : ntot - i0;
+    const int nb = b ? (i0 < L ? (L - i0 < nimg ? L - i0 : nimg) : 0) : 0;   // images with b
+    {
+      ProfScope ps(prof, "grad_rows_fwd", nimg * (img * 4.0 + spec),
+                   nimg * (n / 2.0) * fft, st);
+      k_rows_fwd<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(x, S, tw, tlen, i0);
+    }
+    {
+      ProfScope ps(prof, "grad_cols", nimg * 2.0 * spec + (double)nimg * nh * n * 4.0,
+                   nimg * (double)nh * 2.0 * fft, st);
+      k_cols<NN><<<dim3((nh + CB - 1) / CB, nimg), kThreads, smc, st>>>(S, kspec, L, tw, tlen, i0);
+    }
+    {
+      ProfScope ps(prof, "grad_rows_inv", nimg * (spec + img * 4.0) + nb * img * 4.0,
+                   nimg * (n / 2.0) * fft, st);
+      k_rows_inv<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(S, g, b, L, tw, tlen, i0);
+    }
   }
   return cudaGetLastError();
 }
@@ -298,19 +309,19 @@ cudaError_t gradient_n(const float *x, float *g, const float *b, float2 *S,
 
 cudaError_t launch_gradient(const float *x, float *g, const float *b,
                             float2 *S, const float *kspec, const float2 *tw,
-                            int n, int L, int C, cudaStream_t st, Prof *prof) {
+                            int n, int L, int C, cudaStream_t st, Prof *prof, int chunk) {
   switch (n) {
-    case 2: return gradient_n<2>(x, g, b, S, kspec, tw, L, C, st, prof);
-    case 4: return gradient_n<4>(x, g, b, S, kspec, tw, L, C, st, prof);
-    case 8: return gradient_n<8>(x, g, b, S, kspec, tw, L, C, st, prof);
-    case 16: return gradient_n<16>(x, g, b, S, kspec, tw, L, C, st, prof);
-    case 32: return gradient_n<32>(x, g, b, S, kspec, tw, L, C, st, prof);
-    case 64: return gradient_n<64>(x, g, b, S, kspec, tw, L, C, st, prof);
-    case 128: return gradient_n<128>(x, g, b, S, kspec, tw, L, C, st, prof);
-    case 256: return gradient_n<256>(x, g, b, S, kspec, tw, L, C, st, prof);
-    case 512: return gradient_n<512>(x, g, b, S, kspec, tw, L, C, st, prof);
-    case 1024: return gradient_n<1024>(x, g, b, S, kspec, tw, L, C, st, prof);
-    case 2048: return gradient_n<2048>(x, g, b, S, kspec, tw, L, C, st, prof);
+    case 2: return gradient_n<2>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
+    case 4: return gradient_n<4>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
+    case 8: return gradient_n<8>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
+    case 16: return gradient_n<16>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
+    case 32: return gradient_n<32>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
+    case 64: return gradient_n<64>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
+    case 128: return gradient_n<128>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
+    case 256: return gradient_n<256>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
+    case 512: return gradient_n<512>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
+    case 1024: return gradient_n<1024>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
+    case 2048: return gradient_n<2048>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
     default: return cudaErrorInvalidValue;
   }
 }

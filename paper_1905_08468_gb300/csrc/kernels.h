@@ -25,8 +25,6 @@ struct Prof {
   std::vector<Stat> stats;
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
-  cudaEvent_t cur_a = nullptr;
-  int cur_id = -1;
 
   int find(const char *name, double bytes, double flops) {
     for (size_t i = 0; i < stats.size(); ++i)
@@ -42,16 +40,18 @@ struct Prof {
     cudaEventCreate(&e);
     return e;
   }
-  void begin(const char *name, double bytes, double flops, cudaStream_t st) {
+  // a bracket returns its (stat, start event) token, so brackets may nest
+  // (an aggregate around several launches, e.g. the chunks of the gradient)
+  Pending begin(const char *name, double bytes, double flops, cudaStream_t st) {
     if (pending.size() >= 2048) resolve();
-    cur_id = find(name, bytes, flops);
-    cur_a = take();
-    cudaEventRecord(cur_a, st);
+    Pending t{find(name, bytes, flops), take(), nullptr};
+    cudaEventRecord(t.a, st);
+    return t;
   }
-  void end(cudaStream_t st) {
-    cudaEvent_t b = take();
-    cudaEventRecord(b, st);
-    pending.push_back({cur_id, cur_a, b});
+  void end(Pending t, cudaStream_t st) {
+    t.b = take();
+    cudaEventRecord(t.b, st);
+    pending.push_back(t);
   }
   void resolve() {
     if (pending.empty()) return;
@@ -79,9 +79,10 @@ struct Prof {
 struct ProfScope {
   Prof *p;
   cudaStream_t st;
+  Prof::Pending t{};
   ProfScope(Prof *p_, const char *name, double bytes, double flops, cudaStream_t s)
-      : p(p_), st(s) { if (p) p->begin(name, bytes, flops, st); }
-  ~ProfScope() { if (p) p->end(st); }
+      : p(p_), st(s) { if (p) t = p->begin(name, bytes, flops, st); }
+  ~ProfScope() { if (p) p->end(t, st); }
 };
 
 // Records msg as the thread's muffin_last_error() text and returns s (plan.cu).
@@ -91,10 +92,13 @@ int set_last_error_code(int s, const char *msg);
 // FP32 gradient pipeline: g[c][l] = H_l^T H_l x[c][l] - (c == 0 && b ? b[l] : 0)
 // for nimg = C*L images.  S: spectrum scratch [nimg][n/2+1][n] float2.
 // kspec: [L][n/2+1][n] = |h_hat_l(ky, kx)|^2 / n^2 (kx-major).
+// chunk > 0: the three passes run over `chunk` images at a time (S then
+// needs room for chunk images only and stays in L2 between the passes);
+// chunk <= 0: each pass over all images at once.
 cudaError_t launch_gradient(const float *x, float *g, const float *b,
                             float2 *S, const float *kspec, const float2 *tw,
                             int n, int L, int C, cudaStream_t st,
-                            Prof *prof = nullptr);
+                            Prof *prof = nullptr, int chunk = 0);
 
 // Stage twiddle tables of the FP32 gradient FFT for side n (host side).
 int fft32_table_len(int n);

@@ -170,7 +170,7 @@ muffin_status iterate_group(muffin_plan P, Group &g, int nc = -1) {
   if (nc < 0) nc = P->B;
   const int Lv = nc * P->L;
   CK(launch_gradient(g.x, g.g, g.b, P->S, P->kspec, P->tw32, P->n, Lv, g.C, P->ws,
-                     P->pp()));
+                     P->pp(), P->grad_chunk));
   WaveArgs w = P->wave(g.C);
   w.L = Lv;
   CK(wavelet_synthesis_prox(w, g, P->p.positivity, P->ws));
@@ -387,7 +387,7 @@ muffin_status window_end(muffin_plan P, const muffin_sure_params *sp) {
   Group g0 = g;
   g0.C = 1;
   CK(launch_gradient(g0.x, g0.g, g0.b, P->S, P->kspec, P->tw32, P->n, P->Lt, 1, P->ws,
-                     P->pp()));
+                     P->pp(), P->grad_chunk));
   SureStatsArgs sa{};
   sa.grad = g.g; sa.x = g.x; sa.xb = P->grp[1].x; sa.b = P->b; sa.htd = P->htd;
   sa.wband = P->wband; sa.n = P->n; sa.L = P->Lt;

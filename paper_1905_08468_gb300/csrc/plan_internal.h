@@ -80,6 +80,7 @@ struct muffin_plan_s {
   int syn_packed = 0;     // synthesis variant bits (see WaveArgs::syn_packed)
   int dct_ctas = 0;       // spectral kernel CTAs per SM (0: all resident)
   int dct_tc = 0;         // spectral step on tcgen05 (L = 64)
+  int grad_chunk = 0;     // images per pass of the gradient FFTs (0: all at once)
   int inject_timeout = 0; // test hook (muffin_plan_inject_timeout)
   int *kerr = nullptr;    // device flag: a bounded tensor-core wait gave up
   std::map<std::pair<int, int>, cudaGraphExec_t> gplain;   // (parity, cubes)

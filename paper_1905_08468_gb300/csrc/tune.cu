@@ -1,5 +1,6 @@
 // Per-shape choice of launch variants for the hot kernels (the wavelet
-// synthesis row pass and the persistent spectral kernel's grid).  Every
+// synthesis row pass, the spectral kernel and its grid, the chunking of the
+// gradient's FFT passes).  Every
 // variant yields identical results; only speed differs, and it depends on
 // the cube shape and the GPU, so the plan times the candidates on its own
 // buffers and caches the winner per shape, in process and optionally in a
@@ -22,6 +23,7 @@ struct Choice {
   int syn_packed = 0;
   int dct_ctas = 0;
   int dct_tc = 0;      // spectral step on tcgen05 (64-band plans)
+  int grad_chunk = 0;  // images per pass of the gradient FFTs (0: all)
 };
 
 std::mutex g_mu;
@@ -43,20 +45,22 @@ std::string shape_key(muffin_plan P) {
   return buf;
 }
 
-// the last line "muffin-tune-2 <key> <syn_packed> <dct_ctas> <dct_tc>" with this key
+// the last line "muffin-tune-3 <key> <syn_packed> <dct_ctas> <dct_tc> <grad_chunk>"
+// with this key
 bool file_lookup(const char *path, const std::string &key, Choice *c) {
   FILE *f = std::fopen(path, "r");
   if (!f) return false;
   char line[512], tag[32], k[400];
   bool found = false;
   while (std::fgets(line, sizeof line, f)) {
-    int a = 0, b = 0, t = 0;
-    if (std::sscanf(line, "%31s %399s %d %d %d", tag, k, &a, &b, &t) != 5) continue;
-    if (std::strcmp(tag, "muffin-tune-2") != 0 || key != k) continue;
-    if (a < 0 || a > 3 || b < 0 || t < 0 || t > 1) continue;
+    int a = 0, b = 0, t = 0, g = 0;
+    if (std::sscanf(line, "%31s %399s %d %d %d %d", tag, k, &a, &b, &t, &g) != 6) continue;
+    if (std::strcmp(tag, "muffin-tune-3") != 0 || key != k) continue;
+    if (a < 0 || a > 3 || b < 0 || t < 0 || t > 1 || g < 0) continue;
     c->syn_packed = a;
     c->dct_ctas = b;
     c->dct_tc = t;
+    c->grad_chunk = g;
     found = true;
   }
   std::fclose(f);
@@ -66,7 +70,8 @@ bool file_lookup(const char *path, const std::string &key, Choice *c) {
 void file_append(const char *path, const std::string &key, const Choice &c) {
   FILE *f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "muffin-tune-2 %s %d %d %d\n", key.c_str(), c.syn_packed, c.dct_ctas, c.dct_tc);
+  std::fprintf(f, "muffin-tune-3 %s %d %d %d %d\n", key.c_str(), c.syn_packed, c.dct_ctas,
+               c.dct_tc, c.grad_chunk);
   std::fclose(f);
 }
 
@@ -74,6 +79,7 @@ void apply(muffin_plan P, const Choice &c) {
   P->syn_packed = c.syn_packed;
   P->dct_ctas = c.dct_ctas;
   P->dct_tc = P->L == 64 ? c.dct_tc : 0;
+  P->grad_chunk = c.grad_chunk;
 }
 
 // mean time of one iteration of every chain group with choice c
@@ -144,6 +150,18 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
     ++cand;
     if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
   }
+  // the gradient's FFT passes over image chunks whose spectra fit in L2
+  // (the images of one gradient call: C L of a chain group)
+  const int nimg = P->Cmax * P->Lt;
+  for (int q : {48, 16}) {
+    if (q >= nimg || s != MUFFIN_OK) continue;
+    Choice c = *best;
+    c.grad_chunk = q;
+    double t = 0.0;
+    s = time_choice(P, c, reps, e0, e1, &t);
+    ++cand;
+    if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
+  }
   if (s == MUFFIN_OK) s = muffin::pi::leave(P, true);
   P->profiling = was_profiling;
   cudaEventDestroy(e0);
@@ -190,6 +208,30 @@ muffin_status muffin_plan_set_tuning(muffin_plan P, int32_t syn_packed, int32_t 
   return MUFFIN_OK;
 }
 
+muffin_status muffin_plan_get_schedule(muffin_plan P, muffin_schedule *s) {
+  if (!P || !s) return fail(MUFFIN_EINVAL, "NULL argument");
+  s->syn_packed = P->syn_packed;
+  s->dct_ctas_per_sm = P->dct_ctas;
+  s->spectral_tcgen05 = P->dct_tc;
+  s->grad_chunk = P->grad_chunk;
+  return MUFFIN_OK;
+}
+
+muffin_status muffin_plan_set_schedule(muffin_plan P, const muffin_schedule *s) {
+  if (!P || !s) return fail(MUFFIN_EINVAL, "NULL argument");
+  if (s->syn_packed < 0 || s->syn_packed > 3 || s->dct_ctas_per_sm < 0 || s->grad_chunk < 0 ||
+      (s->spectral_tcgen05 != 0 && s->spectral_tcgen05 != 1))
+    return fail(MUFFIN_EINVAL, "schedule value out of range");
+  if (s->spectral_tcgen05 && P->L != 64)
+    return fail(MUFFIN_EINVAL, "the tcgen05 spectral kernel needs 64 bands (plan has %d)", P->L);
+  muffin::pi::drop_graphs_and_state(P);
+  P->syn_packed = s->syn_packed;
+  P->dct_ctas = s->dct_ctas_per_sm;
+  P->dct_tc = s->spectral_tcgen05;
+  P->grad_chunk = s->grad_chunk;
+  return MUFFIN_OK;
+}
+
 muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin_tune_info *info) {
   if (!P) return fail(MUFFIN_EINVAL, "plan is NULL");
   const std::string key = shape_key(P);
@@ -213,6 +255,7 @@ muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin
       info->syn_packed = c.syn_packed;
       info->dct_ctas_per_sm = c.dct_ctas;
       info->spectral_tcgen05 = P->dct_tc;
+      info->grad_chunk = P->grad_chunk;
       info->from_cache = 1;
     }
     return MUFFIN_OK;
@@ -231,6 +274,7 @@ muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin
     info->syn_packed = c.syn_packed;
     info->dct_ctas_per_sm = c.dct_ctas;
     info->spectral_tcgen05 = P->dct_tc;
+    info->grad_chunk = P->grad_chunk;
     info->from_cache = 0;
   }
   return MUFFIN_OK;

@@ -59,7 +59,12 @@ class TuneInfo(ctypes.Structure):
     _fields_ = [("syn_packed", c_int32), ("dct_ctas_per_sm", c_int32),
                 ("spectral_tcgen05", c_int32),
                 ("from_cache", c_int32), ("candidates", c_int32),
-                ("ms_default", c_double), ("ms_best", c_double)]
+                ("ms_default", c_double), ("ms_best", c_double), ("grad_chunk", c_int32)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("syn_packed", c_int32), ("dct_ctas_per_sm", c_int32),
+                ("spectral_tcgen05", c_int32), ("grad_chunk", c_int32)]
 
 
 class KernelStat(ctypes.Structure):
@@ -89,6 +94,8 @@ SIGNATURES = {
     "muffin_plan_autotune": (c_int32, [c_void_p, ctypes.c_char_p, ctypes.POINTER(TuneInfo)]),
     "muffin_plan_set_tuning": (c_int32, [c_void_p, c_int32, c_int32]),
     "muffin_plan_set_spectral_kernel": (c_int32, [c_void_p, c_int32]),
+    "muffin_plan_get_schedule": (c_int32, [c_void_p, ctypes.POINTER(Schedule)]),
+    "muffin_plan_set_schedule": (c_int32, [c_void_p, ctypes.POINTER(Schedule)]),
     "muffin_plan_inject_timeout": (c_int32, [c_void_p, c_int32]),
     "muffin_sure_params_default": (None, [ctypes.POINTER(SureParams)]),
     "muffin_sure_tune": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p,

@@ -10,10 +10,11 @@ from tests.gpu_util import cuda, dev
 pytestmark = pytest.mark.gpu
 
 
-def _solve(pkg, torch, c, syn, ctas, iters=13):
+def _solve(pkg, torch, c, syn, ctas, iters=13, grad_chunk=0):
     x = torch.zeros((c.L, c.n, c.n), device="cuda")
     with pkg.Plan(c.n, c.L, c.psf) as p:
         p.set_tuning(syn, ctas)
+        p.set_schedule(grad_chunk=grad_chunk)
         p.solve(dev(c.dirty, torch), x, iters, 1e-2, 2e-2)
     return x
 
@@ -29,6 +30,9 @@ def test_plain_variants_bit_identical(n, L):
             if syn == 0 and ctas == 0:
                 continue
             assert torch.equal(_solve(pkg, torch, c, syn, ctas), ref), (syn, ctas)
+    # the gradient's FFT passes over image chunks (ragged last chunk included)
+    for chunk in (1, 3, L - 1):
+        assert torch.equal(_solve(pkg, torch, c, 0, 0, grad_chunk=chunk), ref), chunk
 
 
 def test_sure_batch_variants_bit_identical():
@@ -42,10 +46,11 @@ def test_sure_batch_variants_bit_identical():
     d = dev(np.stack([c.dirty for c in cs]), torch)
     de = dev(np.stack([c.delta for c in cs]), torch)
     out = []
-    for syn, ctas in [(0, 0), (3, 1), (1, 2), (2, 0)]:
+    for syn, ctas, chunk in [(0, 0, 0), (3, 1, 5), (1, 2, 0), (2, 0, 7)]:
         x = torch.zeros((B, L, n, n), device="cuda")
         with pkg.Plan(n, L, psf, sure=True, batch=B) as p:
             p.set_tuning(syn, ctas)
+            p.set_schedule(grad_chunk=chunk)
             th, tr, _ = p.sure_tune(d, de, nv, x, [(0.05, 0.05), (0.02, 0.08)], 15, **args)
         out.append((x, th, tr))
     for x, th, tr in out[1:]:
@@ -74,7 +79,7 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         p.solve(dev(c.dirty, torch), x, 13, 1e-2, 2e-2)
         assert torch.equal(x, ref)
     lines = [ln.split() for ln in cache.read_text().splitlines()]
-    assert len(lines) == 1 and lines[0][0] == "muffin-tune-2" and "n=64,L=8" in lines[0][1]
+    assert len(lines) == 1 and lines[0][0] == "muffin-tune-3" and "n=64,L=8" in lines[0][1]
     # the same shape again: in-process cache
     with pkg.Plan(64, 8, c.psf) as p:
         again = p.autotune(str(cache))
@@ -82,13 +87,14 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         assert (again.syn_packed, again.dct_ctas_per_sm) == (info.syn_packed, info.dct_ctas_per_sm)
     # a shape only the file knows (written by hand), beside lines to ignore
     key = lines[0][1].replace("n=64,L=8", "n=16,L=8")
-    cache.write_text("garbage line\nmuffin-tune-2 %s 9 1 0\nmuffin-tune-1 %s 3 2\n"
-                     "muffin-tune-2 %s 2 1 0\n" % (key, key, key))
+    cache.write_text("garbage line\nmuffin-tune-3 %s 9 1 0 0\nmuffin-tune-2 %s 3 2 0\n"
+                     "muffin-tune-3 %s 2 1 0 3\n" % (key, key, key))
     c16 = make_cube(16, 8, 4, 1, 480, seed=841)
     with pkg.Plan(16, 8, c16.psf) as p:
         got = p.autotune(str(cache))
         assert got.from_cache == 1
-        assert (got.syn_packed, got.dct_ctas_per_sm) == (2, 1)
+        assert (got.syn_packed, got.dct_ctas_per_sm, got.grad_chunk) == (2, 1, 3)
+        assert p.schedule()["grad_chunk"] == 3
 
 
 def test_set_tuning_rejects_bad_values():
