@@ -309,7 +309,7 @@ def run_serve(args) -> None:
     outs_b = {}
 
     def batched(t0, lat):
-        with pkg.Server(max_batch=args.serve_batch, chunk=10) as srv:
+        with pkg.Server(max_batch=args.serve_batch, chunk=args.serve_chunk) as srv:
             nxt, tick, arr = 0, {}, {}
             while len(lat) < len(stream):
                 now = time.perf_counter() - t0
@@ -361,7 +361,7 @@ def run_serve(args) -> None:
                                   "L in {16,32,64}", "requests": len(stream),
                       "arrival_seed": args.serve_seed,
                       "iters": iters, "mu": mu, "gamma": mu, "max_batch": args.serve_batch,
-                      "chunk": 10},
+                      "chunk": args.serve_chunk},
            "batched": {"p50_s": nearest_rank(lb, 0.5), "p99_s": nearest_rank(lb, 0.99),
                        "makespan_s": mb, "voxel_iters_per_s": tb},
            "one_cube_per_launch": {"p50_s": nearest_rank(l1, 0.5),
@@ -471,6 +471,8 @@ def main() -> None:
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-iters", type=int, default=300)
     ap.add_argument("--serve-batch", type=int, default=8)
+    ap.add_argument("--serve-chunk", type=int, default=10,
+                    help="iterations per pool chunk of the server")
     ap.add_argument("--convergence", action="store_true",
                     help="ADA-PT from several initial (mu, gamma): theta, SUGAR, SNR, WMSE curves")
     ap.add_argument("--conv-inits", default="3e-2,1e-1;3e-2,1e-3;3e-4,1e-3;3e-4,1e-1")

@@ -451,12 +451,15 @@ MUFFIN_API muffin_status muffin_op_dct(muffin_plan plan, const float *x, float *
  * Deconvolution requests of any shape (n, L) with fixed (mu, gamma) are
  * queued, admitted in arrival order into free slots of batched plans ("pools",
  * one per shape) while the active work stays under max_active_voxels and the
- * pools' device footprint fits the HBM budget, advanced together
- * in shared launches a few iterations per scheduling step, and retired as
- * soon as their own iteration count is reached; freed slots take the next
- * request at the following step.  A request's result does not depend on the
- * other requests in its pool.  The caller drives the loop (submit as
- * requests arrive, step, poll).  Not thread-safe: one thread per server. */
+ * pools' device footprint fits the HBM budget, and advanced a chunk of
+ * iterations at a time in shared launches.  Pools run independently on their
+ * own streams: a pool takes new requests and retires finished ones at its own
+ * chunk boundaries, and the pool holding the oldest request runs on the
+ * highest-priority stream (the next oldest on the second), so the oldest work
+ * gets the GPU first while younger pools fill the rest.  A request's result
+ * does not depend on the other requests in its pool.  The caller drives the
+ * loop (submit as requests arrive, step, poll).  Not thread-safe: one thread
+ * per server. */
 typedef struct muffin_server_s *muffin_server;
 
 typedef struct {
@@ -468,7 +471,7 @@ typedef struct {
   double sigma;            /* dual step (default 10) */
   int32_t step_rule;       /* as muffin_params (default 0) */
   double tau_safety;       /* default 0.99 */
-  int32_t chunk;           /* iterations per scheduling step (default 10) */
+  int32_t chunk;           /* iterations per pool chunk (default 10) */
   size_t max_active_voxels;/* admission stops (in arrival order) once the
                               requests in slots hold this many voxels; one
                               request is always admitted (default 3 * 2^24) */
@@ -479,21 +482,33 @@ MUFFIN_API void muffin_server_params_default(muffin_server_params *p);
 MUFFIN_API muffin_status muffin_server_create(const muffin_server_params *p,
                                               void *stream, muffin_server *out);
 MUFFIN_API void muffin_server_destroy(muffin_server s);
-/* Queue a request: psf and dirty [L][n][n] (host or device, copied now),
- * Algorithm 2 with fixed (mu, gamma) from X0 = 0 for `iters` iterations.
- * Errors: EINVAL (shape), ENOMEM (one pool of this shape exceeds the budget). */
+/* Queue a request: psf and dirty [L][n][n] (host or device, copied now;
+ * when nothing is queued ahead and an idle pool of its shape has a free slot,
+ * the request is admitted at once, straight from these arrays), Algorithm 2
+ * with fixed (mu, gamma) from X0 = 0 for `iters` iterations.  A request
+ * whose inputs turn out non-finite at admission is rejected: its poll
+ * returns MUFFIN_ENUMERIC (or EINVAL for a PSF whose spectrum is not finite)
+ * and releases the ticket.  Errors: EINVAL (shape), ENOMEM (one pool of this
+ * shape exceeds the budget), ECUDA. */
 MUFFIN_API muffin_status muffin_serve_submit(muffin_server s, int32_t n,
                                              int32_t nbands, const float *psf,
                                              const float *dirty, double mu,
                                              double gamma, int32_t iters,
                                              uint64_t *ticket);
-/* One scheduling step: admit, advance every pool by up to `chunk`
- * iterations, retire finished requests.  Synchronous.  *active / *queued
- * (nullable) report the requests in slots and still waiting. */
+/* One scheduling step, without waiting for the slowest pool: collect the
+ * pools whose chunk has finished and retire their finished requests, admit
+ * queued requests into idle pools, launch the next chunk (up to `chunk`
+ * iterations) of every idle pool with active requests.  When none of these
+ * happened while chunks are in flight, waits for the first of them to finish
+ * and does it again, so every step makes progress.  *active / *queued
+ * (nullable) report the requests in slots and still waiting.  Errors: ECUDA,
+ * ENOMEM, ETIMEOUT (no chunk finished within 60 s). */
 MUFFIN_API muffin_status muffin_serve_step(muffin_server s, int32_t *active,
                                            int32_t *queued);
 /* *done = 1 once the request has finished; then, if x_out != NULL, its cube
- * [L][n][n] is copied to x_out (host or device) and the ticket is released. */
+ * [L][n][n] is copied to x_out (host or device) and the ticket is released.
+ * A rejected request (see muffin_serve_submit) returns its error with
+ * *done = 1 and releases the ticket. */
 MUFFIN_API muffin_status muffin_serve_poll(muffin_server s, uint64_t ticket,
                                            int32_t *done, float *x_out);
 /* Device bytes held by the pools and their number (nullable outputs). */

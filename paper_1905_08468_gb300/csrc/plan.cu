@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -164,20 +165,47 @@ muffin_status adjoint_fp64(muffin_plan P, const float *y_dev, const double2 *hh,
   return MUFFIN_OK;
 }
 
-// one iteration of group g; nc < B restricts a plain group (C = 1) to the
-// first nc cubes (the serving pools skip their free slots)
-muffin_status iterate_group(muffin_plan P, Group &g, int nc = -1) {
-  if (nc < 0) nc = P->B;
-  const int Lv = nc * P->L;
-  CK(launch_gradient(g.x, g.g, g.b, P->S, P->kspec, P->tw32, P->n, Lv, g.C, P->ws,
-                     P->pp(), P->grad_chunk));
+// the kernels of one iteration of group g without the x / x~ swap; a plain
+// group (C = 1) may be restricted to the cubes [c0, c1)
+muffin_status iterate_kernels(muffin_plan P, const Group &g, int c0, int c1) {
+  if (c1 < 0) c1 = P->B;
+  const int Lv = (c1 - c0) * P->L;
+  Group h = g;
   WaveArgs w = P->wave(g.C);
-  w.L = Lv;
-  CK(wavelet_synthesis_prox(w, g, P->p.positivity, P->ws));
-  CK(wavelet_analysis_dual(w, g, P->ws));
   DctArgs d = P->dct(g.C);
-  d.B = nc;
-  CK(dct_dual(d, g, P->ws));
+  const float *kspec = P->kspec;
+  if (c0 > 0) {            // only plain groups (the chain stride is the plan's)
+    const size_t ov = (size_t)c0 * P->NLc;
+    h.x += ov; h.xt += ov; h.v += ov; h.t += ov; h.g += ov; h.b += ov;
+    h.u += ov * P->K;
+    kspec += (size_t)c0 * P->L * (P->n / 2 + 1) * P->n;
+    w.beta += (size_t)c0 * P->L;
+    w.sc += c0;
+    d.alpha += (size_t)c0 * P->N;
+    d.sc += c0;
+  }
+  CK(launch_gradient(h.x, h.g, h.b, P->S, kspec, P->tw32, P->n, Lv, g.C, P->ws,
+                     P->pp(), P->grad_chunk));
+  w.L = Lv;
+  CK(wavelet_synthesis_prox(w, h, P->p.positivity, P->ws));
+  CK(wavelet_analysis_dual(w, h, P->ws));
+  d.B = c1 - c0;
+  CK(dct_dual(d, h, P->ws));
+  return MUFFIN_OK;
+}
+
+// one iteration of group g; a plain group (C = 1) may be restricted to some
+// runs [c0, c1) of cubes (the serving pools skip their free slots)
+muffin_status iterate_group(muffin_plan P, Group &g,
+                            const std::vector<std::pair<int, int>> &runs = {}) {
+  if (runs.empty()) {
+    muffin_status s = iterate_kernels(P, g, 0, P->B);
+    if (s != MUFFIN_OK) return s;
+  }
+  for (const auto &r : runs) {
+    muffin_status s = iterate_kernels(P, g, r.first, r.second);
+    if (s != MUFFIN_OK) return s;
+  }
   float *t = g.x; g.x = g.xt; g.xt = t;
   return MUFFIN_OK;
 }
@@ -645,24 +673,23 @@ muffin_status set_theta(muffin_plan P, int b0, int b1, const double *mu, const d
   return MUFFIN_OK;
 }
 
-muffin_status run_plain(muffin_plan P, int iters, int ncubes) {
+muffin_status run_plain(muffin_plan P, int iters, const std::vector<std::pair<int, int>> &runs) {
   Group &g = P->grp[0];
   Group plain = g;
   plain.C = 1;
-  const int nc = ncubes < 0 || ncubes > P->B ? P->B : ncubes;
   muffin_status s = MUFFIN_OK;
   const bool graphs = P->use_graphs && !P->profiling;
   int k = 0;
   while (k < iters) {
     const int par = plain.x == P->grp_x0[0] ? 0 : 1;
-    const std::pair<int, int> key(par, nc);
+    const std::pair<int, std::vector<std::pair<int, int>>> key(par, runs);
     auto it = P->gplain.find(key);
     if (graphs && iters - k >= 2 && it == P->gplain.end() && k > 0) {
       Group cap = plain;
       cudaGraphExec_t ex = nullptr;
       s = capture(P, &ex, [&]() -> muffin_status {
-        muffin_status r = iterate_group(P, cap, nc);
-        if (r == MUFFIN_OK) r = iterate_group(P, cap, nc);
+        muffin_status r = iterate_group(P, cap, runs);
+        if (r == MUFFIN_OK) r = iterate_group(P, cap, runs);
         return r;
       });
       if (s != MUFFIN_OK) return s;
@@ -672,7 +699,7 @@ muffin_status run_plain(muffin_plan P, int iters, int ncubes) {
       CK(cudaGraphLaunch(it->second, P->ws));
       k += 2;      // two swaps: pointers unchanged
     } else {
-      s = iterate_group(P, plain, nc);
+      s = iterate_group(P, plain, runs);
       if (s != MUFFIN_OK) return s;
       ++k;
     }
@@ -869,7 +896,7 @@ muffin_status muffin_solve_batch(muffin_plan P, const float *dirty, float *x,
   muffin_status numeric = MUFFIN_OK;
   while (done < iters) {
     const int seg = every > 0 ? std::min(every, iters - done) : iters - done;
-    s = pi::run_plain(P, seg, P->B);
+    s = pi::run_plain(P, seg, {});
     if (s != MUFFIN_OK) return s;
     done += seg;
     if (every > 0 && done % every == 0) {

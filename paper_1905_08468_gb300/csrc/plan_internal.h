@@ -5,6 +5,7 @@
 
 #include <map>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -83,7 +84,8 @@ struct muffin_plan_s {
   int grad_chunk = 0;     // images per pass of the gradient FFTs (0: all at once)
   int inject_timeout = 0; // test hook (muffin_plan_inject_timeout)
   int *kerr = nullptr;    // device flag: a bounded tensor-core wait gave up
-  std::map<std::pair<int, int>, cudaGraphExec_t> gplain;   // (parity, cubes)
+  // (parity, runs of cubes) -> two plain iterations
+  std::map<std::pair<int, std::vector<std::pair<int, int>>>, cudaGraphExec_t> gplain;
   cudaGraphExec_t gsure[2] = {nullptr, nullptr};
   int gsure_window = 0, gsure_reset = -1;
   double gsure_eta[2] = {0, 0}, gsure_tmin = 0;
@@ -151,8 +153,9 @@ muffin_status load_dirty(muffin_plan P, int b0, int b1, const float *dirty);
 muffin_status reset_cubes(muffin_plan P, int g, int b0, int b1, const float *x0_dev);
 // (mu, gamma) of cubes [b0, b1) and their tau (host arrays of b1-b0 values)
 muffin_status set_theta(muffin_plan P, int b0, int b1, const double *mu, const double *gamma);
-// `iters` plain iterations of group 0 on the first `ncubes` cubes (work stream)
-muffin_status run_plain(muffin_plan P, int iters, int ncubes);
+// `iters` plain iterations of group 0 on the runs [c0, c1) of cubes (all
+// cubes when runs is empty), on the work stream
+muffin_status run_plain(muffin_plan P, int iters, const std::vector<std::pair<int, int>> &runs);
 // copy X of cubes [b0, b1) of group 0 to dst (host or device)
 muffin_status fetch_x(muffin_plan P, int b0, int b1, float *dst);
 // order the work stream after the caller's stream / the caller's after it

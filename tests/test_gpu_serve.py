@@ -130,3 +130,38 @@ def test_footprint_estimate_matches_allocation(n, L, B, sure, J):
     psf[:, :, 0, 0] = 1.0
     with pkg.Plan(n, L, psf, batch=B, sure=sure, levels=J) as p:
         assert pkg.estimate_bytes(n, L, batch=B, sure=sure, levels=J) == p.device_bytes
+
+
+def test_nonfinite_request_is_rejected_without_stopping_the_server():
+    """A request with a NaN in its dirty cube is rejected at admission (its
+    poll reports MUFFIN_ENUMERIC and releases the ticket); the requests
+    around it are served as usual."""
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    cs = [make_cube(32, 4, 8, 1, 900, seed=600 + i) for i in range(3)]
+    bad = cs[1].dirty.copy()
+    bad[1, 2, 3] = np.nan
+    with pkg.Server(max_batch=2, chunk=5) as srv:
+        t0 = srv.submit(cs[0].psf, cs[0].dirty, 1e-2, 1e-2, 10)
+        t1 = srv.submit(cs[1].psf, bad, 1e-2, 1e-2, 10)
+        t2 = srv.submit(cs[2].psf, cs[2].dirty, 1e-2, 1e-2, 10)
+        outs = {t: np.zeros((4, 32, 32), np.float32) for t in (t0, t2)}
+        rejected, done = False, set()
+        for _ in range(100):
+            srv.step()
+            if not rejected:
+                try:
+                    srv.poll(t1, None)
+                except pkg.MuffinError as e:
+                    assert e.status == 5
+                    rejected = True
+            for t in outs:
+                if t not in done and srv.poll(t, outs[t]):
+                    done.add(t)
+            if rejected and len(done) == 2:
+                break
+        assert rejected and len(done) == 2
+        with pytest.raises(pkg.MuffinError):
+            srv.poll(t1, None)                   # the ticket is released
+    for t, c in ((t0, cs[0]), (t2, cs[2])):
+        assert np.array_equal(outs[t], alone(pkg, torch, c, 1e-2, 1e-2, 10))
