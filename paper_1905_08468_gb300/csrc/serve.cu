@@ -271,8 +271,10 @@ muffin_status launch(muffin_server_s *S, bool *launched) {
     Pool &pl = S->pools[order[rank].second];
     if (pl.busy) continue;
     // the runs of consecutive slots that hold requests (free slots are not
-    // computed; admission fills the lowest free slot first)
-    int run = S->p.chunk;
+    // computed; admission fills the lowest free slot first).  A pool that
+    // is the only one with work while nothing is queued takes longer chunks
+    // (fewer host round trips), up to 4x
+    int run = (order.size() == 1 && S->queue.empty()) ? 4 * S->p.chunk : S->p.chunk;
     std::vector<std::pair<int, int>> runs;
     for (int b = 0; b < (int)pl.slot_req.size(); ++b)
       if (pl.slot_req[b] >= 0) {
@@ -410,13 +412,17 @@ muffin_status muffin_serve_step(muffin_server S, int32_t *active, int32_t *queue
     bool any_busy = false;
     for (const Pool &pl : S->pools) any_busy |= pl.busy;
     if (!any_busy) break;
+    // poll: spin for the first 200 us (a chunk boundary is often that
+    // close), then yield between polls
     for (bool ready = false; !ready;) {
       for (const Pool &pl : S->pools)
         if (pl.busy && cudaEventQuery(pl.done) != cudaErrorNotReady) ready = true;
       if (ready) break;
-      if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
+      const auto dt = std::chrono::steady_clock::now() - t0;
+      if (dt > std::chrono::seconds(60))
         return fail(MUFFIN_ETIMEOUT, "no pool finished its chunk within 60 s");
-      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      if (dt > std::chrono::microseconds(200))
+        std::this_thread::sleep_for(std::chrono::microseconds(10));
     }
   }
   if (active) {
