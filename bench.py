@@ -402,6 +402,7 @@ def run_convergence(args) -> None:
         return 10.0 * math.log10(sky_e / err), float((d.double() * g.double()).sum()) / nl
 
     inits = [tuple(float(v) for v in t.split(",")) for t in args.conv_inits.split(";")]
+    finals = {}
     eta = tuple(float(v) for v in args.conv_eta.split(","))
     runs = []
     t0 = time.perf_counter()
@@ -418,6 +419,7 @@ def run_convergence(args) -> None:
             snr, wm = metrics(x)
             curve.append({"k": k, "snr_db": snr, "wmse": wm})
         last = windows[-10:]
+        finals[f"x{len(runs)}"] = x.cpu().numpy()
         runs.append({"theta0": list(th0), "theta": list(th),
                      "sugar_last": [float(np.mean([w["sugar_mu"] for w in last])),
                                     float(np.mean([w["sugar_gamma"] for w in last]))],
@@ -436,6 +438,8 @@ def run_convergence(args) -> None:
            "config": {"workload": args.workload, "iters": args.conv_iters,
                       "window": args.window, "eta": list(eta), "eps": eps},
            "seconds": secs, "runs": runs}
+    if args.conv_save:
+        np.savez(args.conv_save, **finals)
     print(json.dumps(out), flush=True)
     plan.close()
 
@@ -479,6 +483,8 @@ def main() -> None:
     ap.add_argument("--conv-eta", default="1e-6,1e-5")
     ap.add_argument("--conv-iters", type=int, default=5000)
     ap.add_argument("--conv-chunk", type=int, default=250)
+    ap.add_argument("--conv-save", default="",
+                    help="save the final cube of every start to this .npz (for checks)")
     ap.add_argument("--serve-seed", type=int, default=4,
                     help="arrival-stream seed (request i draws its cube from seed 4000 + i)")
     ap.add_argument("--serve-rate", type=float, default=4.0,

@@ -409,6 +409,23 @@ MUFFIN_API muffin_status muffin_sure_global(muffin_plan plan, const float *dirty
                                             float *x, double *theta, muffin_sure_record *trace,
                                             muffin_info *info);
 
+/* ---- noise level ---------------------------------------------------------
+ * Sec. 3.1 takes the noise variances as known, or estimated in the image
+ * domain by robust statistics such as the median absolute deviation.  Reading
+ * (Donoho and Johnstone's wavelet MAD): for every band, the finest diagonal
+ * (high-high) band of the orthonormal Haar transform of the dirty image,
+ *   d = (y[2i][2j] - y[2i][2j+1] - y[2i+1][2j] + y[2i+1][2j+1]) / 2,
+ * sigma_l = median(|d - median(d)|) / 0.6744897501960817 (Phi^-1(3/4)); the
+ * median of an even count is the mean of the two middle values (exact order
+ * statistics on the FP32 coefficients).  noise_var [B][L] (host) receives
+ * sigma_l^2, the form muffin_sure_tune takes.  The estimate assumes the
+ * finest scale is dominated by noise; a sky whose convolved image has
+ * strong structure at the pixel scale biases it upwards.
+ *   dirty [B][L][n][n] (host or device).
+ * Errors: EINVAL (NULL argument), ENUMERIC (non-finite input), ECUDA. */
+MUFFIN_API muffin_status muffin_noise_mad(muffin_plan plan, const float *dirty,
+                                          double *noise_var);
+
 /* ---- checkpoint / resume ------------------------------------------------
  * The state blob holds the iterates (X, U, V, T of every chain), the
  * dirty-cube terms and theta; importing it into a plan created with the

@@ -298,6 +298,15 @@ class Plan:
         return ([(th[2 * c], th[2 * c + 1]) for c in range(B)],
                 [cube_trace(c) for c in range(B)], info)
 
+    def noise_mad(self, dirty) -> np.ndarray:
+        """Per-band noise variances sigma_l^2 of a dirty cube by the wavelet
+        MAD (``muffin_noise_mad``): [L] (or [B][L] for a batched plan)."""
+        keep = []
+        out = (ctypes.c_double * (self.B * self.L))()
+        native.check(self._lib.muffin_noise_mad(self._h, _ptr(dirty, keep), out))
+        v = np.array(out[:], dtype=np.float64)
+        return v if self.B == 1 else v.reshape(self.B, self.L)
+
     # -- convergence monitor
     def set_monitor(self, every: int = 0, objective: bool = False, rel_tol: float = 0.0,
                     off: bool = False) -> None:

@@ -176,7 +176,7 @@ cudaError_t theta_update(const ThetaUpdateArgs &a, cudaStream_t st);
 // ------------------------------------------------------------ monitor (monitor.cu)
 // Doubles of scratch the monitor reductions need for L bands: partials
 // [L][16][3], then the outputs state [L][3], residual [L], |W_s x| [L],
-// alpha |W_lambda x| [L], input scan [L][3].
+// alpha |W_lambda x| [L], input scan [L][3], noise estimate [L][3].
 size_t monitor_scratch_doubles(int L);
 // out[l][0..2] = {sum (x - xo)^2, sum xo^2 (sum x^2 when xo is NULL), number
 // of NaN/Inf entries of x} over the N values of band l (FP64)
@@ -191,6 +191,13 @@ cudaError_t mon_abs(const float *u, int L, size_t per_band, const float *alpha, 
                     size_t N, double *scratch, double *out, cudaStream_t st);
 // a *= h elementwise (complex FP64)
 cudaError_t mul_c64(double2 *a, const double2 *h, size_t count, cudaStream_t st);
+
+// ------------------------------------------------------------ noise (noise.cu)
+// MAD noise level of L images y [L][n][n]: var[l] = (MAD / Phi^-1(3/4))^2 of
+// the finest Haar high-high band; d_scratch holds L (n/2)^2 floats, med and
+// mad L doubles each
+cudaError_t noise_mad(const float *y, int n, int L, float *d_scratch, double *med,
+                      double *mad, double *var, cudaStream_t st);
 
 // ------------------------------------------------------------ wavelets (wavelet.cu)
 // Filters db1..db8: h, g taps (g[i] = (-1)^i h[2p-1-i]) uploaded to constant memory.

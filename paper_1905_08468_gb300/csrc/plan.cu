@@ -1420,6 +1420,18 @@ muffin_status muffin_objective(muffin_plan P, const float *dirty, const float *x
   return MUFFIN_OK;
 }
 
+muffin_status muffin_noise_mad(muffin_plan P, const float *dirty, double *noise_var) {
+  if (!P || !dirty || !noise_var) return fail(MUFFIN_EINVAL, "NULL argument");
+  muffin_status s = pi::enter(P);
+  if (s == MUFFIN_OK) s = fetch(P, dirty, P->stage_a, P->NL);
+  if (s == MUFFIN_OK) s = scan_input(P, P->stage_a, P->Lt, "the dirty cube");
+  if (s != MUFFIN_OK) return s;
+  double *med = P->mon + 57 * (size_t)P->Lt, *mad = med + P->Lt, *var = mad + P->Lt;
+  CK(noise_mad(P->stage_a, P->n, P->Lt, P->stage_b, med, mad, var, P->ws));
+  CK(cudaMemcpyAsync(noise_var, var, P->Lt * sizeof(double), cudaMemcpyDeviceToHost, P->ws));
+  return pi::leave(P, true);
+}
+
 muffin_status muffin_state_size(muffin_plan P, size_t *bytes) {
   if (!P || !bytes) return fail(MUFFIN_EINVAL, "NULL argument");
   size_t t = sizeof(BlobHeader) + 3 * P->B * sizeof(double);

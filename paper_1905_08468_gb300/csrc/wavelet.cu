@@ -967,7 +967,8 @@ cudaError_t analysis_all(const WaveArgs &w, const AnaArgs &base, cudaStream_t st
   a.last = (w.J == 1);
   a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[1];
   // the size-specialised kernels assume a level below (J > level)
-  cudaError_t e = (w.n == 1024 && w.J > 1) ? launch_ana<CH, MODE, true, 1024, 1024>(a, w.L, st, w.prof)
+  cudaError_t e = (w.n == 2048 && w.J > 1) ? launch_ana<CH, MODE, true, 2048, 2048>(a, w.L, st, w.prof)
+                  : (w.n == 1024 && w.J > 1) ? launch_ana<CH, MODE, true, 1024, 1024>(a, w.L, st, w.prof)
                   : (w.n == 512 && w.J > 1) ? launch_ana<CH, MODE, true, 512, 512>(a, w.L, st, w.prof)
                                             : launch_ana<CH, MODE, true>(a, w.L, st, w.prof);
   for (int j = 2; j <= w.J && e == cudaSuccess; ++j) {
@@ -975,7 +976,8 @@ cudaError_t analysis_all(const WaveArgs &w, const AnaArgs &base, cudaStream_t st
     a.in = w.scratch + w.lvl_off[j - 1];
     a.last = (j == w.J);
     a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[j];
-    if (j == 2 && w.J > 2 && w.n == 1024) e = launch_ana<CH, MODE, false, 1024, 512>(a, w.L * w.K, st, w.prof);
+    if (j == 2 && w.J > 2 && w.n == 2048) e = launch_ana<CH, MODE, false, 2048, 1024>(a, w.L * w.K, st, w.prof);
+    else if (j == 2 && w.J > 2 && w.n == 1024) e = launch_ana<CH, MODE, false, 1024, 512>(a, w.L * w.K, st, w.prof);
     else if (j == 2 && w.J > 2 && w.n == 512) e = launch_ana<CH, MODE, false, 512, 256>(a, w.L * w.K, st, w.prof);
     else e = launch_ana<CH, MODE, false>(a, w.L * w.K, st, w.prof);
   }

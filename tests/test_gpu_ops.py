@@ -1,6 +1,6 @@
 """Tier-1 parity: each CUDA operator against the FP64 oracle, element by
 element, over sizes that span several tiles, partial tiles and degenerate
-levels.  Tolerances (relative L2, FP32 kernels vs FP64): gradient 2e-6,
+levels.  Tolerances (relative L2, FP32 kernels vs FP64): gradient 1e-6,
 wavelet analysis/synthesis 1e-6, 3xTF32 DCT 2e-6."""
 import numpy as np
 import pytest
@@ -36,8 +36,9 @@ def test_gradient_matches_oracle(n, L):
         plan.op_gradient(dev(x, torch), g)
         e2 = rel_l2(host(g), ref_hth)
         assert plan.lipschitz == pytest.approx(convolution.lipschitz(hh), rel=1e-12)
-    assert e1 <= 2e-6, e1
-    assert e2 <= 2e-6, e2
+    print(f"gradient n={n}: {e1:.2e} (H^T H x - b), {e2:.2e} (H^T H x)")
+    assert e1 <= 1e-6, e1
+    assert e2 <= 1e-6, e2
 
 
 def test_gradient_host_buffers_equal_device_buffers():
@@ -131,7 +132,9 @@ def test_full_size_operators_sampled():
             hh = convolution.psf_spectrum(c.psf[l:l + 1])
             ref = convolution.HT(convolution.H(x[l:l + 1].astype(np.float64), hh)
                                  - c.dirty[l:l + 1].astype(np.float64), hh)
-            assert rel_l2(host(g[l:l + 1]), ref) <= 2e-6
+            eg = rel_l2(host(g[l:l + 1]), ref)
+            print(f"gradient 1024 band {l}: {eg:.2e}")
+            assert eg <= 1e-6
             ub = wavelets.Ws(x[l:l + 1].astype(np.float64), filter_bank(8), 3)
             assert rel_l2(host(u[l:l + 1]), ub) <= 1e-6
             # W_s^T W_s = 8 I: synthesis of the analysis returns 8 x

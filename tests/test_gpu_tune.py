@@ -109,18 +109,23 @@ def test_set_tuning_rejects_bad_values():
             assert e.value.status == 1
 
 
-def test_convergence_mode_reports_trajectories():
+def test_convergence_mode_reports_trajectories(tmp_path):
     """bench.py --convergence on a small cube: one record per window, SNR and
-    WMSE per chunk, finite values (the experiment itself is run at 256^2 x 32)."""
+    WMSE per chunk, finite values (the experiment itself is run at 256^2 x 32);
+    the final SNR and WMSE of every start equal the oracle's metrics (Sec.
+    4.1) of the saved cube against the true sky."""
     import json
     import os
     import subprocess
     import sys
+    from oracle import convolution, metrics
+    from synth import make_workload
     cuda()
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    save = str(tmp_path / "final.npz")
     r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--convergence",
                         "--workload", "c1_64x64x8", "--conv-iters", "120", "--conv-chunk", "60",
-                        "--conv-inits", "3e-2,1e-1;3e-4,1e-3"],
+                        "--conv-inits", "3e-2,1e-1;3e-4,1e-3", "--conv-save", save],
                        capture_output=True, text=True, cwd=root, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     out = json.loads(r.stdout.strip().splitlines()[-1])
@@ -130,3 +135,10 @@ def test_convergence_mode_reports_trajectories():
         assert all(np.isfinite(p["snr_db"]) and p["wmse"] > 0 for p in run["curve"])
         assert run["theta_every"][0][0] == 10
         assert all(t >= 1e-8 for t in run["theta"])
+    c = make_workload("c1_64x64x8")
+    hh = convolution.psf_spectrum(c.psf)
+    finals = np.load(save)
+    for i, run in enumerate(out["runs"]):
+        x = finals[f"x{i}"].astype(np.float64)
+        assert run["snr_db"] == pytest.approx(metrics.snr_db(c.sky, x), abs=1e-5)
+        assert run["wmse"] == pytest.approx(metrics.wmse(c.sky, x, hh), rel=1e-5)
