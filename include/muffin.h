@@ -409,6 +409,38 @@ MUFFIN_API muffin_status muffin_sure_global(muffin_plan plan, const float *dirty
                                             float *x, double *theta, muffin_sure_record *trace,
                                             muffin_info *info);
 
+/* ---- band-sharded iteration (Sec. 2.3) -----------------------------------
+ * The paper distributes an iteration of Algorithm 2 over nodes: the
+ * per-band work (eqs. grad2 .. stpu) on slaves that own bands, the per-pixel
+ * spectral work (eqs. vt, v, upt) on a master.  These two calls are the
+ * halves of one iteration for a band-sharded solve over several GPUs, one
+ * process per GPU: between them the caller transposes z = 2 x~ - x from
+ * band-sharded to pixel-sharded and t back (one all-to-all each way; the
+ * Python driver paper_1905_08468_gb300.sharded does this with
+ * torch.distributed).  With every band on one rank the pair computes exactly
+ * what muffin_solve's fused iteration does.
+ *
+ * muffin_shard_spatial: on a plan of this rank's bands (plain, one cube,
+ * Daubechies dictionary) whose state was started by muffin_solve(..., iters
+ * = 0) (dirty cube, X0, U = V = T = 0):
+ *   t     [L][n][n] (host or device): this rank's bands of T from the last
+ *         spectral step (zeros before the first);
+ *   z     [L][n][n] (host or device) receives z = 2 x~ - x; the plan's X
+ *         becomes x~;
+ *   mu, gamma, tau: the iteration's weights and primal step (the caller
+ *         computes tau from the whole cube's step condition).
+ * muffin_shard_spectral: on a plan created for every band of the cube
+ * (nbands = the full L; its pixel weights alpha are used, its PSF is not):
+ *   for the pixels [p0, p0 + npix) of the image, v <- sat(v + sigma gamma
+ *   alpha_n C z^n) and t^n = gamma alpha_n C^T v^n; z, v (in/out), t are
+ *   [L][npix] device arrays, 16-byte aligned, npix a multiple of 4.
+ * Errors: EINVAL, ESTATE (spatial step before the state was started), ECUDA. */
+MUFFIN_API muffin_status muffin_shard_spatial(muffin_plan plan, const float *t, float *z,
+                                              double mu, double gamma, double tau);
+MUFFIN_API muffin_status muffin_shard_spectral(muffin_plan plan, const float *z, float *v,
+                                               float *t, int64_t p0, int64_t npix,
+                                               double gamma);
+
 /* ---- noise level ---------------------------------------------------------
  * Sec. 3.1 takes the noise variances as known, or estimated in the image
  * domain by robust statistics such as the median absolute deviation.  Reading

@@ -56,6 +56,7 @@ __device__ __forceinline__ void cp_wait0() {
 
 struct DctKArgs {
   int n, L, Lp, inverse;
+  size_t npix;                // pixels per band (n * n, or a pixel block)
   int ctas_per_sm;            // persistent grid size (0: max resident)
   int B;                      // cubes; blockIdx.y selects the cube
   const float *a1hi, *a1lo;   // first product: C (or C^T for the inverse operator)
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
   const int Lp = a.Lp, L = a.L;
   float *zin = sm;                       // [CH][Lp][PP]
   float *vo = zin + CH * Lp * PP;        // [CH][Lp][PP]
-  const size_t N = (size_t)a.n * a.n;
+  const size_t N = a.npix;
   const size_t CS = (size_t)a.B * L * N;     // chain stride
   const size_t n0 = (size_t)blockIdx.x * PT;
   const int cube = blockIdx.y;
@@ -292,7 +293,7 @@ __global__ void __launch_bounds__(DT, 3) k_dct_small(DctKArgs a) {
   float *zb = cls + Lp * CP;              // [CH][Lp][PP] products' B operands
   float *vb = zb + CH * Lp * PP;          // [Lp][PP] old duals / t staging
   float *als = vb + Lp * PP;              // [PT] alpha of the tile
-  const size_t N = (size_t)a.n * a.n;
+  const size_t N = a.npix;
   const size_t CS = (size_t)a.B * L * N;  // chain stride
   const int tpc = (int)((N + PT - 1) / PT);
   const int ntiles = tpc * a.B;
@@ -443,7 +444,7 @@ cudaError_t launch_dct_small(const DctKArgs &a, cudaStream_t st, Prof *prof) {
     if (per_sm < 1) per_sm = 1;
     sm_seen = sm;
   }
-  const size_t N = (size_t)a.n * a.n;
+  const size_t N = a.npix;
   const size_t ntiles = ((N + PT - 1) / PT) * (size_t)a.B;
   const int use = a.ctas_per_sm > 0 ? std::min(a.ctas_per_sm, per_sm) : per_sm;
   const size_t grid = std::min(ntiles, (size_t)use * (size_t)sms);
@@ -462,7 +463,7 @@ cudaError_t launch_dct(const DctKArgs &a, cudaStream_t st, Prof *prof) {
                          200 * 1024);
     attr = true;
   }
-  const size_t N = (size_t)a.n * a.n;
+  const size_t N = a.npix;
   const double vox = (double)N * a.L * a.B;
   ProfScope ps(prof, MODE == WAVE_ITERATE ? "spectral_dual" : "spectral_op",
                MODE == WAVE_ITERATE ? CH * vox * 20.0 : vox * 8.0,
@@ -484,6 +485,7 @@ cudaError_t launch_dct_pt(const DctKArgs &a, cudaStream_t st, Prof *prof) {
 cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st) {
   DctKArgs a{};
   a.n = d.n; a.L = d.L; a.Lp = d.Lp; a.B = d.B > 0 ? d.B : 1;
+  a.npix = d.npix ? d.npix : (size_t)d.n * d.n;
   a.a1hi = d.chi; a.a1lo = d.clo; a.a2hi = d.cthi; a.a2lo = d.ctlo;
   a.alpha = d.alpha; a.sc = d.sc; a.ctas_per_sm = d.ctas_per_sm;
   a.xt = gr.xt; a.x = gr.x; a.v = gr.v; a.t = gr.t;
@@ -500,6 +502,7 @@ cudaError_t dct_op(const DctArgs &d, const float *in, float *out, int inverse,
                    cudaStream_t st) {
   DctKArgs a{};
   a.n = d.n; a.L = d.L; a.Lp = d.Lp; a.inverse = inverse; a.B = d.B > 0 ? d.B : 1;
+  a.npix = d.npix ? d.npix : (size_t)d.n * d.n;
   a.a1hi = inverse ? d.cthi : d.chi;
   a.a1lo = inverse ? d.ctlo : d.clo;
   a.in = in; a.out = out;

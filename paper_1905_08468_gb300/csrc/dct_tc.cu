@@ -54,6 +54,7 @@ constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) |
 
 struct TcArgs {
   int n, L, B;
+  size_t npix;                 // pixels per band (n * n, or a pixel block)
   const float *chi, *clo;      // [64][64] C, TF32 high / low part
   const float *cthi, *ctlo;    // [64][64] C^T
   const float *alpha;          // [B][n*n]
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
   const uint32_t sc_lo = (uint32_t)__cvta_generic_to_shared(cth[1]);
   const uint32_t sct_hi = (uint32_t)__cvta_generic_to_shared(cth[2]);
   const uint32_t sct_lo = (uint32_t)__cvta_generic_to_shared(cth[3]);
-  const size_t N = (size_t)a.n * a.n;
+  const size_t N = a.npix;
   const size_t CS = (size_t)a.B * TL * N;
   const int tpc = (int)((N + TM - 1) / TM);
   const int ntiles = tpc * a.B;
@@ -361,7 +362,7 @@ cudaError_t launch_tc(const TcArgs &a, cudaStream_t st, Prof *prof) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     attr = true;
   }
-  const size_t N = (size_t)a.n * a.n;
+  const size_t N = a.npix;
   const size_t ntiles = ((N + TM - 1) / TM) * (size_t)a.B;
   const size_t ctas = (ntiles + NG - 1) / NG;
   const size_t grid = ctas < (size_t)sms ? ctas : (size_t)sms;
@@ -377,6 +378,7 @@ cudaError_t dct_dual_tc(const DctArgs &d, const Group &gr, int *err, cudaStream_
   if (d.L != TL || d.Lp != TL) return cudaErrorInvalidValue;
   TcArgs a{};
   a.n = d.n; a.L = d.L; a.B = d.B > 0 ? d.B : 1;
+  a.npix = d.npix ? d.npix : (size_t)d.n * d.n;
   a.chi = d.chi; a.clo = d.clo; a.cthi = d.cthi; a.ctlo = d.ctlo;
   a.alpha = d.alpha; a.sc = d.sc;
   a.xt = gr.xt; a.x = gr.x; a.v = gr.v; a.t = gr.t; a.err = err;

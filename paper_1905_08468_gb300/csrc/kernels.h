@@ -191,6 +191,9 @@ cudaError_t mon_abs(const float *u, int L, size_t per_band, const float *alpha, 
                     size_t N, double *scratch, double *out, cudaStream_t st);
 // a *= h elementwise (complex FP64)
 cudaError_t mul_c64(double2 *a, const double2 *h, size_t count, cudaStream_t st);
+// z = 2 xt - x (the spectral step's input, Alg. 2 eq. vt)
+cudaError_t twice_minus(const float *xt, const float *x, float *z, size_t count,
+                        cudaStream_t st);
 
 // ------------------------------------------------------------ noise (noise.cu)
 // MAD noise level of L images y [L][n][n]: var[l] = (MAD / Phi^-1(3/4))^2 of
@@ -243,6 +246,7 @@ cudaError_t wavelet_synthesis_op(const WaveArgs &w, const float *u, float *x,
 // ------------------------------------------------------------ DCT (dct.cu)
 struct DctArgs {
   int n, L, Lp, C;         // L = bands per cube, Lp = L rounded up to 16
+  size_t npix;             // pixels per band: 0 = n * n; else a block of pixels
   int B;                   // cubes in the batch (band-major, cube after cube)
   const float *chi, *clo;  // [Lp][Lp] C split in TF32 hi + lo (zero padded)
   const float *cthi, *ctlo;// [Lp][Lp] C^T split

@@ -117,6 +117,13 @@ __global__ void k_mul_c64(double2 *__restrict__ a, const double2 *__restrict__ h
   }
 }
 
+__global__ void k_twice_minus(const float *__restrict__ xt, const float *__restrict__ x,
+                              float *__restrict__ z, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    z[i] = 2.f * xt[i] - x[i];
+}
+
 int bpb_for(size_t per_band) {
   const size_t g = (per_band + kThreads - 1) / kThreads;
   return (int)(g > kMaxBpb ? kMaxBpb : (g ? g : 1));
@@ -147,6 +154,14 @@ cudaError_t mon_abs(const float *u, int L, size_t per_band, const float *alpha, 
   const int bpb = bpb_for(per_band);
   k_mon_abs<<<dim3(bpb, L), kThreads, 0, st>>>(u, per_band, alpha, Lc, N, scratch);
   k_mon_final<<<L, 32, 0, st>>>(scratch, 1, bpb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t twice_minus(const float *xt, const float *x, float *z, size_t count,
+                        cudaStream_t st) {
+  const size_t g = (count + 255) / 256;
+  const int nb = (int)(g > 152 * 16 ? 152 * 16 : (g ? g : 1));
+  k_twice_minus<<<nb, 256, 0, st>>>(xt, x, z, count);
   return cudaGetLastError();
 }
 

@@ -1420,6 +1420,71 @@ muffin_status muffin_objective(muffin_plan P, const float *dirty, const float *x
   return MUFFIN_OK;
 }
 
+// ---------------------------------------------------------------- band-sharded iteration
+muffin_status muffin_shard_spatial(muffin_plan P, const float *t, float *z, double mu,
+                                   double gamma, double tau) {
+  if (!P || !t || !z) return fail(MUFFIN_EINVAL, "NULL argument");
+  if (P->B != 1 || P->p.sure || P->dict != 0)
+    return fail(MUFFIN_EINVAL, "the sharded spatial step needs a plain single-cube Daubechies plan");
+  if (!P->have_state || !P->have_b)
+    return fail(MUFFIN_ESTATE, "start the plan's state first (muffin_solve with iters = 0)");
+  if (!(mu >= 0) || !(gamma >= 0) || !(tau > 0) || !std::isfinite(tau))
+    return fail(MUFFIN_EINVAL, "mu, gamma >= 0 and tau > 0 required");
+  muffin_status s = pi::enter(P);
+  if (s != MUFFIN_OK) return s;
+  Group &g = P->grp[0];
+  s = fetch(P, t, g.t, P->NL);
+  if (s != MUFFIN_OK) return s;
+  DevScalars sc{mu, gamma, tau, P->p.sigma};
+  CK(cudaMemcpyAsync(P->sc, &sc, sizeof sc, cudaMemcpyHostToDevice, P->ws));
+  P->mu[0] = mu; P->gamma[0] = gamma;
+  Group h = g;
+  h.C = 1;
+  CK(launch_gradient(h.x, h.g, h.b, P->S, P->kspec, P->tw32, P->n, P->Lt, 1, P->ws, P->pp(),
+                     P->grad_chunk));
+  WaveArgs w = P->wave(1);
+  CK(wavelet_synthesis_prox(w, h, P->p.positivity, P->ws));
+  CK(wavelet_analysis_dual(w, h, P->ws));
+  float *zd = is_device_ptr(z) ? z : P->stage_b;
+  CK(twice_minus(h.xt, h.x, zd, P->NL, P->ws));
+  if (zd != z) s = store(P, zd, z, P->NL);
+  if (s != MUFFIN_OK) return s;
+  std::swap(g.x, g.xt);
+  P->k_done++;
+  return pi::leave(P, true);
+}
+
+muffin_status muffin_shard_spectral(muffin_plan P, const float *z, float *v, float *t,
+                                    int64_t p0, int64_t npix, double gamma) {
+  if (!P || !z || !v || !t) return fail(MUFFIN_EINVAL, "NULL argument");
+  if (P->B != 1) return fail(MUFFIN_EINVAL, "the sharded spectral step needs a single-cube plan");
+  if (p0 < 0 || npix < 4 || npix % 4 != 0 || (size_t)(p0 + npix) > P->N)
+    return fail(MUFFIN_EINVAL, "pixel block [%lld, %lld) must lie in the image, npix a multiple of 4",
+                (long long)p0, (long long)(p0 + npix));
+  if (!is_device_ptr(z) || !is_device_ptr(v) || !is_device_ptr(t))
+    return fail(MUFFIN_EINVAL, "z, v and t must be device arrays");
+  if ((reinterpret_cast<uintptr_t>(z) | reinterpret_cast<uintptr_t>(v) |
+       reinterpret_cast<uintptr_t>(t)) & 15)
+    return fail(MUFFIN_EINVAL, "z, v and t must be 16-byte aligned");
+  if (!(gamma >= 0)) return fail(MUFFIN_EINVAL, "gamma must be >= 0");
+  muffin_status s = pi::enter(P);
+  if (s != MUFFIN_OK) return s;
+  DevScalars sc{0.0, gamma, 0.0, P->p.sigma};
+  CK(cudaMemcpyAsync(P->sc, &sc, sizeof sc, cudaMemcpyHostToDevice, P->ws));
+  Group g{};
+  g.C = 1;
+  g.xt = const_cast<float *>(z);     // 2 z - z = z exactly: the kernel's 2 x~ - x
+  g.x = const_cast<float *>(z);
+  g.v = v;
+  g.t = t;
+  DctArgs d = P->dct(1);
+  d.npix = (size_t)npix;
+  d.alpha = P->alpha + p0;
+  d.B = 1;
+  CK(dct_dual(d, g, P->ws));
+  return pi::leave(P, true);
+}
+
 muffin_status muffin_noise_mad(muffin_plan P, const float *dirty, double *noise_var) {
   if (!P || !dirty || !noise_var) return fail(MUFFIN_EINVAL, "NULL argument");
   muffin_status s = pi::enter(P);

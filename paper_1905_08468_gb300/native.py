@@ -118,6 +118,10 @@ SIGNATURES = {
     "muffin_plan_weights_from_x0": (c_int32, [c_void_p, c_void_p, c_double, c_double,
                                               c_void_p, c_void_p]),
     "muffin_noise_mad": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(c_double)]),
+    "muffin_shard_spatial": (c_int32, [c_void_p, c_void_p, c_void_p, c_double, c_double,
+                                       c_double]),
+    "muffin_shard_spectral": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p,
+                                        ctypes.c_int64, ctypes.c_int64, c_double]),
     "muffin_state_size": (c_int32, [c_void_p, ctypes.POINTER(c_size_t)]),
     "muffin_state_export": (c_int32, [c_void_p, c_void_p, c_size_t]),
     "muffin_state_import": (c_int32, [c_void_p, c_void_p, c_size_t]),
