@@ -174,6 +174,8 @@ typedef struct {
   double ms_default;       /* one iteration of every chain group, default */
   double ms_best;          /* the same with the chosen variants */
   int32_t grad_chunk;      /* chosen gradient chunking (muffin_schedule) */
+  int32_t fft_radix;       /* chosen FFT plan */
+  int32_t group_order;     /* chosen kernel order of the ADA-PT groups */
 } muffin_tune_info;
 
 /* Times each candidate configuration on this plan's own buffers (a few
@@ -181,7 +183,8 @@ typedef struct {
  * with sure = 1, one plain group otherwise), keeps the fastest and caches it
  * per shape (n, bands, batch, chains, levels, bases, SM count, device name):
  * in process, and in the text file `cache_path` when it is not NULL (read
- * first, one line "muffin-tune-3 <key> <syn_packed> <dct_ctas> <tcgen05> <grad_chunk>"
+ * first, one line "muffin-tune-4 <key> <syn_packed> <dct_ctas> <tcgen05> <grad_chunk>
+ * <fft_radix> <group_order>"
  * appended per new shape; lines that do not parse are ignored).  The timing iterations overwrite the plan's iterate state: a
  * following solve or sure_tune must start cold (warm = 0; a warm call
  * returns MUFFIN_ESTATE), and captured graphs are rebuilt.  info may be NULL.
@@ -215,8 +218,8 @@ MUFFIN_API muffin_status muffin_plan_set_tuning(muffin_plan plan, int32_t syn_pa
                                                 int32_t dct_ctas_per_sm);
 
 /* Every launch choice of the per-iteration schedule (what the tuner picks).
- * None changes results except spectral_tcgen05 (FP32 rounding order, see
- * muffin_plan_set_spectral_kernel). */
+ * None changes results except spectral_tcgen05 and fft_radix (FP32 rounding
+ * order; both variants stay within the same tolerance of the oracle). */
 typedef struct {
   int32_t syn_packed;       /* synthesis row-pass variant bits, 0..3 */
   int32_t dct_ctas_per_sm;  /* mma.sync spectral grid, 0 = all resident */
@@ -225,6 +228,12 @@ typedef struct {
                                passes: 0 = each pass over all images of a
                                chain group; k > 0 = the three passes run k
                                images at a time, so the spectra stay in L2 */
+  int32_t fft_radix;        /* largest radix of the gradient's FFT plan: 16
+                               (default) or 8 (n >= 64; 1024 = 8.8.8.2 instead
+                               of 16.16.4); results agree to FP32 rounding */
+  int32_t group_order;      /* ADA-PT plans: 0 = one chain group's kernels
+                               after the other's, 1 = both groups phase by
+                               phase (identical results) */
 } muffin_schedule;
 
 /* Reads / sets the schedule (set drops captured graphs and the iterate

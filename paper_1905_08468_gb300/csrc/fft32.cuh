@@ -3,8 +3,10 @@
 // A batch of nb length-N sequences (N a power of two) lives in shared memory
 // in a padded layout (element i of a sequence at i + i/16, which makes the
 // stride-16 stores of the first stage bank-conflict free).  Every thread owns
-// VPT = min(16, N) complex values per stage: radix-16 stages while at least
-// 16 points remain, then one radix-8, -4 or -2 stage (N = 1024: 16, 16, 4).
+// VPT = min(16, N) complex values per stage: radix-RMAX stages while at
+// least RMAX points remain, then one smaller stage (RMAX = 16, the default
+// plan: N = 1024 is 16, 16, 4; RMAX = 8, the alternative plan the tuner may
+// pick: 8, 8, 8, 2, each thread running two radix-8 butterflies per stage).
 // A stage is the Stockham step  out[(j-k) R + k + r Ns] = DFT_R(w^{kr} in[j +
 // r N/R]); it reads, synchronises, then writes in place.  Stage twiddles
 // w = exp(-2 pi i k r / (Ns R)) come from a host-computed table laid out
@@ -162,46 +164,46 @@ __device__ __forceinline__ void fft_stage(float2 *d, int pitch, int nthr,
 
 __host__ __device__ constexpr int fft_vpt(int N) { return N < 16 ? N : 16; }
 
-template <int N, int NS, bool INV>
+template <int N, int NS, bool INV, int RMAX>
 __device__ __forceinline__ void fft_stages(float2 *d, int pitch, int nthr,
                                            const float2 *tw) {
   if constexpr (NS < N) {
     constexpr int REM = N / NS;
-    constexpr int R = REM >= 16 ? 16 : REM;
+    constexpr int R = REM >= RMAX ? RMAX : REM;
     fft_stage<N, NS, R, fft_vpt(N), INV>(d, pitch, nthr, tw);
-    fft_stages<N, NS * R, INV>(d, pitch, nthr, tw + (NS > 1 ? (R - 1) * NS : 0));
+    fft_stages<N, NS * R, INV, RMAX>(d, pitch, nthr, tw + (NS > 1 ? (R - 1) * NS : 0));
   }
 }
 
 // In-place transform of nb sequences (sequence s at d + s * pitch, padded
 // layout).  Needs nb * N / fft_vpt(N) <= blockDim.x.  Caller syncs before.
-template <int N, bool INV>
+template <int N, bool INV, int RMAX = 16>
 __device__ __forceinline__ void fft_inplace(float2 *d, int nb, int pitch,
                                             const float2 *tws) {
-  fft_stages<N, 1, INV>(d, pitch, nb * N / fft_vpt(N), tws);
+  fft_stages<N, 1, INV, RMAX>(d, pitch, nb * N / fft_vpt(N), tws);
 }
 
 // number of complex entries of the stage twiddle tables for N
-inline int fft_table_len(int N) {
+inline int fft_table_len(int N, int rmax = 16) {
   if (N < 16) return 1;
   int Ns = 1, len = 0;
   while (Ns < N) {
     const int rem = N / Ns;
-    const int R = rem >= 16 ? 16 : rem;
+    const int R = rem >= rmax ? rmax : rem;
     if (Ns > 1) len += (R - 1) * Ns;
     Ns *= R;
   }
   return len > 0 ? len : 1;
 }
 
-// fills tab[fft_table_len(N)] in the order the stages read it
-inline void fft_tables(int N, float2 *tab) {
+// fills tab[fft_table_len(N, rmax)] in the order the stages read it
+inline void fft_tables(int N, float2 *tab, int rmax = 16) {
   const double pi = 3.14159265358979323846;
   if (N < 16) { tab[0] = make_float2(1.f, 0.f); return; }
   int Ns = 1, off = 0;
   while (Ns < N) {
     const int rem = N / Ns;
-    const int R = rem >= 16 ? 16 : rem;
+    const int R = rem >= rmax ? rmax : rem;
     if (Ns > 1) {
       for (int r = 1; r < R; ++r)
         for (int k = 0; k < Ns; ++k) {

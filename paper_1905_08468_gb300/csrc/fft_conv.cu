@@ -35,7 +35,7 @@ __device__ __forceinline__ void load_tw(float2 *dst, const float2 *__restrict__ 
   for (int i = threadIdx.x; i < tlen; i += blockDim.x) dst[i] = src[i];
 }
 
-template <int NN>
+template <int NN, int RMAX>
 __global__ void __launch_bounds__(kThreads)
 k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S,
            const float2 *__restrict__ tw, int tlen, int img0) {
@@ -68,7 +68,7 @@ k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S,
     if (tid + u * kThreads < nq * n) d[sb + q * pitch + fpad(c)] = v[u];
   }
   __syncthreads();
-  fft_inplace<NN, false>(d, nq, pitch, tws);
+  fft_inplace<NN, false, RMAX>(d, nq, pitch, tws);
   float4 *Si = reinterpret_cast<float4 *>(S + (size_t)img * nh * n);
   for (int i = threadIdx.x; i < nh * nq; i += blockDim.x) {
     const int k = i / nq, q = i - k * nq;
@@ -83,7 +83,7 @@ k_rows_fwd(const float *__restrict__ x, float2 *__restrict__ S,
   }
 }
 
-template <int NN>
+template <int NN, int RMAX>
 __global__ void __launch_bounds__(kThreads)
 k_cols(float2 *__restrict__ S, const float *__restrict__ kspec, int L,
        const float2 *__restrict__ tw, int tlen, int img0) {
@@ -118,7 +118,7 @@ k_cols(float2 *__restrict__ S, const float *__restrict__ kspec, int L,
         d[sb + ((kThreads * u) / n) * pitch + fpad((kThreads * u) % n)] = v[u];
   }
   __syncthreads();
-  fft_inplace<NN, false>(d, ncol, pitch, tws);
+  fft_inplace<NN, false, RMAX>(d, ncol, pitch, tws);
 #pragma unroll
   for (int u = 0; u < KPT; ++u) {
     if (c0 + (kThreads * u) / n < ncol) {
@@ -128,14 +128,14 @@ k_cols(float2 *__restrict__ S, const float *__restrict__ kspec, int L,
     }
   }
   __syncthreads();
-  fft_inplace<NN, true>(d, ncol, pitch, tws);
+  fft_inplace<NN, true, RMAX>(d, ncol, pitch, tws);
 #pragma unroll
   for (int u = 0; u < KPT; ++u)
     if (c0 + (kThreads * u) / n < ncol)
       Si[kThreads * u] = d[sb + ((kThreads * u) / n) * pitch + fpad((kThreads * u) % n)];
 }
 
-template <int NN>
+template <int NN, int RMAX>
 __global__ void __launch_bounds__(kThreads)
 k_rows_inv(const float2 *__restrict__ S, float *__restrict__ g,
            const float *__restrict__ bdata, int L,
@@ -157,7 +157,7 @@ k_rows_inv(const float2 *__restrict__ S, float *__restrict__ g,
       d[q * pitch + fpad(n - k)] = make_float2(v.x + v.w, v.z - v.y);  // conj Xa + i conj Xb
   }
   __syncthreads();
-  fft_inplace<NN, true>(d, nq, pitch, tws);
+  fft_inplace<NN, true, RMAX>(d, nq, pitch, tws);
   const bool sub = (bdata != nullptr) && (gimg < L);
   // element u of the thread: row pair tid / n + 256 u / n (see k_rows_fwd)
   const int tid = threadIdx.x;
@@ -254,7 +254,7 @@ inline int grid_for(size_t count) {
 }
 
 
-template <int NN>
+template <int NN, int RMAX>
 cudaError_t gradient_n(const float *x, float *g, const float *b, float2 *S,
                        const float *kspec, const float2 *tw, int L, int C,
                        cudaStream_t st, Prof *prof, int chunk) {
@@ -264,14 +264,14 @@ cudaError_t gradient_n(const float *x, float *g, const float *b, float2 *S,
   const int CB = seqs_per_cta(n);                   // columns per CTA
   const int nh = (n >> 1) + 1;
   const int pitch = n + (n >> 4);
-  const int tlen = fft_table_len(n);
+  const int tlen = fft_table_len(n, RMAX);
   const size_t smr = ((size_t)(RB / 2) * pitch + tlen) * sizeof(float2);
   const size_t smc = ((size_t)CB * pitch + tlen) * sizeof(float2);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_rows_fwd<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_rows_inv<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_cols<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_rows_fwd<NN, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_rows_inv<NN, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_cols<NN, RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   const double img = (double)n * n, spec = (double)nh * n * 8.0;
@@ -289,17 +289,17 @@ cudaError_t gradient_n(const float *x, float *g, const float *b, float2 *S,
     {
       ProfScope ps(prof, "grad_rows_fwd", nimg * (img * 4.0 + spec),
                    nimg * (n / 2.0) * fft, st);
-      k_rows_fwd<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(x, S, tw, tlen, i0);
+      k_rows_fwd<NN, RMAX><<<dim3(n / RB, nimg), kThreads, smr, st>>>(x, S, tw, tlen, i0);
     }
     {
       ProfScope ps(prof, "grad_cols", nimg * 2.0 * spec + (double)nimg * nh * n * 4.0,
                    nimg * (double)nh * 2.0 * fft, st);
-      k_cols<NN><<<dim3((nh + CB - 1) / CB, nimg), kThreads, smc, st>>>(S, kspec, L, tw, tlen, i0);
+      k_cols<NN, RMAX><<<dim3((nh + CB - 1) / CB, nimg), kThreads, smc, st>>>(S, kspec, L, tw, tlen, i0);
     }
     {
       ProfScope ps(prof, "grad_rows_inv", nimg * (spec + img * 4.0) + nb * img * 4.0,
                    nimg * (n / 2.0) * fft, st);
-      k_rows_inv<NN><<<dim3(n / RB, nimg), kThreads, smr, st>>>(S, g, b, L, tw, tlen, i0);
+      k_rows_inv<NN, RMAX><<<dim3(n / RB, nimg), kThreads, smr, st>>>(S, g, b, L, tw, tlen, i0);
     }
   }
   return cudaGetLastError();
@@ -309,25 +309,33 @@ cudaError_t gradient_n(const float *x, float *g, const float *b, float2 *S,
 
 cudaError_t launch_gradient(const float *x, float *g, const float *b,
                             float2 *S, const float *kspec, const float2 *tw,
-                            int n, int L, int C, cudaStream_t st, Prof *prof, int chunk) {
+                            int n, int L, int C, cudaStream_t st, Prof *prof, int chunk,
+                            int radix) {
+  const bool r8 = radix == 8 && n >= 64;   // the alternative plan exists from n = 64
+#define MUFFIN_GRAD(NN)                                                                    \
+  return r8 ? gradient_n<NN, 8>(x, g, b, S, kspec, tw, L, C, st, prof, chunk)              \
+            : gradient_n<NN, 16>(x, g, b, S, kspec, tw, L, C, st, prof, chunk)
+#define MUFFIN_GRAD16(NN) return gradient_n<NN, 16>(x, g, b, S, kspec, tw, L, C, st, prof, chunk)
   switch (n) {
-    case 2: return gradient_n<2>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
-    case 4: return gradient_n<4>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
-    case 8: return gradient_n<8>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
-    case 16: return gradient_n<16>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
-    case 32: return gradient_n<32>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
-    case 64: return gradient_n<64>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
-    case 128: return gradient_n<128>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
-    case 256: return gradient_n<256>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
-    case 512: return gradient_n<512>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
-    case 1024: return gradient_n<1024>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
-    case 2048: return gradient_n<2048>(x, g, b, S, kspec, tw, L, C, st, prof, chunk);
+    case 2: MUFFIN_GRAD16(2);
+    case 4: MUFFIN_GRAD16(4);
+    case 8: MUFFIN_GRAD16(8);
+    case 16: MUFFIN_GRAD16(16);
+    case 32: MUFFIN_GRAD16(32);
+    case 64: MUFFIN_GRAD(64);
+    case 128: MUFFIN_GRAD(128);
+    case 256: MUFFIN_GRAD(256);
+    case 512: MUFFIN_GRAD(512);
+    case 1024: MUFFIN_GRAD(1024);
+    case 2048: MUFFIN_GRAD(2048);
+#undef MUFFIN_GRAD
+#undef MUFFIN_GRAD16
     default: return cudaErrorInvalidValue;
   }
 }
 
-int fft32_table_len(int n) { return fft_table_len(n); }
-void fft32_tables(int n, float2 *tab) { fft_tables(n, tab); }
+int fft32_table_len(int n, int radix) { return fft_table_len(n, radix); }
+void fft32_tables(int n, float2 *tab, int radix) { fft_tables(n, tab, radix); }
 
 cudaError_t fft2d_c64(double2 *data, double2 *tmp, int n, int nimg,
                       bool inverse, const double2 *tw64, cudaStream_t st) {

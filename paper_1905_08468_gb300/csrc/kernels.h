@@ -95,14 +95,17 @@ int set_last_error_code(int s, const char *msg);
 // chunk > 0: the three passes run over `chunk` images at a time (S then
 // needs room for chunk images only and stays in L2 between the passes);
 // chunk <= 0: each pass over all images at once.
+// radix 16 (default) or 8 (n >= 64): the largest radix of the FFT plan; tw
+// must hold that plan's twiddle tables (fft32_tables with the same radix).
 cudaError_t launch_gradient(const float *x, float *g, const float *b,
                             float2 *S, const float *kspec, const float2 *tw,
                             int n, int L, int C, cudaStream_t st,
-                            Prof *prof = nullptr, int chunk = 0);
+                            Prof *prof = nullptr, int chunk = 0, int radix = 16);
 
-// Stage twiddle tables of the FP32 gradient FFT for side n (host side).
-int fft32_table_len(int n);
-void fft32_tables(int n, float2 *tab);
+// Stage twiddle tables of the FP32 gradient FFT for side n (host side), for
+// the plan whose largest radix is `radix`.
+int fft32_table_len(int n, int radix = 16);
+void fft32_tables(int n, float2 *tab, int radix = 16);
 
 // FP64 helpers used when a plan or a call is set up.
 // In-place 2D DFT of nimg complex n x n images; inverse is unnormalised.

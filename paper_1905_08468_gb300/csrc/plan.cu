@@ -184,8 +184,8 @@ muffin_status iterate_kernels(muffin_plan P, const Group &g, int c0, int c1) {
     d.alpha += (size_t)c0 * P->N;
     d.sc += c0;
   }
-  CK(launch_gradient(h.x, h.g, h.b, P->S, kspec, P->tw32, P->n, Lv, g.C, P->ws,
-                     P->pp(), P->grad_chunk));
+  CK(launch_gradient(h.x, h.g, h.b, P->S, kspec, P->tw(), P->n, Lv, g.C, P->ws,
+                     P->pp(), P->grad_chunk, P->fft_radix));
   w.L = Lv;
   CK(wavelet_synthesis_prox(w, h, P->p.positivity, P->ws));
   CK(wavelet_analysis_dual(w, h, P->ws));
@@ -193,6 +193,14 @@ muffin_status iterate_kernels(muffin_plan P, const Group &g, int c0, int c1) {
   CK(dct_dual(d, h, P->ws));
   return MUFFIN_OK;
 }
+
+// one iteration of every chain group: with ADA-PT the two groups (on y and
+// on y_bar) are independent within an iteration, so their kernels run either
+// group after group (group_order 0) or phase by phase (1: both gradients,
+// both syntheses, both analyses, both spectral steps).  The scratch (FFT
+// spectra, LL approximations) is consumed within each call, so both orders
+// compute identical results.
+muffin_status iterate_groups(muffin_plan P);
 
 // one iteration of group g; a plain group (C = 1) may be restricted to some
 // runs [c0, c1) of cubes (the serving pools skip their free slots)
@@ -207,6 +215,25 @@ muffin_status iterate_group(muffin_plan P, Group &g,
     if (s != MUFFIN_OK) return s;
   }
   float *t = g.x; g.x = g.xt; g.xt = t;
+  return MUFFIN_OK;
+}
+
+muffin_status iterate_groups(muffin_plan P) {
+  if (!P->p.sure || P->group_order == 0) {
+    muffin_status s = iterate_group(P, P->grp[0]);
+    if (s == MUFFIN_OK && P->p.sure) s = iterate_group(P, P->grp[1]);
+    return s;
+  }
+  Group *gs[2] = {&P->grp[0], &P->grp[1]};
+  for (Group *g : gs)
+    CK(launch_gradient(g->x, g->g, g->b, P->S, P->kspec, P->tw(), P->n, P->Lt, g->C, P->ws,
+                       P->pp(), P->grad_chunk, P->fft_radix));
+  for (Group *g : gs) CK(wavelet_synthesis_prox(P->wave(g->C), *g, P->p.positivity, P->ws));
+  for (Group *g : gs) CK(wavelet_analysis_dual(P->wave(g->C), *g, P->ws));
+  for (Group *g : gs) {
+    CK(dct_dual(P->dct(g->C), *g, P->ws));
+    std::swap(g->x, g->xt);
+  }
   return MUFFIN_OK;
 }
 
@@ -292,7 +319,8 @@ muffin_status plan_alloc_init(muffin_plan P, const float *alpha, const float *be
   CK(P->alloc(&P->w64a, NL));
   CK(P->alloc(&P->w64b, NL));
   CK(P->alloc(&P->kspec, (size_t)Lt * nh * n));
-  CK(P->alloc(&P->tw32, (size_t)fft32_table_len(n)));
+  P->tw_len16 = fft32_table_len(n, 16);
+  CK(P->alloc(&P->tw32, (size_t)P->tw_len16 + fft32_table_len(n, 8)));
   CK(P->alloc(&P->tw64, (size_t)n));
   const size_t LL2 = (size_t)P->Lp * P->Lp;
   CK(P->alloc(&P->chi, LL2));
@@ -344,8 +372,9 @@ muffin_status plan_alloc_init(muffin_plan P, const float *alpha, const float *be
     const double a = -2.0 * pi * k / n;
     t64[k] = make_double2(std::cos(a), std::sin(a));
   }
-  std::vector<float2> t32(fft32_table_len(n));
-  fft32_tables(n, t32.data());
+  std::vector<float2> t32((size_t)P->tw_len16 + fft32_table_len(n, 8));
+  fft32_tables(n, t32.data(), 16);
+  fft32_tables(n, t32.data() + P->tw_len16, 8);
   CK(cudaMemcpyAsync(P->tw32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice, P->ws));
   CK(cudaMemcpyAsync(P->tw64, t64.data(), n * sizeof(double2), cudaMemcpyHostToDevice, P->ws));
 
@@ -414,8 +443,8 @@ muffin_status window_end(muffin_plan P, const muffin_sure_params *sp) {
   Group &g = P->grp[0];
   Group g0 = g;
   g0.C = 1;
-  CK(launch_gradient(g0.x, g0.g, g0.b, P->S, P->kspec, P->tw32, P->n, P->Lt, 1, P->ws,
-                     P->pp(), P->grad_chunk));
+  CK(launch_gradient(g0.x, g0.g, g0.b, P->S, P->kspec, P->tw(), P->n, P->Lt, 1, P->ws,
+                     P->pp(), P->grad_chunk, P->fft_radix));
   SureStatsArgs sa{};
   sa.grad = g.g; sa.x = g.x; sa.xb = P->grp[1].x; sa.b = P->b; sa.htd = P->htd;
   sa.wband = P->wband; sa.n = P->n; sa.L = P->Lt;
@@ -570,9 +599,7 @@ muffin_status enter(muffin_plan P) {
 }
 
 muffin_status iterate_all(muffin_plan P) {
-  muffin_status s = iterate_group(P, P->grp[0]);
-  if (s == MUFFIN_OK && P->p.sure) s = iterate_group(P, P->grp[1]);
-  return s;
+  return iterate_groups(P);
 }
 
 void drop_graphs_and_state(muffin_plan P) {
@@ -722,7 +749,7 @@ size_t estimate_bytes(const muffin_params *p) {
   if (p->dictionary == 1) ll = 2 * C * Lt * N;
   else
     for (int j = 1; j < p->levels; ++j) ll += C * Lt * K * (n >> j) * (n >> j);
-  size_t b = 3 * NL * 16 + Lt * nh * n * 4 + (size_t)fft32_table_len((int)n) * 8 + n * 16 +
+  size_t b = 3 * NL * 16 + Lt * nh * n * 4 + (size_t)(fft32_table_len((int)n, 16) + fft32_table_len((int)n, 8)) * 8 + n * 16 +
              4 * Lp * Lp * 4 + B * N * 4 + Lt * 4 + B * sizeof(DevScalars) + B * 32 + 4 + 4 +
              (kRedSure + 65 * Lt + 6 * (Lt > 4096 ? Lt : 4096)) * 8 + Lt * 8 +
              C * Lt * nh * n * 8 + (ll ? ll : 1) * 4 + 3 * NL * 4 +
@@ -1056,8 +1083,7 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
         const Group c0 = P->grp[0], c1 = P->grp[1];
         s = capture(P, &P->gsure[par], [&]() -> muffin_status {
           for (int q = 0; q < sp->window; ++q) {
-            muffin_status r = iterate_group(P, P->grp[0]);
-            if (r == MUFFIN_OK) r = iterate_group(P, P->grp[1]);
+            muffin_status r = iterate_groups(P);
             if (r != MUFFIN_OK) return r;
           }
           return window_end(P, sp);
@@ -1081,8 +1107,7 @@ muffin_status muffin_sure_tune(muffin_plan P, const float *dirty,
       if (stop) break;
       continue;
     }
-    s = iterate_group(P, P->grp[0]);
-    if (s == MUFFIN_OK) s = iterate_group(P, P->grp[1]);
+    s = iterate_groups(P);
     if (s != MUFFIN_OK) return s;
     ++it;
     P->k_done++;
@@ -1440,8 +1465,8 @@ muffin_status muffin_shard_spatial(muffin_plan P, const float *t, float *z, doub
   P->mu[0] = mu; P->gamma[0] = gamma;
   Group h = g;
   h.C = 1;
-  CK(launch_gradient(h.x, h.g, h.b, P->S, P->kspec, P->tw32, P->n, P->Lt, 1, P->ws, P->pp(),
-                     P->grad_chunk));
+  CK(launch_gradient(h.x, h.g, h.b, P->S, P->kspec, P->tw(), P->n, P->Lt, 1, P->ws, P->pp(),
+                     P->grad_chunk, P->fft_radix));
   WaveArgs w = P->wave(1);
   CK(wavelet_synthesis_prox(w, h, P->p.positivity, P->ws));
   CK(wavelet_analysis_dual(w, h, P->ws));
@@ -1582,7 +1607,8 @@ muffin_status muffin_op_gradient(muffin_plan P, const float *x, const float *dir
   }
   s = fetch(P, x, P->op_in, P->NL);
   if (s != MUFFIN_OK) return s;
-  CK(launch_gradient(P->op_in, P->op_out, bb, P->S, P->kspec, P->tw32, P->n, P->Lt, 1, P->ws));
+  CK(launch_gradient(P->op_in, P->op_out, bb, P->S, P->kspec, P->tw(), P->n, P->Lt, 1, P->ws,
+                     nullptr, 0, P->fft_radix));
   s = store(P, P->op_out, g, P->NL);
   if (s != MUFFIN_OK) return s;
   return pi::leave(P, true);

@@ -82,6 +82,9 @@ struct muffin_plan_s {
   int dct_ctas = 0;       // spectral kernel CTAs per SM (0: all resident)
   int dct_tc = 0;         // spectral step on tcgen05 (L = 64)
   int grad_chunk = 0;     // images per pass of the gradient FFTs (0: all at once)
+  int fft_radix = 16;     // largest radix of the gradient FFT plan (16, or 8 from n = 64)
+  int group_order = 0;    // ADA-PT: 0 group after group, 1 phase-interleaved (see iterate_all)
+  int tw_len16 = 0;       // entries of the radix-16 twiddle tables (the radix-8 ones follow)
   int inject_timeout = 0; // test hook (muffin_plan_inject_timeout)
   int *kerr = nullptr;    // device flag: a bounded tensor-core wait gave up
   // (parity, runs of cubes) -> two plain iterations
@@ -95,6 +98,8 @@ struct muffin_plan_s {
   long long k_done = 0;
 
   muffin::Prof *pp() { return profiling ? &prof : nullptr; }
+  // twiddle tables of the selected FFT plan
+  const float2 *tw() const { return fft_radix == 8 && n >= 64 ? tw32 + tw_len16 : tw32; }
 
   template <typename T>
   cudaError_t alloc(T **ptr, size_t count) {

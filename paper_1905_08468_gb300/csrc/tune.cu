@@ -24,6 +24,8 @@ struct Choice {
   int dct_ctas = 0;
   int dct_tc = 0;      // spectral step on tcgen05 (64-band plans)
   int grad_chunk = 0;  // images per pass of the gradient FFTs (0: all)
+  int fft_radix = 16;  // largest radix of the gradient FFT plan
+  int group_order = 0; // ADA-PT groups: 0 one after the other, 1 phase by phase
 };
 
 std::mutex g_mu;
@@ -45,22 +47,27 @@ std::string shape_key(muffin_plan P) {
   return buf;
 }
 
-// the last line "muffin-tune-3 <key> <syn_packed> <dct_ctas> <dct_tc> <grad_chunk>"
-// with this key
+// the last line "muffin-tune-4 <key> <syn_packed> <dct_ctas> <dct_tc> <grad_chunk>
+// <fft_radix> <group_order>" with this key
 bool file_lookup(const char *path, const std::string &key, Choice *c) {
   FILE *f = std::fopen(path, "r");
   if (!f) return false;
   char line[512], tag[32], k[400];
   bool found = false;
   while (std::fgets(line, sizeof line, f)) {
-    int a = 0, b = 0, t = 0, g = 0;
-    if (std::sscanf(line, "%31s %399s %d %d %d %d", tag, k, &a, &b, &t, &g) != 6) continue;
-    if (std::strcmp(tag, "muffin-tune-3") != 0 || key != k) continue;
-    if (a < 0 || a > 3 || b < 0 || t < 0 || t > 1 || g < 0) continue;
+    int a = 0, b = 0, t = 0, g = 0, r = 0, o = 0;
+    if (std::sscanf(line, "%31s %399s %d %d %d %d %d %d", tag, k, &a, &b, &t, &g, &r, &o) != 8)
+      continue;
+    if (std::strcmp(tag, "muffin-tune-4") != 0 || key != k) continue;
+    if (a < 0 || a > 3 || b < 0 || t < 0 || t > 1 || g < 0 || (r != 8 && r != 16) ||
+        o < 0 || o > 1)
+      continue;
     c->syn_packed = a;
     c->dct_ctas = b;
     c->dct_tc = t;
     c->grad_chunk = g;
+    c->fft_radix = r;
+    c->group_order = o;
     found = true;
   }
   std::fclose(f);
@@ -70,8 +77,8 @@ bool file_lookup(const char *path, const std::string &key, Choice *c) {
 void file_append(const char *path, const std::string &key, const Choice &c) {
   FILE *f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "muffin-tune-3 %s %d %d %d %d\n", key.c_str(), c.syn_packed, c.dct_ctas,
-               c.dct_tc, c.grad_chunk);
+  std::fprintf(f, "muffin-tune-4 %s %d %d %d %d %d %d\n", key.c_str(), c.syn_packed, c.dct_ctas,
+               c.dct_tc, c.grad_chunk, c.fft_radix, c.group_order);
   std::fclose(f);
 }
 
@@ -80,6 +87,8 @@ void apply(muffin_plan P, const Choice &c) {
   P->dct_ctas = c.dct_ctas;
   P->dct_tc = P->L == 64 ? c.dct_tc : 0;
   P->grad_chunk = c.grad_chunk;
+  P->fft_radix = P->n >= 64 ? c.fft_radix : 16;
+  P->group_order = P->p.sure ? c.group_order : 0;
 }
 
 // mean time of one iteration of every chain group with choice c
@@ -162,6 +171,22 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
     ++cand;
     if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
   }
+  if (P->n >= 64 && s == MUFFIN_OK) {   // the radix-8 FFT plan
+    Choice c = *best;
+    c.fft_radix = 8;
+    double t = 0.0;
+    s = time_choice(P, c, reps, e0, e1, &t);
+    ++cand;
+    if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
+  }
+  if (P->p.sure && s == MUFFIN_OK) {     // the chain groups phase by phase
+    Choice c = *best;
+    c.group_order = 1;
+    double t = 0.0;
+    s = time_choice(P, c, reps, e0, e1, &t);
+    ++cand;
+    if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
+  }
   if (s == MUFFIN_OK) s = muffin::pi::leave(P, true);
   P->profiling = was_profiling;
   cudaEventDestroy(e0);
@@ -214,13 +239,16 @@ muffin_status muffin_plan_get_schedule(muffin_plan P, muffin_schedule *s) {
   s->dct_ctas_per_sm = P->dct_ctas;
   s->spectral_tcgen05 = P->dct_tc;
   s->grad_chunk = P->grad_chunk;
+  s->fft_radix = P->fft_radix;
+  s->group_order = P->group_order;
   return MUFFIN_OK;
 }
 
 muffin_status muffin_plan_set_schedule(muffin_plan P, const muffin_schedule *s) {
   if (!P || !s) return fail(MUFFIN_EINVAL, "NULL argument");
   if (s->syn_packed < 0 || s->syn_packed > 3 || s->dct_ctas_per_sm < 0 || s->grad_chunk < 0 ||
-      (s->spectral_tcgen05 != 0 && s->spectral_tcgen05 != 1))
+      (s->spectral_tcgen05 != 0 && s->spectral_tcgen05 != 1) ||
+      (s->fft_radix != 16 && s->fft_radix != 8) || s->group_order < 0 || s->group_order > 1)
     return fail(MUFFIN_EINVAL, "schedule value out of range");
   if (s->spectral_tcgen05 && P->L != 64)
     return fail(MUFFIN_EINVAL, "the tcgen05 spectral kernel needs 64 bands (plan has %d)", P->L);
@@ -229,6 +257,8 @@ muffin_status muffin_plan_set_schedule(muffin_plan P, const muffin_schedule *s) 
   P->dct_ctas = s->dct_ctas_per_sm;
   P->dct_tc = s->spectral_tcgen05;
   P->grad_chunk = s->grad_chunk;
+  P->fft_radix = P->n >= 64 ? s->fft_radix : 16;
+  P->group_order = P->p.sure ? s->group_order : 0;
   return MUFFIN_OK;
 }
 
@@ -256,6 +286,8 @@ muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin
       info->dct_ctas_per_sm = c.dct_ctas;
       info->spectral_tcgen05 = P->dct_tc;
       info->grad_chunk = P->grad_chunk;
+      info->fft_radix = P->fft_radix;
+      info->group_order = P->group_order;
       info->from_cache = 1;
     }
     return MUFFIN_OK;
@@ -275,6 +307,8 @@ muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin
     info->dct_ctas_per_sm = c.dct_ctas;
     info->spectral_tcgen05 = P->dct_tc;
     info->grad_chunk = P->grad_chunk;
+    info->fft_radix = P->fft_radix;
+    info->group_order = P->group_order;
     info->from_cache = 0;
   }
   return MUFFIN_OK;

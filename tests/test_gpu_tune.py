@@ -35,6 +35,54 @@ def test_plain_variants_bit_identical(n, L):
         assert torch.equal(_solve(pkg, torch, c, 0, 0, grad_chunk=chunk), ref), chunk
 
 
+def test_fft_radix_plans_agree_and_match_oracle():
+    """The radix-8 FFT plan (n >= 64) against the default radix-16 plan: same
+    operator up to FP32 rounding, both within the gradient tolerance of the
+    oracle, and a plain solve within the cube tolerance."""
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    from oracle import convolution
+    from tests.gpu_util import host, rel_l2
+    for n, L in ((64, 3), (256, 2), (1024, 1)):
+        c = make_cube(n, L, max(2, n // 4), 1, 30 * n, seed=860 + n)
+        x = np.random.default_rng(n).uniform(0, 1, (L, n, n)).astype(np.float32)
+        hh = convolution.psf_spectrum(c.psf)
+        ref = convolution.HT(convolution.H(x.astype(np.float64), hh) - c.dirty.astype(np.float64), hh)
+        out = {}
+        for radix in (16, 8):
+            with pkg.Plan(n, L, c.psf) as p:
+                p.set_schedule(fft_radix=radix)
+                g = torch.empty((L, n, n), device="cuda")
+                p.op_gradient(dev(x, torch), g, dirty=dev(c.dirty, torch))
+                out[radix] = host(g)
+            assert rel_l2(out[radix], ref) <= 1e-6, (n, radix)
+    c = make_cube(64, 8, 16, 1, 1900, seed=870)
+    xs = [_solve(pkg, torch, c, 0, 0, iters=30) for _ in range(1)]
+    x8 = torch.zeros((c.L, c.n, c.n), device="cuda")
+    with pkg.Plan(c.n, c.L, c.psf) as p:
+        p.set_schedule(fft_radix=8)
+        p.solve(dev(c.dirty, torch), x8, 30, 1e-2, 2e-2)
+    assert rel_l2(host(x8), host(xs[0])) <= 1e-5
+
+
+def test_group_order_bit_identical():
+    """ADA-PT: the two chain groups' kernels phase by phase give the same
+    bits as group after group."""
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    c = make_cube(64, 8, 16, 1, 1900, seed=880)
+    eps = fdmc_eps(c.noise_var)
+    res = []
+    for order in (0, 1):
+        x = torch.zeros((c.L, c.n, c.n), device="cuda")
+        with pkg.Plan(c.n, c.L, c.psf, sure=True) as p:
+            p.set_schedule(group_order=order)
+            th, tr, _ = p.sure_tune(dev(c.dirty, torch), dev(c.delta, torch), c.noise_var, x,
+                                    (0.03, 0.03), 23, window=5, eta=(1e-5, 1e-4), eps=eps)
+        res.append((x, th, tr))
+    assert torch.equal(res[0][0], res[1][0]) and res[0][1] == res[1][1] and res[0][2] == res[1][2]
+
+
 def test_sure_batch_variants_bit_identical():
     torch = cuda()
     import paper_1905_08468_gb300 as pkg
@@ -68,7 +116,7 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         x = torch.zeros_like(ref)
         p.solve(dev(c.dirty, torch), x, 3, 1e-2, 2e-2)
         info = p.autotune(str(cache))
-        assert info.from_cache == 0 and info.candidates == 6
+        assert info.from_cache == 0 and info.candidates == 7    # 4 syn, 2 grids, radix 8
         assert 0 <= info.syn_packed <= 3 and info.dct_ctas_per_sm >= 0
         assert 0 < info.ms_best <= info.ms_default
         # the timing iterations replaced the iterate state: no warm start
@@ -79,7 +127,7 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         p.solve(dev(c.dirty, torch), x, 13, 1e-2, 2e-2)
         assert torch.equal(x, ref)
     lines = [ln.split() for ln in cache.read_text().splitlines()]
-    assert len(lines) == 1 and lines[0][0] == "muffin-tune-3" and "n=64,L=8" in lines[0][1]
+    assert len(lines) == 1 and lines[0][0] == "muffin-tune-4" and "n=64,L=8" in lines[0][1]
     # the same shape again: in-process cache
     with pkg.Plan(64, 8, c.psf) as p:
         again = p.autotune(str(cache))
@@ -87,14 +135,15 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         assert (again.syn_packed, again.dct_ctas_per_sm) == (info.syn_packed, info.dct_ctas_per_sm)
     # a shape only the file knows (written by hand), beside lines to ignore
     key = lines[0][1].replace("n=64,L=8", "n=16,L=8")
-    cache.write_text("garbage line\nmuffin-tune-3 %s 9 1 0 0\nmuffin-tune-2 %s 3 2 0\n"
-                     "muffin-tune-3 %s 2 1 0 3\n" % (key, key, key))
+    cache.write_text("garbage line\nmuffin-tune-4 %s 9 1 0 0 16 0\nmuffin-tune-3 %s 3 2 0 1\n"
+                     "muffin-tune-4 %s 2 1 0 3 8 0\n" % (key, key, key))
     c16 = make_cube(16, 8, 4, 1, 480, seed=841)
     with pkg.Plan(16, 8, c16.psf) as p:
         got = p.autotune(str(cache))
         assert got.from_cache == 1
         assert (got.syn_packed, got.dct_ctas_per_sm, got.grad_chunk) == (2, 1, 3)
-        assert p.schedule()["grad_chunk"] == 3
+        # a 16 px side has no radix-8 plan: the cached radix falls back to 16
+        assert p.schedule()["grad_chunk"] == 3 and p.schedule()["fft_radix"] == 16
 
 
 def test_set_tuning_rejects_bad_values():
