@@ -43,6 +43,7 @@ WORKLOADS = {
     # a mid-size cube for profiler captures (state ~2 GB, inputs > L2)
     "prof_512x512x32": (512, 32, 500, 25, 50000, 6),
     "prof_512x512x64": (512, 64, 500, 25, 50000, 7),
+    "prof_256x256x64": (256, 64, 125, 6, 12500, 8),
 }
 
 
