@@ -233,7 +233,9 @@ typedef struct {
                                of 16.16.4); results agree to FP32 rounding */
   int32_t group_order;      /* ADA-PT plans: 0 = one chain group's kernels
                                after the other's, 1 = both groups phase by
-                               phase (identical results) */
+                               phase, 2 = the two groups concurrently on two
+                               streams, each with its own scratch (identical
+                               results) */
 } muffin_schedule;
 
 /* Reads / sets the schedule (set drops captured graphs and the iterate

@@ -91,6 +91,9 @@ muffin_plan_s::~muffin_plan_s() {
   for (void *q : allocs) cudaFree(q);
   if (ev_in) cudaEventDestroy(ev_in);
   if (ev_out) cudaEventDestroy(ev_out);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (ws2) cudaStreamDestroy(ws2);
   if (ws) cudaStreamDestroy(ws);
 }
 
@@ -167,8 +170,11 @@ muffin_status adjoint_fp64(muffin_plan P, const float *y_dev, const double2 *hh,
 
 // the kernels of one iteration of group g without the x / x~ swap; a plain
 // group (C = 1) may be restricted to the cubes [c0, c1)
-muffin_status iterate_kernels(muffin_plan P, const Group &g, int c0, int c1) {
+muffin_status iterate_kernels(muffin_plan P, const Group &g, int c0, int c1,
+                              cudaStream_t st = nullptr, float2 *S = nullptr,
+                              float *ll = nullptr) {
   if (c1 < 0) c1 = P->B;
+  if (!st) { st = P->ws; S = P->S; ll = P->llscr; }
   const int Lv = (c1 - c0) * P->L;
   Group h = g;
   WaveArgs w = P->wave(g.C);
@@ -184,13 +190,14 @@ muffin_status iterate_kernels(muffin_plan P, const Group &g, int c0, int c1) {
     d.alpha += (size_t)c0 * P->N;
     d.sc += c0;
   }
-  CK(launch_gradient(h.x, h.g, h.b, P->S, kspec, P->tw(), P->n, Lv, g.C, P->ws,
+  CK(launch_gradient(h.x, h.g, h.b, S, kspec, P->tw(), P->n, Lv, g.C, st,
                      P->pp(), P->grad_chunk, P->fft_radix));
   w.L = Lv;
-  CK(wavelet_synthesis_prox(w, h, P->p.positivity, P->ws));
-  CK(wavelet_analysis_dual(w, h, P->ws));
+  w.scratch = ll;
+  CK(wavelet_synthesis_prox(w, h, P->p.positivity, st));
+  CK(wavelet_analysis_dual(w, h, st));
   d.B = c1 - c0;
-  CK(dct_dual(d, h, P->ws));
+  CK(dct_dual(d, h, st));
   return MUFFIN_OK;
 }
 
@@ -219,6 +226,19 @@ muffin_status iterate_group(muffin_plan P, Group &g,
 }
 
 muffin_status iterate_groups(muffin_plan P) {
+  if (P->p.sure && P->group_order == 2) {
+    // the group on y_bar on the second stream with its own scratch, forked
+    // from and joined back into the work stream (captured graphs keep both)
+    CK(cudaEventRecord(P->ev_fork, P->ws));
+    CK(cudaStreamWaitEvent(P->ws2, P->ev_fork, 0));
+    muffin_status s = iterate_kernels(P, P->grp[1], 0, P->B, P->ws2, P->S2, P->llscr2);
+    if (s == MUFFIN_OK) s = iterate_kernels(P, P->grp[0], 0, P->B);
+    if (s != MUFFIN_OK) return s;
+    CK(cudaEventRecord(P->ev_join, P->ws2));
+    CK(cudaStreamWaitEvent(P->ws, P->ev_join, 0));
+    for (Group *g : {&P->grp[0], &P->grp[1]}) std::swap(g->x, g->xt);
+    return MUFFIN_OK;
+  }
   if (!P->p.sure || P->group_order == 0) {
     muffin_status s = iterate_group(P, P->grp[0]);
     if (s == MUFFIN_OK && P->p.sure) s = iterate_group(P, P->grp[1]);
@@ -359,6 +379,12 @@ muffin_status plan_alloc_init(muffin_plan P, const float *alpha, const float *be
     if (s != MUFFIN_OK) return s;
     CK(P->alloc(&P->bbar, NL));
     CK(P->alloc(&P->htd, NL));
+    // second stream and scratch: the two chain groups may run concurrently
+    CK(P->alloc(&P->S2, (size_t)P->Cmax * Lt * nh * n));
+    CK(P->alloc(&P->llscr2, off ? off : 1));
+    CK(cudaStreamCreateWithFlags(&P->ws2, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
   }
   P->grp[0].b = P->b;
   P->grp[1].b = P->bbar;
@@ -754,9 +780,9 @@ size_t estimate_bytes(const muffin_params *p) {
              (kRedSure + 65 * Lt + 6 * (Lt > 4096 ? Lt : 4096)) * 8 + Lt * 8 +
              C * Lt * nh * n * 8 + (ll ? ll : 1) * 4 + 3 * NL * 4 +
              C * NL * (5 + K) * 4;
-  if (p->sure) b += 3 * NL * (5 + K) * 4 + 2 * NL * 4;
+  if (p->sure) b += 3 * NL * (5 + K) * 4 + 2 * NL * 4 + C * Lt * nh * n * 8 + (ll ? ll : 1) * 4;
   b += monitor_scratch_doubles((int)Lt) * 8;
-  return b + (p->sure ? 38 : 30) * 16;   // 16 bytes of slack per allocation
+  return b + (p->sure ? 40 : 30) * 16;   // 16 bytes of slack per allocation
 }
 
 muffin_status create(const muffin_params *p, const float *psf, const float *alpha,

@@ -44,6 +44,8 @@ struct muffin_plan_s {
   cudaStream_t st = nullptr;   // caller's stream
   cudaStream_t ws = nullptr;   // plan's own work stream (graph capture)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaStream_t ws2 = nullptr;                          // second work stream (ADA-PT)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;    // its fork and join
   std::vector<void *> allocs;
   size_t bytes = 0;
 
@@ -62,6 +64,8 @@ struct muffin_plan_s {
   int max_records = 0;
   float2 *S = nullptr;
   float *llscr = nullptr;
+  float2 *S2 = nullptr;        // scratch of the group on the second stream
+  float *llscr2 = nullptr;
   size_t lvl_off[16] = {};
   muffin::Group grp[2];
   float *grp_x0[2] = {nullptr, nullptr};   // x buffer at allocation (graph parity)
@@ -83,7 +87,7 @@ struct muffin_plan_s {
   int dct_tc = 0;         // spectral step on tcgen05 (L = 64)
   int grad_chunk = 0;     // images per pass of the gradient FFTs (0: all at once)
   int fft_radix = 16;     // largest radix of the gradient FFT plan (16, or 8 from n = 64)
-  int group_order = 0;    // ADA-PT: 0 group after group, 1 phase-interleaved (see iterate_all)
+  int group_order = 0;    // ADA-PT: 0 group after group, 1 phase by phase, 2 concurrent streams
   int tw_len16 = 0;       // entries of the radix-16 twiddle tables (the radix-8 ones follow)
   int inject_timeout = 0; // test hook (muffin_plan_inject_timeout)
   int *kerr = nullptr;    // device flag: a bounded tensor-core wait gave up

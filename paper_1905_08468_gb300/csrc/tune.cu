@@ -60,7 +60,7 @@ bool file_lookup(const char *path, const std::string &key, Choice *c) {
       continue;
     if (std::strcmp(tag, "muffin-tune-4") != 0 || key != k) continue;
     if (a < 0 || a > 3 || b < 0 || t < 0 || t > 1 || g < 0 || (r != 8 && r != 16) ||
-        o < 0 || o > 1)
+        o < 0 || o > 2)
       continue;
     c->syn_packed = a;
     c->dct_ctas = b;
@@ -179,9 +179,9 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
     ++cand;
     if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
   }
-  if (P->p.sure && s == MUFFIN_OK) {     // the chain groups phase by phase
+  for (int o = 1; o <= 2 && P->p.sure && s == MUFFIN_OK; ++o) {   // kernel order of the groups
     Choice c = *best;
-    c.group_order = 1;
+    c.group_order = o;
     double t = 0.0;
     s = time_choice(P, c, reps, e0, e1, &t);
     ++cand;
@@ -248,7 +248,7 @@ muffin_status muffin_plan_set_schedule(muffin_plan P, const muffin_schedule *s) 
   if (!P || !s) return fail(MUFFIN_EINVAL, "NULL argument");
   if (s->syn_packed < 0 || s->syn_packed > 3 || s->dct_ctas_per_sm < 0 || s->grad_chunk < 0 ||
       (s->spectral_tcgen05 != 0 && s->spectral_tcgen05 != 1) ||
-      (s->fft_radix != 16 && s->fft_radix != 8) || s->group_order < 0 || s->group_order > 1)
+      (s->fft_radix != 16 && s->fft_radix != 8) || s->group_order < 0 || s->group_order > 2)
     return fail(MUFFIN_EINVAL, "schedule value out of range");
   if (s->spectral_tcgen05 && P->L != 64)
     return fail(MUFFIN_EINVAL, "the tcgen05 spectral kernel needs 64 bands (plan has %d)", P->L);

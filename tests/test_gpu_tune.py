@@ -66,21 +66,22 @@ def test_fft_radix_plans_agree_and_match_oracle():
 
 
 def test_group_order_bit_identical():
-    """ADA-PT: the two chain groups' kernels phase by phase give the same
-    bits as group after group."""
+    """ADA-PT: the two chain groups' kernels phase by phase, or concurrently
+    on two streams, give the same bits as group after group."""
     torch = cuda()
     import paper_1905_08468_gb300 as pkg
     c = make_cube(64, 8, 16, 1, 1900, seed=880)
     eps = fdmc_eps(c.noise_var)
     res = []
-    for order in (0, 1):
+    for order in (0, 1, 2):
         x = torch.zeros((c.L, c.n, c.n), device="cuda")
         with pkg.Plan(c.n, c.L, c.psf, sure=True) as p:
             p.set_schedule(group_order=order)
             th, tr, _ = p.sure_tune(dev(c.dirty, torch), dev(c.delta, torch), c.noise_var, x,
                                     (0.03, 0.03), 23, window=5, eta=(1e-5, 1e-4), eps=eps)
         res.append((x, th, tr))
-    assert torch.equal(res[0][0], res[1][0]) and res[0][1] == res[1][1] and res[0][2] == res[1][2]
+    for r in res[1:]:
+        assert torch.equal(res[0][0], r[0]) and res[0][1] == r[1] and res[0][2] == r[2]
 
 
 def test_sure_batch_variants_bit_identical():
