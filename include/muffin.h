@@ -176,6 +176,7 @@ typedef struct {
   int32_t grad_chunk;      /* chosen gradient chunking (muffin_schedule) */
   int32_t fft_radix;       /* chosen FFT plan */
   int32_t group_order;     /* chosen kernel order of the ADA-PT groups */
+  int32_t ana_ring;        /* chosen analysis U staging */
 } muffin_tune_info;
 
 /* Times each candidate configuration on this plan's own buffers (a few
@@ -183,8 +184,8 @@ typedef struct {
  * with sure = 1, one plain group otherwise), keeps the fastest and caches it
  * per shape (n, bands, batch, chains, levels, bases, SM count, device name):
  * in process, and in the text file `cache_path` when it is not NULL (read
- * first, one line "muffin-tune-4 <key> <syn_packed> <dct_ctas> <tcgen05> <grad_chunk>
- * <fft_radix> <group_order>"
+ * first, one line "muffin-tune-5 <key> <syn_packed> <dct_ctas> <tcgen05> <grad_chunk>
+ * <fft_radix> <group_order> <ana_ring>"
  * appended per new shape; lines that do not parse are ignored).  The timing iterations overwrite the plan's iterate state: a
  * following solve or sure_tune must start cold (warm = 0; a warm call
  * returns MUFFIN_ESTATE), and captured graphs are rebuilt.  info may be NULL.
@@ -236,6 +237,12 @@ typedef struct {
                                phase, 2 = the two groups concurrently on two
                                streams, each with its own scratch (identical
                                results) */
+  int32_t ana_ring;         /* analysis of the levels specialised for 512,
+                               1024 and 2048 px: 0 = the dual update's U
+                               values loaded by each thread, 1 = the U detail
+                               tiles staged two steps ahead in a shared-memory
+                               ring by cp.async (3 CTAs per SM instead of 4;
+                               identical results) */
 } muffin_schedule;
 
 /* Reads / sets the schedule (set drops captured graphs and the iterate

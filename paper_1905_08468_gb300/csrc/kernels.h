@@ -220,6 +220,8 @@ struct WaveArgs {
                            // [C][L][K][n>>j][n>>j] at scratch + lvl_off[j]
   size_t lvl_off[16];
   int dict;                // 0: union of K Daubechies bases, 1: IUWT (K = J + 1 planes)
+  int ana_ring;            // analysis of the size-specialised levels: 1 stages the
+                           // U detail tiles in a shared-memory ring by cp.async
   int syn_packed;          // synthesis variant: bit 0 coarse levels, bit 1
                            // level 1 (0 scalar row pass, 1 packed row pairs)
   Prof *prof;              // optional per-kernel timing

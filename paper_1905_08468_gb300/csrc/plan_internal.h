@@ -83,6 +83,7 @@ struct muffin_plan_s {
   bool profiling = false;
   bool use_graphs = true;
   int syn_packed = 0;     // synthesis variant bits (see WaveArgs::syn_packed)
+  int ana_ring = 0;       // analysis U staging (see WaveArgs::ana_ring)
   int dct_ctas = 0;       // spectral kernel CTAs per SM (0: all resident)
   int dct_tc = 0;         // spectral step on tcgen05 (L = 64)
   int grad_chunk = 0;     // images per pass of the gradient FFTs (0: all at once)
@@ -131,6 +132,7 @@ struct muffin_plan_s {
     w.beta = beta; w.sc = sc; w.scratch = llscr;
     for (int j = 0; j < 16; ++j) w.lvl_off[j] = lvl_off[j];
     w.syn_packed = syn_packed;
+    w.ana_ring = ana_ring;
     w.prof = pp();
     return w;
   }

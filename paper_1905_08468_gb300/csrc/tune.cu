@@ -25,7 +25,8 @@ struct Choice {
   int dct_tc = 0;      // spectral step on tcgen05 (64-band plans)
   int grad_chunk = 0;  // images per pass of the gradient FFTs (0: all)
   int fft_radix = 16;  // largest radix of the gradient FFT plan
-  int group_order = 0; // ADA-PT groups: 0 one after the other, 1 phase by phase
+  int group_order = 0; // ADA-PT groups: 0 one after the other, 1 phase by phase, 2 two streams
+  int ana_ring = 0;    // analysis U staging in a shared-memory ring
 };
 
 std::mutex g_mu;
@@ -55,13 +56,15 @@ bool file_lookup(const char *path, const std::string &key, Choice *c) {
   char line[512], tag[32], k[400];
   bool found = false;
   while (std::fgets(line, sizeof line, f)) {
-    int a = 0, b = 0, t = 0, g = 0, r = 0, o = 0;
-    if (std::sscanf(line, "%31s %399s %d %d %d %d %d %d", tag, k, &a, &b, &t, &g, &r, &o) != 8)
+    int a = 0, b = 0, t = 0, g = 0, r = 0, o = 0, ar = 0;
+    if (std::sscanf(line, "%31s %399s %d %d %d %d %d %d %d", tag, k, &a, &b, &t, &g, &r, &o,
+                    &ar) != 9)
       continue;
-    if (std::strcmp(tag, "muffin-tune-4") != 0 || key != k) continue;
+    if (std::strcmp(tag, "muffin-tune-5") != 0 || key != k) continue;
     if (a < 0 || a > 3 || b < 0 || t < 0 || t > 1 || g < 0 || (r != 8 && r != 16) ||
-        o < 0 || o > 2)
+        o < 0 || o > 2 || ar < 0 || ar > 1)
       continue;
+    c->ana_ring = ar;
     c->syn_packed = a;
     c->dct_ctas = b;
     c->dct_tc = t;
@@ -77,8 +80,8 @@ bool file_lookup(const char *path, const std::string &key, Choice *c) {
 void file_append(const char *path, const std::string &key, const Choice &c) {
   FILE *f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "muffin-tune-4 %s %d %d %d %d %d %d\n", key.c_str(), c.syn_packed, c.dct_ctas,
-               c.dct_tc, c.grad_chunk, c.fft_radix, c.group_order);
+  std::fprintf(f, "muffin-tune-5 %s %d %d %d %d %d %d %d\n", key.c_str(), c.syn_packed,
+               c.dct_ctas, c.dct_tc, c.grad_chunk, c.fft_radix, c.group_order, c.ana_ring);
   std::fclose(f);
 }
 
@@ -89,6 +92,7 @@ void apply(muffin_plan P, const Choice &c) {
   P->grad_chunk = c.grad_chunk;
   P->fft_radix = P->n >= 64 ? c.fft_radix : 16;
   P->group_order = P->p.sure ? c.group_order : 0;
+  P->ana_ring = c.ana_ring;
 }
 
 // mean time of one iteration of every chain group with choice c
@@ -179,6 +183,16 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
     ++cand;
     if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
   }
+  // the analysis U ring, where the size-specialised analysis runs
+  if ((P->n == 512 || P->n == 1024 || P->n == 2048) && P->J > 1 && P->dict == 0 &&
+      s == MUFFIN_OK) {
+    Choice c = *best;
+    c.ana_ring = 1;
+    double t = 0.0;
+    s = time_choice(P, c, reps, e0, e1, &t);
+    ++cand;
+    if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
+  }
   for (int o = 1; o <= 2 && P->p.sure && s == MUFFIN_OK; ++o) {   // kernel order of the groups
     Choice c = *best;
     c.group_order = o;
@@ -241,6 +255,7 @@ muffin_status muffin_plan_get_schedule(muffin_plan P, muffin_schedule *s) {
   s->grad_chunk = P->grad_chunk;
   s->fft_radix = P->fft_radix;
   s->group_order = P->group_order;
+  s->ana_ring = P->ana_ring;
   return MUFFIN_OK;
 }
 
@@ -248,7 +263,8 @@ muffin_status muffin_plan_set_schedule(muffin_plan P, const muffin_schedule *s) 
   if (!P || !s) return fail(MUFFIN_EINVAL, "NULL argument");
   if (s->syn_packed < 0 || s->syn_packed > 3 || s->dct_ctas_per_sm < 0 || s->grad_chunk < 0 ||
       (s->spectral_tcgen05 != 0 && s->spectral_tcgen05 != 1) ||
-      (s->fft_radix != 16 && s->fft_radix != 8) || s->group_order < 0 || s->group_order > 2)
+      (s->fft_radix != 16 && s->fft_radix != 8) || s->group_order < 0 || s->group_order > 2 ||
+      s->ana_ring < 0 || s->ana_ring > 1)
     return fail(MUFFIN_EINVAL, "schedule value out of range");
   if (s->spectral_tcgen05 && P->L != 64)
     return fail(MUFFIN_EINVAL, "the tcgen05 spectral kernel needs 64 bands (plan has %d)", P->L);
@@ -259,6 +275,7 @@ muffin_status muffin_plan_set_schedule(muffin_plan P, const muffin_schedule *s) 
   P->grad_chunk = s->grad_chunk;
   P->fft_radix = P->n >= 64 ? s->fft_radix : 16;
   P->group_order = P->p.sure ? s->group_order : 0;
+  P->ana_ring = s->ana_ring;
   return MUFFIN_OK;
 }
 
@@ -288,6 +305,7 @@ muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin
       info->grad_chunk = P->grad_chunk;
       info->fft_radix = P->fft_radix;
       info->group_order = P->group_order;
+      info->ana_ring = P->ana_ring;
       info->from_cache = 1;
     }
     return MUFFIN_OK;
@@ -309,6 +327,7 @@ muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin
     info->grad_chunk = P->grad_chunk;
     info->fft_radix = P->fft_radix;
     info->group_order = P->group_order;
+    info->ana_ring = P->ana_ring;
     info->from_cache = 0;
   }
   return MUFFIN_OK;

@@ -71,6 +71,15 @@ constexpr int QXS = 4;                               // scalar synthesis row ite
 constexpr size_t ana_smem(int ch) {
   return ((size_t)ch * A_RP * A_IP + 2 * A_RP * A_LP) * sizeof(float2);
 }
+// the U-ring variant of the size-specialised analysis: the three detail
+// tiles of the next steps' (basis, chain) arrive by cp.async into a ring of
+// shared-memory slots, RING_AHEAD steps ahead of their dual update
+constexpr int RING_SLOTS = 3, RING_AHEAD = 2;
+constexpr size_t ring_off(int ch) { return (ana_smem(ch) + 15) / 16 * 16; }
+constexpr size_t ring_slot_floats() { return (size_t)3 * TY * TX; }
+constexpr size_t ana_smem_ring(int ch) {
+  return ring_off(ch) + (size_t)RING_SLOTS * ring_slot_floats() * sizeof(float);
+}
 constexpr size_t syn_smem(int) {
   return (size_t)(8 * S_CH * S_CP) * sizeof(float) + (size_t)(2 * TY * S_LP) * sizeof(float2);
 }
@@ -102,6 +111,24 @@ struct SynArgs {
   const float *beta;
   const DevScalars *sc;
 };
+
+// cp.async helpers (16- and 4-byte copies global -> shared)
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
 
 // ------------------------------------------------------------ analysis
 template <int CH, int MODE>
@@ -285,11 +312,14 @@ __device__ __forceinline__ void ana_emit_step(const AnaArgs &a, int l, int bb, i
 // NS, MS > 0: the image side n and the level's input side M fixed at
 // compile time (levels 1 and 2 of the common sizes), so every U offset of
 // the dual update is an immediate
-template <int CH, int MODE, bool LEVEL1, int NS, int MS>
-__global__ void __launch_bounds__(NT, 4) k_ana(AnaArgs a) {
+template <int CH, int MODE, bool LEVEL1, int NS, int MS, bool RING = false>
+__global__ void __launch_bounds__(NT, RING ? 3 : 4) k_ana(AnaArgs a) {
+  static_assert(!RING || (NS > 0 && MODE == WAVE_ITERATE),
+                "the U ring serves the size-specialised iteration kernels (full tiles)");
   extern __shared__ float2 smem2[];
   float2 *in_s = smem2;                     // [CH][A_RP][A_IP] row pairs
   float2 *lohi = in_s + CH * A_RP * A_IP;   // [A_RP][A_LP] lo, then hi
+  float *ring = reinterpret_cast<float *>(reinterpret_cast<char *>(smem2) + ring_off(CH));
   const int n = NS ? NS : a.n, M = MS ? MS : a.M;
   const int h = M >> 1;
   const int ntx = (h + TX - 1) / TX;
@@ -356,13 +386,46 @@ __global__ void __launch_bounds__(NT, 4) k_ana(AnaArgs a) {
   const int nsteps = (LEVEL1 ? a.K : 1) * CH;
   constexpr int LH = A_RP * A_LP;
   uint32_t keep = 0;
+  // ring variant: the detail tiles (DX, DY, HH; TY rows of TX coefficients
+  // each) of step t go to slot t mod RING_SLOTS, in 16-byte copies
+  auto ring_issue = [&](int t) {
+    if (RING && t < nsteps) {
+      const int bt = b0 + t / CH, ct = t % CH;
+      const int hh = M >> 1, hn = hh * n;
+      const float *up = a.u + ((size_t)(ct * a.L + l) * a.K + bt) * ((size_t)n * n);
+      float *slot = ring + (size_t)(t % RING_SLOTS) * ring_slot_floats();
+      for (int it = threadIdx.x; it < 3 * TY * (TX / 4); it += NT) {
+        const int sb = it / (TY * (TX / 4)), r = (it / (TX / 4)) % TY, q = it % (TX / 4);
+        const int so = sb == 0 ? hh : (sb == 1 ? hn : hn + hh);
+        cp_async16(slot + (sb * TY + r) * TX + 4 * q, up + so + (ky0 + r) * n + kx0 + 4 * q);
+      }
+    }
+    if (RING) cp_commit();
+  };
+  for (int t = 0; t < RING_AHEAD; ++t) ring_issue(t);
 #pragma unroll 1
   for (int s = 0; s < nsteps; ++s) {
     const int bb = b0 + s / CH, c = s % CH;
     float pre[4][QY];
-    ana_prefetch<MODE, NS, MS>(a, l, bb, c, kx0, ky0, pre);
+    if (RING) ring_issue(s + RING_AHEAD);
+    else ana_prefetch<MODE, NS, MS>(a, l, bb, c, kx0, ky0, pre);
     ana_rows_dispatch(bb + 1, in_s + c * A_RP * A_IP, lohi, lohi + LH);
-    __syncthreads();
+    if (RING) {
+      cp_wait<RING_AHEAD>();        // this step's tiles are in (other threads': barrier)
+      __syncthreads();
+      const float *slot = ring + (size_t)(s % RING_SLOTS) * ring_slot_floats();
+      const int kx = threadIdx.x % TX, sq = threadIdx.x / TX;
+#pragma unroll
+      for (int qq = 0; qq < QY; ++qq) {
+        const int r = QY * sq + qq;
+        pre[0][qq] = slot[(0 * TY + r) * TX + kx];
+        pre[1][qq] = slot[(1 * TY + r) * TX + kx];
+        pre[2][qq] = slot[(2 * TY + r) * TX + kx];
+        pre[3][qq] = 0.f;
+      }
+    } else {
+      __syncthreads();
+    }
     float cf[4][QY];
     ana_cols_dispatch(bb + 1, lohi, lohi + LH, cf);
     // dual step scale: sigma mu_l (primal, d/dgamma), sigma beta_l (d/dmu)
@@ -383,24 +446,8 @@ __global__ void __launch_bounds__(NT, 4) k_ana(AnaArgs a) {
 // d/dmu chain's synthesis of (u + mu u'_mu) (Algorithm 3) is accumulated as
 // W^T u + mu W^T u'_mu, continuing from chain 0's finished sum.
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 constexpr int SUB = S_CH * S_CP;   // one subband tile in shared memory
 
-__device__ __forceinline__ void cp_async16(float *dst, const float *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
 
 // copies of the four subband tiles of a (chain, basis) step: rows ky0-8 ..
 // ky0+TY-1 and columns kx0-8 .. kx0+TX-1 (mod the level size h).  With
@@ -881,7 +928,7 @@ inline double level_flops(int CH, int L, int K, int h) {
   return (double)CH * L * 32.0 * (K * (K + 1) / 2) * (double)h * h;
 }
 
-template <int CH, int MODE, bool L1, int NS = 0, int MS = 0>
+template <int CH, int MODE, bool L1, int NS = 0, int MS = 0, bool RING = false>
 cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st, Prof *prof) {
   const double h = a.M >> 1, rw = MODE == WAVE_ITERATE ? 2.0 : 1.0;
   const double in = L1 ? (double)CH * a.L * a.M * a.M * (MODE == WAVE_ITERATE ? 8.0 : 4.0)
@@ -890,14 +937,24 @@ cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st, Prof *prof
   const double ll = (double)CH * a.L * a.K * h * h * 4.0 * (a.last ? rw : 1.0);
   ProfScope ps(prof, L1 ? "ana_level1_dual" : "ana_level_dual", in + det + ll,
                level_flops(CH, a.L, L1 ? a.K : a.K, (int)h), st);
+  constexpr size_t smem = RING ? ana_smem_ring(CH) : ana_smem(CH);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_ana<CH, MODE, L1, NS, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)ana_smem(CH));
+    cudaFuncSetAttribute(k_ana<CH, MODE, L1, NS, MS, RING>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_ana<CH, MODE, L1, NS, MS><<<dim3(tiles(a.M >> 1), nblk_y), NT, ana_smem(CH), st>>>(a);
+  k_ana<CH, MODE, L1, NS, MS, RING><<<dim3(tiles(a.M >> 1), nblk_y), NT, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+// the size-specialised analysis launch, with or without the U ring
+template <int CH, int MODE, bool L1, int NS, int MS>
+cudaError_t launch_ana_sized(const AnaArgs &a, int nblk_y, bool ring, cudaStream_t st,
+                             Prof *prof) {
+  if constexpr (MODE == WAVE_ITERATE)
+    if (ring) return launch_ana<CH, MODE, L1, NS, MS, true>(a, nblk_y, st, prof);
+  return launch_ana<CH, MODE, L1, NS, MS, false>(a, nblk_y, st, prof);
 }
 
 template <int CH, int MODE, bool L1, bool PACKED>
@@ -967,18 +1024,19 @@ cudaError_t analysis_all(const WaveArgs &w, const AnaArgs &base, cudaStream_t st
   a.last = (w.J == 1);
   a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[1];
   // the size-specialised kernels assume a level below (J > level)
-  cudaError_t e = (w.n == 2048 && w.J > 1) ? launch_ana<CH, MODE, true, 2048, 2048>(a, w.L, st, w.prof)
-                  : (w.n == 1024 && w.J > 1) ? launch_ana<CH, MODE, true, 1024, 1024>(a, w.L, st, w.prof)
-                  : (w.n == 512 && w.J > 1) ? launch_ana<CH, MODE, true, 512, 512>(a, w.L, st, w.prof)
+  const bool ring = w.ana_ring != 0;
+  cudaError_t e = (w.n == 2048 && w.J > 1) ? launch_ana_sized<CH, MODE, true, 2048, 2048>(a, w.L, ring, st, w.prof)
+                  : (w.n == 1024 && w.J > 1) ? launch_ana_sized<CH, MODE, true, 1024, 1024>(a, w.L, ring, st, w.prof)
+                  : (w.n == 512 && w.J > 1) ? launch_ana_sized<CH, MODE, true, 512, 512>(a, w.L, ring, st, w.prof)
                                             : launch_ana<CH, MODE, true>(a, w.L, st, w.prof);
   for (int j = 2; j <= w.J && e == cudaSuccess; ++j) {
     a.M = w.n >> (j - 1);
     a.in = w.scratch + w.lvl_off[j - 1];
     a.last = (j == w.J);
     a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[j];
-    if (j == 2 && w.J > 2 && w.n == 2048) e = launch_ana<CH, MODE, false, 2048, 1024>(a, w.L * w.K, st, w.prof);
-    else if (j == 2 && w.J > 2 && w.n == 1024) e = launch_ana<CH, MODE, false, 1024, 512>(a, w.L * w.K, st, w.prof);
-    else if (j == 2 && w.J > 2 && w.n == 512) e = launch_ana<CH, MODE, false, 512, 256>(a, w.L * w.K, st, w.prof);
+    if (j == 2 && w.J > 2 && w.n == 2048) e = launch_ana_sized<CH, MODE, false, 2048, 1024>(a, w.L * w.K, ring, st, w.prof);
+    else if (j == 2 && w.J > 2 && w.n == 1024) e = launch_ana_sized<CH, MODE, false, 1024, 512>(a, w.L * w.K, ring, st, w.prof);
+    else if (j == 2 && w.J > 2 && w.n == 512) e = launch_ana_sized<CH, MODE, false, 512, 256>(a, w.L * w.K, ring, st, w.prof);
     else e = launch_ana<CH, MODE, false>(a, w.L * w.K, st, w.prof);
   }
   return e;

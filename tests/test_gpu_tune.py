@@ -65,6 +65,32 @@ def test_fft_radix_plans_agree_and_match_oracle():
     assert rel_l2(host(x8), host(xs[0])) <= 1e-5
 
 
+@pytest.mark.parametrize("sure", [False, True])
+def test_analysis_ring_bit_identical(sure):
+    """The U ring of the size-specialised analysis (512 px: levels 1 and 2)
+    gives the same bits as the per-thread loads, plain and ADA-PT."""
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    c = make_cube(512, 2, 30, 2, 3000, seed=890)
+    eps = fdmc_eps(c.noise_var)
+    res = []
+    for ring in (0, 1):
+        x = torch.zeros((c.L, c.n, c.n), device="cuda")
+        with pkg.Plan(c.n, c.L, c.psf, sure=sure) as p:
+            p.set_schedule(ana_ring=ring)
+            if sure:
+                th, tr, _ = p.sure_tune(dev(c.dirty, torch), dev(c.delta, torch), c.noise_var, x,
+                                        (1e-2, 1e-2), 6, window=3, eta=(2e-3, 2e-2), eps=eps)
+            else:
+                p.solve(dev(c.dirty, torch), x, 6, 1e-2, 1e-2)
+                th, tr = None, None
+            st = p.state_arrays()
+        res.append((x, th, tr, st))
+    assert torch.equal(res[0][0], res[1][0]) and res[0][1] == res[1][1] and res[0][2] == res[1][2]
+    for k in ("x", "u", "v", "t"):
+        assert np.array_equal(res[0][3][k], res[1][3][k]), k
+
+
 def test_group_order_bit_identical():
     """ADA-PT: the two chain groups' kernels phase by phase, or concurrently
     on two streams, give the same bits as group after group."""
@@ -128,7 +154,7 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         p.solve(dev(c.dirty, torch), x, 13, 1e-2, 2e-2)
         assert torch.equal(x, ref)
     lines = [ln.split() for ln in cache.read_text().splitlines()]
-    assert len(lines) == 1 and lines[0][0] == "muffin-tune-4" and "n=64,L=8" in lines[0][1]
+    assert len(lines) == 1 and lines[0][0] == "muffin-tune-5" and "n=64,L=8" in lines[0][1]
     # the same shape again: in-process cache
     with pkg.Plan(64, 8, c.psf) as p:
         again = p.autotune(str(cache))
@@ -136,8 +162,8 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         assert (again.syn_packed, again.dct_ctas_per_sm) == (info.syn_packed, info.dct_ctas_per_sm)
     # a shape only the file knows (written by hand), beside lines to ignore
     key = lines[0][1].replace("n=64,L=8", "n=16,L=8")
-    cache.write_text("garbage line\nmuffin-tune-4 %s 9 1 0 0 16 0\nmuffin-tune-3 %s 3 2 0 1\n"
-                     "muffin-tune-4 %s 2 1 0 3 8 0\n" % (key, key, key))
+    cache.write_text("garbage line\nmuffin-tune-5 %s 9 1 0 0 16 0 0\nmuffin-tune-4 %s 3 2 0 1 16 0\n"
+                     "muffin-tune-5 %s 2 1 0 3 8 0 0\n" % (key, key, key))
     c16 = make_cube(16, 8, 4, 1, 480, seed=841)
     with pkg.Plan(16, 8, c16.psf) as p:
         got = p.autotune(str(cache))
