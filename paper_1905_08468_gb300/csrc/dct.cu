@@ -80,17 +80,26 @@ __device__ __forceinline__ void tile_gemm(const float *__restrict__ Ahi,
   for (int nt = 0; nt < PT / 8; ++nt)
 #pragma unroll
     for (int e = 0; e < 4; ++e) acc[nt][e] = 0.f;
+  // the A fragments (rows of C from global memory, L2-resident) of the next
+  // k-step are requested before the current step's products
+  uint32_t nh[4], nl[4];
+  auto frag = [&](int k0, uint32_t (&h)[4], uint32_t (&lo)[4]) {
+    const int r0 = (m0 + g) * Lp + k0 + t, r1 = (m0 + g + 8) * Lp + k0 + t;
+    h[0] = __float_as_uint(__ldg(Ahi + r0));
+    h[1] = __float_as_uint(__ldg(Ahi + r1));
+    h[2] = __float_as_uint(__ldg(Ahi + r0 + 4));
+    h[3] = __float_as_uint(__ldg(Ahi + r1 + 4));
+    lo[0] = __float_as_uint(__ldg(Alo + r0));
+    lo[1] = __float_as_uint(__ldg(Alo + r1));
+    lo[2] = __float_as_uint(__ldg(Alo + r0 + 4));
+    lo[3] = __float_as_uint(__ldg(Alo + r1 + 4));
+  };
+  frag(0, nh, nl);
   for (int k0 = 0; k0 < Lp; k0 += 8) {
     uint32_t ah[4], al[4];
-    const int r0 = (m0 + g) * Lp + k0 + t, r1 = (m0 + g + 8) * Lp + k0 + t;
-    ah[0] = __float_as_uint(__ldg(Ahi + r0));
-    ah[1] = __float_as_uint(__ldg(Ahi + r1));
-    ah[2] = __float_as_uint(__ldg(Ahi + r0 + 4));
-    ah[3] = __float_as_uint(__ldg(Ahi + r1 + 4));
-    al[0] = __float_as_uint(__ldg(Alo + r0));
-    al[1] = __float_as_uint(__ldg(Alo + r1));
-    al[2] = __float_as_uint(__ldg(Alo + r0 + 4));
-    al[3] = __float_as_uint(__ldg(Alo + r1 + 4));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { ah[q] = nh[q]; al[q] = nl[q]; }
+    if (k0 + 8 < Lp) frag(k0 + 8, nh, nl);
     const float *b0p = B + (k0 + t) * PP + g;
     const float *b1p = B + (k0 + t + 4) * PP + g;
 #pragma unroll
@@ -169,8 +178,10 @@ __device__ __forceinline__ void store_rows(const float *src, float *dst, int L, 
   }
 }
 
-template <int CH, int MODE, int PT>
-__global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
+// NTHR threads: one warp per 16-band m-tile of C where L allows (256
+// bands: 16 warps), so the products of a tile run in parallel
+template <int CH, int MODE, int PT, int NTHR>
+__global__ void __launch_bounds__(NTHR) k_dct(DctKArgs a) {
   extern __shared__ float sm[];
   constexpr int PP = PT + 8;
   const int Lp = a.Lp, L = a.L;
@@ -186,7 +197,7 @@ __global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
   const size_t cb = (size_t)cube * L * N;    // the cube's first band
   const float *__restrict__ alpha = a.alpha + (size_t)cube * N;
 
-  for (int it = threadIdx.x; it < Lp * PT; it += DT) {
+  for (int it = threadIdx.x; it < Lp * PT; it += NTHR) {
     const int l = it / PT, p = it - l * PT;
     const size_t pix = n0 + p;
     const bool ok = l < L && pix < N;
@@ -205,7 +216,7 @@ __global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
   __syncthreads();
 
   const int nmt = Lp >> 4;
-  for (int mt = warp; mt < nmt; mt += DT / 32) {
+  for (int mt = warp; mt < nmt; mt += NTHR / 32) {
     uint32_t mask = 0;
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -245,14 +256,14 @@ __global__ void __launch_bounds__(DT) k_dct(DctKArgs a) {
   if (MODE == WAVE_TRANSFORM) return;
   __syncthreads();
   if (CH == 3) {
-    for (int it = threadIdx.x; it < Lp * PT; it += DT) {
+    for (int it = threadIdx.x; it < Lp * PT; it += NTHR) {
       const int l = it / PT, p = it - l * PT;
       float *d = vo + (2 * Lp + l) * PP + p;
       *d = fmaf(gamma, *d, vo[l * PP + p]);     // gamma v'_gamma + v
     }
     __syncthreads();
   }
-  for (int mt = warp; mt < nmt; mt += DT / 32) {
+  for (int mt = warp; mt < nmt; mt += NTHR / 32) {
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
       float acc[PT / 8][4];
@@ -454,12 +465,12 @@ cudaError_t launch_dct_small(const DctKArgs &a, cudaStream_t st, Prof *prof) {
   return cudaGetLastError();
 }
 
-template <int CH, int MODE, int PT>
-cudaError_t launch_dct(const DctKArgs &a, cudaStream_t st, Prof *prof) {
+template <int CH, int MODE, int PT, int NTHR>
+cudaError_t launch_dct_t(const DctKArgs &a, cudaStream_t st, Prof *prof) {
   const size_t sm = (size_t)2 * CH * a.Lp * (PT + 8) * sizeof(float);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_dct<CH, MODE, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_dct<CH, MODE, PT, NTHR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
     attr = true;
   }
@@ -468,14 +479,26 @@ cudaError_t launch_dct(const DctKArgs &a, cudaStream_t st, Prof *prof) {
   ProfScope ps(prof, MODE == WAVE_ITERATE ? "spectral_dual" : "spectral_op",
                MODE == WAVE_ITERATE ? CH * vox * 20.0 : vox * 8.0,
                (MODE == WAVE_ITERATE ? 2.0 : 1.0) * CH * 2.0 * a.L * vox, st);
-  k_dct<CH, MODE, PT><<<dim3((unsigned)((N + PT - 1) / PT), a.B), DT, sm, st>>>(a);
+  k_dct<CH, MODE, PT, NTHR><<<dim3((unsigned)((N + PT - 1) / PT), a.B), NTHR, sm, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int CH, int MODE, int PT>
+cudaError_t launch_dct(const DctKArgs &a, cudaStream_t st, Prof *prof) {
+  if (a.Lp >= 256) return launch_dct_t<CH, MODE, PT, 512>(a, st, prof);
+  if (a.Lp >= 128) return launch_dct_t<CH, MODE, PT, 256>(a, st, prof);
+  return launch_dct_t<CH, MODE, PT, DT>(a, st, prof);
 }
 
 template <int CH, int MODE>
 cudaError_t launch_dct_pt(const DctKArgs &a, cudaStream_t st, Prof *prof) {
-  // largest pixel tile whose two [CH][Lp][PT+8] buffers fit in ~160 KB
+  // largest pixel tile whose two [CH][Lp][PT+8] buffers fit in the shared
+  // memory: every tile reads all of C from L2 once per product, so wider
+  // tiles cut that traffic per pixel (64 pixels for one chain up to 256
+  // bands)
+  const size_t per64 = (size_t)2 * CH * a.Lp * 72 * sizeof(float);
   const size_t per32 = (size_t)2 * CH * a.Lp * 40 * sizeof(float);
+  if (a.Lp > 64 && per64 <= 200 * 1024) return launch_dct<CH, MODE, 64>(a, st, prof);
   if (per32 <= 160 * 1024) return launch_dct<CH, MODE, 32>(a, st, prof);
   return launch_dct<CH, MODE, 16>(a, st, prof);
 }

@@ -87,3 +87,30 @@ def test_dct_256_bands(inverse):
         v = torch.empty((L, n, n), device="cuda")
         plan.op_dct(dev(x, torch), v, inverse=inverse)
     assert rel_l2(host(v), ref) <= 2e-6
+
+
+@pytest.mark.parametrize("n,L,sure", [(32, 256, False), (16, 128, True), (16, 100, True)])
+def test_many_bands_iteration_matches_oracle(n, L, sure):
+    """The spectral step with more than 64 bands (the wide-tile mma.sync
+    kernel, one warp per 16-band tile of C) inside the iteration: plain
+    MUFFIN and ADA-PT (three chains) against the oracle."""
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    from oracle import muffin as om, sure as osure
+    from synth import fdmc_eps
+    c = make_cube(n, L, 10, 1, 40 * n, seed=57 + L)
+    prob = om.make_problem(c.dirty, c.psf)
+    x = dev(np.zeros_like(c.dirty), torch)
+    with pkg.Plan(n, L, c.psf, sure=sure) as plan:
+        if sure:
+            eps = fdmc_eps(c.noise_var)
+            th, _, _ = plan.sure_tune(dev(c.dirty, torch), dev(c.delta, torch), c.noise_var, x,
+                                      (1e-2, 1e-2), 8, window=4, eta=(1e-6, 1e-5), eps=eps)
+            ref = osure.ada_pt(prob, c.delta, eps, c.noise_var, (1e-2, 1e-2), 8, Delta=4,
+                               eta=(1e-6, 1e-5))
+            assert np.allclose(th, ref.theta, rtol=1e-3, atol=0)
+            ref_x = ref.x
+        else:
+            plan.solve(dev(c.dirty, torch), x, 20, 1e-2, 1e-2)
+            ref_x = om.solve(prob, 1e-2, 1e-2, 20)[0].x
+    assert rel_l2(host(x), ref_x) <= 1e-5
