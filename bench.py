@@ -249,7 +249,10 @@ def workload_config(args, oracle=False) -> dict:
            "window": args.window,
            "wavelets": ("IUWT (starlet), 3 scales" if getattr(args, "dictionary", "daubechies") == "iuwt"
                         else "db1..db8, 3 levels"),
-           "spectral": "DCT-II, 3xTF32 products on the tensor cores (tcgen05 for 64 bands, else mma.sync)", "chains": 1 if plain else 6,
+           "spectral": ("DCT-II in FP32 on the CUDA cores (fast DCT, one complex DFT per pixel pair)"
+                        if getattr(args, "precision", "tf32") == "fp32" else
+                        "DCT-II, 3xTF32 products on the tensor cores (tcgen05 for 64 bands, else mma.sync)"),
+           "chains": 1 if plain else 6,
            "theta0": None if plain else list(THETA0), "eta": None if plain else list(ETA),
            "l2": "inputs larger than L2 (state ~26 GB per cube at 1024^2 x 64 ADA-PT)"}
     if oracle:
@@ -492,6 +495,9 @@ def main() -> None:
     ap.add_argument("--plain", action="store_true",
                     help="plain MUFFIN (Algorithm 2, fixed mu = gamma = --mu) instead of ADA-PT")
     ap.add_argument("--mu", type=float, default=1e-2)
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32"],
+                    help="spectral DCT: 3xTF32 tensor-core products (default) or the FP32 "
+                         "fast DCT on the CUDA cores")
     ap.add_argument("--grad-chunk", type=int, default=-1,
                     help="images per pass of the gradient FFTs (-1: the tuner's choice)")
     ap.add_argument("--no-cufft", action="store_true",
@@ -634,7 +640,8 @@ def run_gpu(args) -> None:
     dirty = torch.from_numpy(c.dirty).to(dev)
     delta = torch.from_numpy(c.delta).to(dev) if mode == "adapt" else None
     x = torch.zeros_like(dirty)
-    plan = pkg.Plan(c.n, c.L, psf, sure=mode == "adapt", dictionary=args.dictionary)
+    plan = pkg.Plan(c.n, c.L, psf, sure=mode == "adapt", dictionary=args.dictionary,
+                    precision=args.precision)
     del psf
     tuning = None
     if args.tuning:

@@ -84,6 +84,18 @@ typedef struct {
                          K; 1 = isotropic undecimated wavelet transform
                          (starlet, B3 spline, periodic) with J = levels <= 4
                          scales, K = J + 1 planes, ||W_s||^2 = 1 */
+  int32_t precision;  /* arithmetic of the spectral DCT W_lambda (Sec. 4.2.1):
+                         0 (default) = dense L x L products as 3xTF32 split
+                         products on the tensor cores, FP32 accumulation;
+                         1 = FP32 on the CUDA cores by a fast DCT-II
+                         (Makhoul's reordering into one complex DFT per
+                         pixel, O(L log L)); needs nbands a power of two in
+                         [2, 1024] */
+  double tau;         /* primal step override: > 0 makes every solve and
+                         every ADA-PT window use this tau instead of the
+                         step rule (the caller then answers for the step
+                         condition of Sec. 2.2); 0 (default) = from
+                         step_rule and tau_safety */
 } muffin_params;
 
 /* Fill *p with the defaults above for an n x n x nbands cube. */

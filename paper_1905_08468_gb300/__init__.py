@@ -83,7 +83,8 @@ class Plan:
                  levels: int = 3, sigma: float = 10.0, step_rule: int = 0,
                  tau_safety: float = 0.99, positivity: bool = True,
                  sure: bool = False, alpha=None, beta=None, stream=None,
-                 batch: int = 1, dictionary: str = "daubechies"):
+                 batch: int = 1, dictionary: str = "daubechies", precision: str = "tf32",
+                 tau: float = 0.0):
         lib = library()
         self._lib = lib
         self.n, self.L, self.B = n, nbands, batch
@@ -96,6 +97,10 @@ class Plan:
         p.step_rule, p.tau_safety = step_rule, tau_safety
         p.positivity, p.sure, p.batch = int(positivity), int(sure), int(batch)
         p.dictionary = _dictionary(dictionary)
+        if precision not in ("tf32", "fp32"):
+            raise ValueError(f"precision must be 'tf32' or 'fp32', got {precision!r}")
+        p.precision = 1 if precision == "fp32" else 0
+        p.tau = float(tau)
         keep = []
         handle = ctypes.c_void_p()
         st = stream if stream is not None else _stream_handle()
@@ -441,13 +446,15 @@ class Plan:
 
 
 def estimate_bytes(n: int, nbands: int, *, n_wavelets: int = 8, levels: int = 3,
-                   sure: bool = False, batch: int = 1, dictionary: str = "daubechies") -> int:
+                   sure: bool = False, batch: int = 1, dictionary: str = "daubechies",
+                   precision: str = "tf32") -> int:
     """Device bytes a plan of this shape allocates."""
     lib = library()
     p = native.Params()
     lib.muffin_params_default(ctypes.byref(p), n, nbands)
     p.n_wavelets, p.levels, p.sure, p.batch = n_wavelets, levels, int(sure), batch
     p.dictionary = _dictionary(dictionary)
+    p.precision = 1 if precision == "fp32" else 0
     out = ctypes.c_size_t()
     native.check(lib.muffin_plan_estimate_bytes(ctypes.byref(p), ctypes.byref(out)))
     return int(out.value)

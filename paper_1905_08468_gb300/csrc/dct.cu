@@ -180,13 +180,20 @@ __device__ __forceinline__ void store_rows(const float *src, float *dst, int L, 
 
 // NTHR threads: one warp per 16-band m-tile of C where L allows (256
 // bands: 16 warps), so the products of a tile run in parallel
-template <int CH, int MODE, int PT, int NTHR>
+// ALIAS (one chain, at most one m-tile per warp): the new duals stay in
+// registers until every warp has finished the first product, then overwrite
+// the input tile, so one [Lp][PT + 8] buffer serves both products and the
+// pixel tile can be twice as wide (half the L2 reads of C per pixel)
+template <int CH, int MODE, int PT, int NTHR, bool ALIAS = false>
 __global__ void __launch_bounds__(NTHR) k_dct(DctKArgs a) {
+  static_assert(!ALIAS || CH == 1, "the aliased tile holds one chain");
   extern __shared__ float sm[];
   constexpr int PP = PT + 8;
   const int Lp = a.Lp, L = a.L;
-  float *zin = sm;                       // [CH][Lp][PP]
-  float *vo = zin + CH * Lp * PP;        // [CH][Lp][PP]
+  float *zin = sm;                                  // [CH][Lp][PP]
+  float *vo = ALIAS ? zin : zin + CH * Lp * PP;     // [CH][Lp][PP]
+  float vkeep[ALIAS ? PT / 8 : 1][4];
+  int mt_own = -1;
   const size_t N = a.npix;
   const size_t CS = (size_t)a.B * L * N;     // chain stride
   const size_t n0 = (size_t)blockIdx.x * PT;
@@ -248,13 +255,27 @@ __global__ void __launch_bounds__(NTHR) k_dct(DctKArgs a) {
             }
             a.v[c * CS + j] = vn;
           }
-          vo[(c * Lp + k) * PP + p] = vn;
+          if constexpr (ALIAS) vkeep[nt][e] = vn;
+          else vo[(c * Lp + k) * PP + p] = vn;
         }
       }
     }
+    if constexpr (ALIAS) mt_own = mt;
   }
   if (MODE == WAVE_TRANSFORM) return;
   __syncthreads();
+  if constexpr (ALIAS) {
+    if (mt_own >= 0) {
+#pragma unroll
+      for (int nt = 0; nt < PT / 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = mt_own * 16 + g + (e >= 2 ? 8 : 0);
+          vo[k * PP + nt * 8 + 2 * t + (e & 1)] = vkeep[nt][e];
+        }
+    }
+    __syncthreads();
+  }
   if (CH == 3) {
     for (int it = threadIdx.x; it < Lp * PT; it += NTHR) {
       const int l = it / PT, p = it - l * PT;
@@ -465,13 +486,13 @@ cudaError_t launch_dct_small(const DctKArgs &a, cudaStream_t st, Prof *prof) {
   return cudaGetLastError();
 }
 
-template <int CH, int MODE, int PT, int NTHR>
+template <int CH, int MODE, int PT, int NTHR, bool ALIAS = false>
 cudaError_t launch_dct_t(const DctKArgs &a, cudaStream_t st, Prof *prof) {
-  const size_t sm = (size_t)2 * CH * a.Lp * (PT + 8) * sizeof(float);
+  const size_t sm = (size_t)(ALIAS ? 1 : 2) * CH * a.Lp * (PT + 8) * sizeof(float);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_dct<CH, MODE, PT, NTHR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         200 * 1024);
+    cudaFuncSetAttribute(k_dct<CH, MODE, PT, NTHR, ALIAS>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
   const size_t N = a.npix;
@@ -479,7 +500,7 @@ cudaError_t launch_dct_t(const DctKArgs &a, cudaStream_t st, Prof *prof) {
   ProfScope ps(prof, MODE == WAVE_ITERATE ? "spectral_dual" : "spectral_op",
                MODE == WAVE_ITERATE ? CH * vox * 20.0 : vox * 8.0,
                (MODE == WAVE_ITERATE ? 2.0 : 1.0) * CH * 2.0 * a.L * vox, st);
-  k_dct<CH, MODE, PT, NTHR><<<dim3((unsigned)((N + PT - 1) / PT), a.B), NTHR, sm, st>>>(a);
+  k_dct<CH, MODE, PT, NTHR, ALIAS><<<dim3((unsigned)((N + PT - 1) / PT), a.B), NTHR, sm, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -498,6 +519,10 @@ cudaError_t launch_dct_pt(const DctKArgs &a, cudaStream_t st, Prof *prof) {
   // bands)
   const size_t per64 = (size_t)2 * CH * a.Lp * 72 * sizeof(float);
   const size_t per32 = (size_t)2 * CH * a.Lp * 40 * sizeof(float);
+  // one chain with 129 .. 256 bands: the aliased 128-pixel tile (16 warps,
+  // one 16-band tile of C each)
+  if (CH == 1 && a.Lp > 128 && a.Lp <= 256)
+    return launch_dct_t<1, MODE, 128, 512, true>(a, st, prof);
   if (a.Lp > 64 && per64 <= 200 * 1024) return launch_dct<CH, MODE, 64>(a, st, prof);
   if (per32 <= 160 * 1024) return launch_dct<CH, MODE, 32>(a, st, prof);
   return launch_dct<CH, MODE, 16>(a, st, prof);
@@ -512,6 +537,7 @@ cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st) {
   a.a1hi = d.chi; a.a1lo = d.clo; a.a2hi = d.cthi; a.a2lo = d.ctlo;
   a.alpha = d.alpha; a.sc = d.sc; a.ctas_per_sm = d.ctas_per_sm;
   a.xt = gr.xt; a.x = gr.x; a.v = gr.v; a.t = gr.t;
+  if (d.f32) return dct_dual_f32(d, gr, st);
   if (d.tc && d.L == 64 && d.Lp == 64) return dct_dual_tc(d, gr, d.err, st);
   if (d.Lp <= 64) {
     if (gr.C == 3) return launch_dct_small<3>(a, st, d.prof);
@@ -523,6 +549,7 @@ cudaError_t dct_dual(const DctArgs &d, const Group &gr, cudaStream_t st) {
 
 cudaError_t dct_op(const DctArgs &d, const float *in, float *out, int inverse,
                    cudaStream_t st) {
+  if (d.f32) return dct_op_f32(d, in, out, inverse, st);
   DctKArgs a{};
   a.n = d.n; a.L = d.L; a.Lp = d.Lp; a.inverse = inverse; a.B = d.B > 0 ? d.B : 1;
   a.npix = d.npix ? d.npix : (size_t)d.n * d.n;

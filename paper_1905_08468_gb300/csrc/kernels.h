@@ -173,6 +173,7 @@ struct ThetaUpdateArgs {
   // tau = safety / (beta/2 + sigma * (K * mu^2 * Bsum + gamma^2 * Asum))
   const double *cube_const;
   double safety, K;
+  double tau_fixed;        // > 0: tau stays at this value (the plan's override)
 };
 cudaError_t theta_update(const ThetaUpdateArgs &a, cudaStream_t st);
 
@@ -261,6 +262,9 @@ struct DctArgs {
   int tc;                  // 1: tcgen05 kernel (L = 64), 0: mma.sync kernel
   int *err;                // device flag raised when a tensor-core wait gives up
   int inject_timeout;      // test hook: the tcgen05 kernel issues no products
+  int f32;                 // 1: FP32 fast DCT on the CUDA cores (dct_f32.cu)
+  const float2 *ftab;      // its tables: DFT stage twiddles, then (cos, sin)(pi k / 2L)
+  int ftw_len;             // stage twiddle entries at the head of ftab
   Prof *prof;              // optional per-kernel timing
 };
 // Spectral dual update and back-projection (Alg. 2 eqs. vt, v, upt and the
@@ -271,5 +275,12 @@ cudaError_t dct_dual_tc(const DctArgs &d, const Group &gr, int *err, cudaStream_
 // Operator: out^n = C in^n (inverse = 0) or C^T in^n (inverse = 1).
 cudaError_t dct_op(const DctArgs &d, const float *in, float *out, int inverse,
                    cudaStream_t st);
+// The FP32 forms (L a power of two in [2, 1024]) and their tables:
+// dct_f32_table_len(L) float2 entries, filled by dct_f32_tables.
+cudaError_t dct_dual_f32(const DctArgs &d, const Group &gr, cudaStream_t st);
+cudaError_t dct_op_f32(const DctArgs &d, const float *in, float *out, int inverse,
+                       cudaStream_t st);
+int dct_f32_table_len(int L);
+void dct_f32_tables(int L, float2 *tab);
 
 }  // namespace muffin

@@ -120,9 +120,17 @@ muffin_status validate(const muffin_params *p) {
     return fail(MUFFIN_EINVAL, "tau_safety must be in (0, 1)");
   if (p->step_rule != 0 && p->step_rule != 1)
     return fail(MUFFIN_EINVAL, "step_rule must be 0 or 1");
+  if (p->precision != 0 && p->precision != 1)
+    return fail(MUFFIN_EINVAL, "precision=%d must be 0 (3xTF32) or 1 (FP32)", p->precision);
+  if (p->precision == 1 &&
+      (p->nbands < 2 || p->nbands > 1024 || (p->nbands & (p->nbands - 1))))
+    return fail(MUFFIN_EINVAL, "the FP32 spectral step needs nbands a power of two in "
+                "[2, 1024] (got %d)", p->nbands);
+  if (!(p->tau >= 0) || !std::isfinite(p->tau))
+    return fail(MUFFIN_EINVAL, "tau must be finite and >= 0 (0: from the step rule)");
   // the spectral tile kernel keeps two [C][Lp][24] float tiles in shared memory
   const size_t lp = (size_t)(p->nbands + 15) / 16 * 16;
-  if ((size_t)2 * (p->sure ? 3 : 1) * lp * 24 * sizeof(float) > 200 * 1024)
+  if (p->precision == 0 && (size_t)2 * (p->sure ? 3 : 1) * lp * 24 * sizeof(float) > 200 * 1024)
     return fail(MUFFIN_EINVAL, "nbands=%d too large for the spectral tile (sure=%d)",
                 p->nbands, p->sure);
   return MUFFIN_OK;
@@ -347,6 +355,10 @@ muffin_status plan_alloc_init(muffin_plan P, const float *alpha, const float *be
   CK(P->alloc(&P->clo, LL2));
   CK(P->alloc(&P->cthi, LL2));
   CK(P->alloc(&P->ctlo, LL2));
+  if (P->p.precision == 1) {
+    P->ftw_len = dct_f32_table_len(L) - L;
+    CK(P->alloc(&P->ftab, (size_t)dct_f32_table_len(L)));
+  }
   CK(P->alloc(&P->alpha, (size_t)B * N));
   CK(P->alloc(&P->beta, (size_t)Lt));
   CK(P->alloc(&P->sc, (size_t)B));
@@ -426,6 +438,12 @@ muffin_status plan_alloc_init(muffin_plan P, const float *alpha, const float *be
   CK(cudaMemcpyAsync(P->clo, lo.data(), LL2 * 4, cudaMemcpyHostToDevice, P->ws));
   CK(cudaMemcpyAsync(P->cthi, thi.data(), LL2 * 4, cudaMemcpyHostToDevice, P->ws));
   CK(cudaMemcpyAsync(P->ctlo, tlo.data(), LL2 * 4, cudaMemcpyHostToDevice, P->ws));
+  std::vector<float2> ft(P->p.precision == 1 ? (size_t)dct_f32_table_len(L) : 0);
+  if (P->p.precision == 1) {
+    dct_f32_tables(L, ft.data());
+    CK(cudaMemcpyAsync(P->ftab, ft.data(), ft.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                       P->ws));
+  }
   CK(cudaStreamSynchronize(P->ws));
 
   // ---- weights (Eq. 2regpar), per cube
@@ -485,6 +503,7 @@ muffin_status window_end(muffin_plan P, const muffin_sure_params *sp) {
   ta.record = P->records; ta.rec_count = P->rec_count;
   ta.eta_mu = sp->eta_mu; ta.eta_gamma = sp->eta_gamma; ta.theta_min = sp->theta_min;
   ta.cube_const = P->cube_const; ta.safety = P->p.tau_safety; ta.K = P->wsn2;
+  ta.tau_fixed = P->p.tau;
   {
     ProfScope ps(P->pp(), "theta_update", 6.0 * 8.0 * bpb * P->Lt, 0.0, P->ws);
     CK(theta_update(ta, P->ws));
@@ -782,6 +801,7 @@ size_t estimate_bytes(const muffin_params *p) {
              C * NL * (5 + K) * 4;
   if (p->sure) b += 3 * NL * (5 + K) * 4 + 2 * NL * 4 + C * Lt * nh * n * 8 + (ll ? ll : 1) * 4;
   b += monitor_scratch_doubles((int)Lt) * 8;
+  if (p->precision == 1) b += (size_t)dct_f32_table_len((int)L) * 8 + 16;
   return b + (p->sure ? 40 : 30) * 16;   // 16 bytes of slack per allocation
 }
 
@@ -801,7 +821,7 @@ muffin_status create(const muffin_params *p, const float *psf, const float *alph
   P->p = *p;
   P->n = p->n; P->L = p->nbands; P->J = p->levels;
   P->dict = p->dictionary;
-  P->dct_tc = p->nbands == 64 ? 1 : 0;
+  P->dct_tc = p->nbands == 64 && p->precision == 0 ? 1 : 0;
   P->K = P->dict == 1 ? p->levels + 1 : p->n_wavelets;
   P->wsn2 = P->dict == 1 ? iuwt_norm2(p->n, p->levels) : (double)p->n_wavelets;
   P->B = p->batch; P->Lt = P->B * P->L;
@@ -839,6 +859,7 @@ void muffin_params_default(muffin_params *p, int32_t n, int32_t nbands) {
   p->n = n; p->nbands = nbands; p->n_wavelets = 8; p->levels = 3;
   p->sigma = 10.0; p->step_rule = 0; p->tau_safety = 0.99; p->positivity = 1;
   p->sure = 0; p->batch = 1; p->dictionary = 0;
+  p->precision = 0; p->tau = 0.0;
 }
 
 void muffin_sure_params_default(muffin_sure_params *s) {

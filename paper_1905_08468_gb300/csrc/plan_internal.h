@@ -54,6 +54,8 @@ struct muffin_plan_s {
   float2 *tw32 = nullptr;
   double2 *tw64 = nullptr;
   float *chi = nullptr, *clo = nullptr, *cthi = nullptr, *ctlo = nullptr;
+  float2 *ftab = nullptr;   // FP32 spectral step tables (precision 1)
+  int ftw_len = 0;
   float *alpha = nullptr, *beta = nullptr;
   muffin::DevScalars *sc = nullptr;   // [B]
   double *cube_const = nullptr;       // [B][4] for the theta update
@@ -124,6 +126,7 @@ struct muffin_plan_s {
     return wsn2 * m * m * Bmax2[c] + g * g * Amax2[c];
   }
   double tau_for(int c, double m, double g) const {
+    if (p.tau > 0) return p.tau;
     return p.tau_safety / (0.5 * lips[c] + p.sigma * lnorm2(c, m, g));
   }
   muffin::WaveArgs wave(int C) {
@@ -143,6 +146,7 @@ struct muffin_plan_s {
     d.alpha = alpha; d.sc = sc;
     d.ctas_per_sm = dct_ctas;
     d.tc = dct_tc; d.err = kerr; d.inject_timeout = inject_timeout;
+    d.f32 = p.precision == 1; d.ftab = ftab; d.ftw_len = ftw_len;
     d.prof = pp();
     return d;
   }

@@ -212,7 +212,9 @@ __global__ void k_theta_update(ThetaUpdateArgs a) {
     const double nga = fmax(fma(-a.eta_gamma, sug_ga, gamma), a.theta_min);
     sc->mu = nmu;
     sc->gamma = nga;
-    sc->tau = a.safety / (0.5 * cc[1] + sc->sigma * (a.K * nmu * nmu * cc[2] + nga * nga * cc[3]));
+    sc->tau = a.tau_fixed > 0
+                  ? a.tau_fixed
+                  : a.safety / (0.5 * cc[1] + sc->sigma * (a.K * nmu * nmu * cc[2] + nga * nga * cc[3]));
   }
 }
 

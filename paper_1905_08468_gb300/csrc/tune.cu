@@ -42,9 +42,10 @@ std::string shape_key(muffin_plan P) {
   for (char &ch : name)
     if (ch == ' ' || ch == '\t') ch = '_';
   char buf[256];
-  std::snprintf(buf, sizeof buf, "n=%d,L=%d,B=%d,C=%d,J=%d,K=%d,dict=%d,sure=%d,sm=%d,dev=%s",
-                P->n, P->L, P->B, P->Cmax, P->J, P->K, P->dict, P->p.sure ? 1 : 0, sms,
-                name.c_str());
+  std::snprintf(buf, sizeof buf,
+                "n=%d,L=%d,B=%d,C=%d,J=%d,K=%d,dict=%d,sure=%d,prec=%d,sm=%d,dev=%s", P->n,
+                P->L, P->B, P->Cmax, P->J, P->K, P->dict, P->p.sure ? 1 : 0, P->p.precision,
+                sms, name.c_str());
   return buf;
 }
 
@@ -88,7 +89,7 @@ void file_append(const char *path, const std::string &key, const Choice &c) {
 void apply(muffin_plan P, const Choice &c) {
   P->syn_packed = c.syn_packed;
   P->dct_ctas = c.dct_ctas;
-  P->dct_tc = P->L == 64 ? c.dct_tc : 0;
+  P->dct_tc = P->L == 64 && P->p.precision == 0 ? c.dct_tc : 0;
   P->grad_chunk = c.grad_chunk;
   P->fft_radix = P->n >= 64 ? c.fft_radix : 16;
   P->group_order = P->p.sure ? c.group_order : 0;
@@ -131,7 +132,8 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
   const double vox = (double)P->NL * P->Cmax * (P->p.sure ? 2 : 1);
   const int reps = vox >= 2e7 ? 3 : (vox >= 1e6 ? 5 : 10);
   Choice cur{};
-  cur.dct_tc = P->L == 64 ? 1 : 0;       // the default kernel for 64 bands
+  const bool tf32 = P->p.precision == 0;   // the FP32 spectral step has no variants
+  cur.dct_tc = P->L == 64 && tf32 ? 1 : 0; // the default kernel for 64 bands
   double t_def = 0.0, t_best = 0.0;
   int cand = 0;
   if (s == MUFFIN_OK) s = time_choice(P, cur, reps, e0, e1, &t_def);
@@ -147,7 +149,7 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
     ++cand;
     if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
   }
-  if (P->L == 64 && s == MUFFIN_OK) {     // the other spectral kernel
+  if (P->L == 64 && tf32 && s == MUFFIN_OK) {     // the other spectral kernel
     Choice c = *best;
     c.dct_tc = 0;
     double t = 0.0;
@@ -155,7 +157,7 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
     ++cand;
     if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
   }
-  for (int k = 1; k <= 2 && s == MUFFIN_OK && !best->dct_tc; ++k) {
+  for (int k = 1; k <= 2 && tf32 && s == MUFFIN_OK && !best->dct_tc; ++k) {
     Choice c = *best;
     c.dct_ctas = k;
     double t = 0.0;
@@ -223,6 +225,8 @@ muffin_status muffin_plan_set_spectral_kernel(muffin_plan P, int32_t tcgen05) {
   if (tcgen05 != 0 && tcgen05 != 1) return fail(MUFFIN_EINVAL, "tcgen05 must be 0 or 1");
   if (tcgen05 && P->L != 64)
     return fail(MUFFIN_EINVAL, "the tcgen05 spectral kernel needs 64 bands (plan has %d)", P->L);
+  if (tcgen05 && P->p.precision != 0)
+    return fail(MUFFIN_EINVAL, "the plan computes the spectral step in FP32");
   muffin::pi::drop_graphs_and_state(P);
   P->dct_tc = tcgen05;
   return MUFFIN_OK;
@@ -268,6 +272,8 @@ muffin_status muffin_plan_set_schedule(muffin_plan P, const muffin_schedule *s) 
     return fail(MUFFIN_EINVAL, "schedule value out of range");
   if (s->spectral_tcgen05 && P->L != 64)
     return fail(MUFFIN_EINVAL, "the tcgen05 spectral kernel needs 64 bands (plan has %d)", P->L);
+  if (s->spectral_tcgen05 && P->p.precision != 0)
+    return fail(MUFFIN_EINVAL, "the plan computes the spectral step in FP32");
   muffin::pi::drop_graphs_and_state(P);
   P->syn_packed = s->syn_packed;
   P->dct_ctas = s->dct_ctas_per_sm;

@@ -17,7 +17,8 @@ class Params(ctypes.Structure):
     _fields_ = [("n", c_int32), ("nbands", c_int32), ("n_wavelets", c_int32),
                 ("levels", c_int32), ("sigma", c_double), ("step_rule", c_int32),
                 ("tau_safety", c_double), ("positivity", c_int32), ("sure", c_int32),
-                ("batch", c_int32), ("dictionary", c_int32)]
+                ("batch", c_int32), ("dictionary", c_int32), ("precision", c_int32),
+                ("tau", c_double)]
 
 
 class Info(ctypes.Structure):

@@ -99,10 +99,11 @@ def check_trace(trace, ref_trace):
         assert tg["psure"] == pytest.approx(to["psure"], rel=1e-3)
 
 
-def run_case(c, theta0, iters, window, eta, reset=True, n_wavelets=8, levels=3, workers=None):
+def run_case(c, theta0, iters, window, eta, reset=True, n_wavelets=8, levels=3, workers=None,
+             **plan_kw):
     eps = fdmc_eps(c.noise_var)
     th, trace, st = gpu_run(c, theta0, iters, window, eta, eps, reset,
-                            n_wavelets=n_wavelets, levels=levels)
+                            n_wavelets=n_wavelets, levels=levels, **plan_kw)
     prob = om.make_problem(c.dirty, c.psf, n_wavelets=n_wavelets, J=levels)
     if workers:
         _, ref_theta, ref_trace, states = opar.ada_pt(prob, c.delta, eps, c.noise_var, theta0,
