@@ -133,12 +133,16 @@ def zero_state(prob: Problem, x0=None) -> State:
                  t=np.zeros((L, n, n)))
 
 
-def iteration(st: State, prob: Problem, y, mu_l, gamma_n, tau) -> dict:
+def iteration(st: State, prob: Problem, y, mu_l, gamma_n, tau, grad_fn=None) -> dict:
     """One Algorithm-2 update in place; returns the intermediates that the
     derivative iterates of Algorithms 3/4 need (m, p, v-tilde, pre-update u,
-    updated v, x and x-tilde)."""
+    updated v, x and x-tilde).  grad_fn(x), when given, replaces the
+    gradient of the image-domain data term (another direct operator, Sec. 1)."""
     x = st.x                                               # eq. updatenode2
-    grad = convolution.HT(convolution.H(x, prob.hhat) - y, prob.hhat)  # grad2
+    if grad_fn is None:
+        grad = convolution.HT(convolution.H(x, prob.hhat) - y, prob.hhat)  # grad2
+    else:
+        grad = grad_fn(x)
     s = mu_l[:, None, None] * prob.WsT(st.u)               # eq. adjointspat2
     m = x - tau * (grad + s + st.t)                         # eq. stpm
     xt = pos(m) if prob.positivity else m                   # eq. stpx
@@ -155,14 +159,14 @@ def iteration(st: State, prob: Problem, y, mu_l, gamma_n, tau) -> dict:
 
 
 def solve(prob: Problem, mu: float, gamma: float, n_iter: int, x0=None,
-          tau=None, step_rule: int = 0, safety: float = 0.99, state=None):
+          tau=None, step_rule: int = 0, safety: float = 0.99, state=None, grad_fn=None):
     """Run n_iter Algorithm-2 iterations; returns (state, tau)."""
     mu_l, gamma_n = weights(prob, mu, gamma)
     if tau is None:
         tau = step_tau(prob, mu_l, gamma_n, step_rule, safety)
     st = zero_state(prob, x0) if state is None else state
     for _ in range(n_iter):
-        iteration(st, prob, prob.y, mu_l, gamma_n, tau)
+        iteration(st, prob, prob.y, mu_l, gamma_n, tau, grad_fn)
     return st, tau
 
 

@@ -5,8 +5,8 @@ path.  It draws skies, PSFs, dirty cubes, noise variances and the FDMC probe
 vector from one seed; it holds none of the deconvolution method's arithmetic
 (no gradient, wavelet, DCT, proximal, derivative or risk-estimate step).
 """
-from .generator import (Cube, WORKLOADS, make_cube, make_workload, fdmc_eps,
-                        serve_stream)
+from .generator import (Cube, VisCube, WORKLOADS, make_cube, make_visibilities,
+                        make_workload, fdmc_eps, serve_stream)
 
-__all__ = ["Cube", "WORKLOADS", "make_cube", "make_workload", "fdmc_eps",
-           "serve_stream"]
+__all__ = ["Cube", "VisCube", "WORKLOADS", "make_cube", "make_visibilities",
+           "make_workload", "fdmc_eps", "serve_stream"]

@@ -16,11 +16,18 @@ documented recipe instead:
 * dirty cube: circular convolution of sky and PSF plus noise with per-band
   variance sigma_l^2 = ||h_l * x_l||^2 / (N 10^(SNR/10));
 * delta: the N(0, I) probe of the finite-difference Monte-Carlo risk estimate
-  (Sec. 3.1), drawn once here so both implementations see the same vector.
+  (Sec. 3.1), drawn once here so both implementations see the same vector;
+* visibilities (make_visibilities, the same sky and uv points): each kept uv
+  point samples the unitary 2D DFT of the band's sky at its nearest cell k,
+  d = (U x_l)_k + complex white noise (per-sample variance set by the SNR
+  against the mean |(U x_l)_k|^2 of the samples), and its Hermitian mirror
+  cell -k receives conj(d); the samples are gridded into per-cell sums D_l
+  and counts m_l (natural weights).
 
 Draw order from ``numpy.random.default_rng(seed)``: source positions,
 amplitudes, source indices, blob centres, blob widths, blob indices, uv
-points, noise (band by band), delta (band by band).
+points, noise (band by band), delta (band by band); for visibilities the
+noise is one (n_kept, 2) standard normal draw per band.
 
 All returned images are float32 (the arrays both implementations consume);
 noise variances are float64.
@@ -75,14 +82,12 @@ def fdmc_eps(noise_var: np.ndarray) -> float:
     return 0.1 * math.sqrt(float(np.mean(noise_var)))
 
 
-def make_cube(n: int, L: int, n_src: int, n_blob: int, n_uv: int,
-              seed: int, snr_db: float = 20.0,
-              with_delta: bool = True) -> Cube:
+def _draw_sky_uv(n: int, L: int, n_src: int, n_blob: int, n_uv: int, rng):
+    """nu_l / nu0, the float32 sky cube and the uv points (the first draws)."""
     if n < 2 or n & (n - 1):
         raise ValueError("image side must be a power of two >= 2")
     if L < 1:
         raise ValueError("need at least one band")
-    rng = np.random.default_rng(seed)
     nu = (1.0 + np.arange(L, dtype=np.float64) / (L - 1)) if L > 1 \
         else np.ones(1)
 
@@ -98,13 +103,7 @@ def make_cube(n: int, L: int, n_src: int, n_blob: int, n_uv: int,
         if n_blob else np.zeros((0, n))
     gx = np.stack([_wrapped_gauss(n, c[1], w) for c, w in zip(centres, widths)]) \
         if n_blob else np.zeros((0, n))
-
     sky = np.empty((L, n, n), np.float32)
-    psf = np.empty((L, n, n), np.float32)
-    dirty = np.empty((L, n, n), np.float32)
-    noise_var = np.empty(L, np.float64)
-    clean = np.empty((L, n, n), np.float64)
-    N = n * n
     for l in range(L):
         s = np.zeros((n, n), np.float64)
         np.add.at(s, (pos[:, 0], pos[:, 1]), amp * nu[l] ** a_src)
@@ -112,13 +111,34 @@ def make_cube(n: int, L: int, n_src: int, n_blob: int, n_uv: int,
             w = 0.3 * nu[l] ** a_blob
             s += (gy * w[:, None]).T @ gx
         sky[l] = s
+    return nu, sky, uv
+
+
+def _cells(uv: np.ndarray, nu_l: float, n: int, l: int):
+    """Nearest Fourier cells (ky, kx) of the uv points kept in band l."""
+    sc = uv * nu_l
+    keep = np.all(np.abs(sc) < 0.5, axis=1)
+    kx = np.rint(sc[keep, 0] * n).astype(np.int64)
+    ky = np.rint(sc[keep, 1] * n).astype(np.int64)
+    if kx.size == 0:
+        raise ValueError(f"band {l} has an empty uv coverage")
+    return ky, kx
+
+
+def make_cube(n: int, L: int, n_src: int, n_blob: int, n_uv: int,
+              seed: int, snr_db: float = 20.0,
+              with_delta: bool = True) -> Cube:
+    rng = np.random.default_rng(seed)
+    nu, sky, uv = _draw_sky_uv(n, L, n_src, n_blob, n_uv, rng)
+
+    psf = np.empty((L, n, n), np.float32)
+    dirty = np.empty((L, n, n), np.float32)
+    noise_var = np.empty(L, np.float64)
+    clean = np.empty((L, n, n), np.float64)
+    N = n * n
+    for l in range(L):
         # uv coverage of band l, nearest-cell gridding plus Hermitian mirror
-        sc = uv * nu[l]
-        keep = np.all(np.abs(sc) < 0.5, axis=1)
-        kx = np.rint(sc[keep, 0] * n).astype(np.int64)
-        ky = np.rint(sc[keep, 1] * n).astype(np.int64)
-        if kx.size == 0:
-            raise ValueError(f"band {l} has an empty uv coverage")
+        ky, kx = _cells(uv, nu[l], n, l)
         g = np.zeros((n, n), np.float64)
         np.add.at(g, (ky % n, kx % n), 1.0)
         np.add.at(g, ((-ky) % n, (-kx) % n), 1.0)
@@ -141,6 +161,41 @@ def make_cube(n: int, L: int, n_src: int, n_blob: int, n_uv: int,
         delta = np.zeros((0,), np.float32)
     return Cube(n=n, L=L, sky=sky, psf=psf, dirty=dirty, noise_var=noise_var,
                 delta=delta, nu=nu)
+
+
+@dataclasses.dataclass
+class VisCube:
+    """Gridded visibilities of a synthetic sky (band-major [L][n][n])."""
+    n: int
+    L: int
+    sky: np.ndarray        # float32 [L, n, n], the true cube X*
+    vis: np.ndarray        # complex64 [L, n, n], per-cell sums D_l of the samples
+    weights: np.ndarray    # float32 [L, n, n], per-cell sample counts m_l
+    noise_std: np.ndarray  # float64 [L], per-sample noise std (real and imaginary)
+    nu: np.ndarray         # float64 [L]
+
+
+def make_visibilities(n: int, L: int, n_src: int, n_blob: int, n_uv: int,
+                      seed: int, snr_db: float = 20.0) -> VisCube:
+    rng = np.random.default_rng(seed)
+    nu, sky, uv = _draw_sky_uv(n, L, n_src, n_blob, n_uv, rng)
+    vis = np.zeros((L, n, n), np.complex128)
+    weights = np.zeros((L, n, n), np.float64)
+    noise_std = np.empty(L, np.float64)
+    for l in range(L):
+        ky, kx = _cells(uv, nu[l], n, l)
+        spec = np.fft.fft2(sky[l].astype(np.float64), norm="ortho")
+        s = spec[ky % n, kx % n]
+        var = float(np.mean(np.abs(s) ** 2)) / 10.0 ** (snr_db / 10.0)
+        noise_std[l] = math.sqrt(var / 2.0)
+        w = rng.standard_normal((kx.size, 2))
+        d = s + noise_std[l] * (w[:, 0] + 1j * w[:, 1])
+        np.add.at(vis[l], (ky % n, kx % n), d)
+        np.add.at(vis[l], ((-ky) % n, (-kx) % n), np.conj(d))
+        np.add.at(weights[l], (ky % n, kx % n), 1.0)
+        np.add.at(weights[l], ((-ky) % n, (-kx) % n), 1.0)
+    return VisCube(n=n, L=L, sky=sky, vis=vis.astype(np.complex64),
+                   weights=weights.astype(np.float32), noise_std=noise_std, nu=nu)
 
 
 def make_workload(name: str, **kw) -> Cube:
