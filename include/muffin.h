@@ -135,6 +135,31 @@ MUFFIN_API muffin_status muffin_plan_estimate_bytes(const muffin_params *p,
 MUFFIN_API muffin_status muffin_plan_load_psf(muffin_plan plan, int32_t b0,
                                               int32_t b1, const float *psf);
 
+/*
+ * Visibility-domain data term (Sec. 1: the method applies unchanged when the
+ * direct operator maps the sky to its visibilities).  Reading: the
+ * visibilities of band l sample the unitary 2D DFT U = F / n of x_l on the
+ * n x n grid (nearest cell), and the data term is
+ * 1/2 sum_p |d_p - (U x_l)_{k(p)}|^2; gridded into per-cell sums D_l[k] and
+ * natural weights m_l[k] (sample counts), its gradient for real x is
+ *   F^-1 (m~_l . F x_l) - Re U^H D_l,   m~_l[k] = (m_l[k] + m_l[-k]) / 2.
+ * The call replaces every cube's PSF spectra by h_hat_l = sqrt(m~_l) and
+ * b = H^T y by Re U^H D_l (FP64), and recomputes beta = max m~; a following
+ * muffin_solve / muffin_solve_batch with dirty = NULL then runs Algorithm 2
+ * on this data term from the given X0 (a dirty cube passed to a later call
+ * returns the plan to the image-domain model with the current spectra; a
+ * PSF load replaces them).
+ *   vis     [B][L][n][n][2] float32 (re, im) per-cell sums D, host or device,
+ *           cell (ky, kx) at index ky * n + kx (FFT order, DC at 0);
+ *   weights [B][L][n][n] float32 m >= 0, host or device.
+ * Both are read during the call only.  ADA-PT and the monitor's objective
+ * need a dirty cube (they return EINVAL / ESTATE for this data term).
+ * Errors: EINVAL (NULL, a negative, NaN or Inf weight, all weights of a
+ * cube zero), ENUMERIC (NaN/Inf visibility), ECUDA.
+ */
+MUFFIN_API muffin_status muffin_plan_load_visibilities(muffin_plan plan, const float *vis,
+                                                       const float *weights);
+
 /* on = 1 (default): repeated launch sequences (two plain iterations, one
  * ADA-PT window) are captured once into CUDA graphs and replayed; 0 launches
  * every kernel directly.  Results are identical either way. */

@@ -439,6 +439,23 @@ class Plan:
         keep = []
         native.check(self._lib.muffin_op_synthesis(self._h, _ptr(u, keep), _ptr(x, keep)))
 
+    def load_visibilities(self, vis, weights):
+        """Visibility-domain data term (see ``muffin_plan_load_visibilities``):
+        vis [B][L][n][n] complex per-cell sums (numpy complex or a torch
+        complex64 tensor, or float32 [..., 2] re/im pairs), weights
+        [B][L][n][n] float32 natural weights.  A following ``solve`` with
+        dirty = None runs on this data term."""
+        keep = []
+        if isinstance(vis, np.ndarray) and np.iscomplexobj(vis):
+            vis = np.ascontiguousarray(vis.astype(np.complex64)).view(np.float32)
+        elif hasattr(vis, "is_complex") and vis.is_complex():
+            import torch
+            vis = torch.view_as_real(vis.to(torch.complex64)).contiguous()
+        if isinstance(weights, np.ndarray):
+            weights = np.ascontiguousarray(weights, np.float32)
+        native.check(self._lib.muffin_plan_load_visibilities(
+            self._h, _ptr(vis, keep), _ptr(weights, keep)))
+
     def op_dct(self, x, v, inverse: bool = False):
         keep = []
         native.check(self._lib.muffin_op_dct(self._h, _ptr(x, keep), _ptr(v, keep),

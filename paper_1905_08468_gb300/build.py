@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmuffin.so")
 
-SOURCES = ["fft_conv.cu", "wavelet.cu", "iuwt.cu", "dct.cu", "dct_tc.cu", "dct_f32.cu", "reduce.cu", "monitor.cu", "noise.cu", "plan.cu",
+SOURCES = ["fft_conv.cu", "wavelet.cu", "iuwt.cu", "dct.cu", "dct_tc.cu", "dct_f32.cu", "visibility.cu", "reduce.cu", "monitor.cu", "noise.cu", "plan.cu",
            "serve.cu", "noalloc.cu", "tune.cu", "host_math.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

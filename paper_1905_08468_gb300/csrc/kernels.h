@@ -283,4 +283,12 @@ cudaError_t dct_op_f32(const DctArgs &d, const float *in, float *out, int invers
 int dct_f32_table_len(int L);
 void dct_f32_tables(int L, float2 *tab);
 
+// ------------------------------------------------------------ visibilities (visibility.cu)
+// h_hat = sqrt((m[k] + m[-k]) / 2) of nimg weight images; chk = m with NaN
+// where m < 0
+cudaError_t vis_weights(const float *m, double2 *hh, float *chk, int n, int nimg,
+                        cudaStream_t st);
+// count complex visibilities (re, im float pairs) -> FP64 complex
+cudaError_t vis_to_c64(const float *vis, double2 *out, size_t count, cudaStream_t st);
+
 }  // namespace muffin

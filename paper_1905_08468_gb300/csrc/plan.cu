@@ -675,6 +675,7 @@ muffin_status leave(muffin_plan P, bool sync) {
 }
 
 muffin_status load_psf(muffin_plan P, int b0, int b1, const float *psf) {
+  P->vis_b = false;
   const size_t cnt = (size_t)(b1 - b0) * P->NLc;
   const size_t off = (size_t)b0 * P->NLc;
   const int nimg = (b1 - b0) * P->L;
@@ -699,6 +700,7 @@ muffin_status load_psf(muffin_plan P, int b0, int b1, const float *psf) {
 }
 
 muffin_status load_dirty(muffin_plan P, int b0, int b1, const float *dirty) {
+  P->vis_b = false;
   const size_t cnt = (size_t)(b1 - b0) * P->NLc;
   const size_t off = (size_t)b0 * P->NLc;
   muffin_status s = fetch(P, dirty, P->stage_a + off, cnt);
@@ -913,6 +915,50 @@ muffin_status muffin_plan_estimate_bytes(const muffin_params *p, size_t *bytes) 
   return MUFFIN_OK;
 }
 
+muffin_status muffin_plan_load_visibilities(muffin_plan P, const float *vis,
+                                            const float *weights) {
+  if (!P || !vis || !weights) return fail(MUFFIN_EINVAL, "NULL argument");
+  const size_t cnt = P->NL;
+  const int nimg = P->Lt;
+  muffin_status s = pi::enter(P);
+  if (s != MUFFIN_OK) return s;
+  // weights -> h_hat = sqrt(m~) (FP64), |h_hat|^2 / n^2 for the FP32 gradient, beta
+  s = fetch(P, weights, P->stage_a, cnt);
+  if (s != MUFFIN_OK) return s;
+  CK(vis_weights(P->stage_a, P->hhat, P->stage_b, P->n, nimg, P->ws));
+  s = scan_input(P, P->stage_b, nimg, "the visibility weights (negative counted as NaN)");
+  if (s != MUFFIN_OK) {
+    const std::string msg = muffin_last_error();
+    return fail(MUFFIN_EINVAL, "%s", msg.c_str());
+  }
+  CK(make_kspec(P->hhat, P->kspec, 1.0 / ((double)P->n * P->n), P->n, nimg, P->ws));
+  for (int c = 0; c < P->B; ++c) {
+    CK(max_abs2_c64(P->hhat + (size_t)c * P->NLc, P->NLc, P->dred + 16, P->dred, P->ws));
+    double lip = 0;
+    CK(cudaMemcpyAsync(&lip, P->dred, sizeof(double), cudaMemcpyDeviceToHost, P->ws));
+    CK(cudaStreamSynchronize(P->ws));
+    if (!(lip > 0) || !std::isfinite(lip))
+      return fail(MUFFIN_EINVAL, "the visibility weights of cube %d are all zero", c);
+    P->lips[c] = lip;
+  }
+  // visibilities (re, im pairs) -> b = Re U^H D = Re(unnormalised inverse DFT of D) / n
+  float *vf = reinterpret_cast<float *>(P->w64b);   // 2 cnt floats fit in cnt double2
+  const cudaMemcpyKind k = is_device_ptr(vis) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(vf, vis, 2 * cnt * sizeof(float), k, P->ws));
+  s = scan_input(P, vf, nimg, "the visibilities");
+  if (s == MUFFIN_OK) s = scan_input(P, vf + cnt, nimg, "the visibilities");
+  if (s != MUFFIN_OK) return s;
+  CK(vis_to_c64(vf, P->w64a, cnt, P->ws));
+  CK(fft2d_c64(P->w64a, P->w64b, P->n, nimg, true, P->tw64, P->ws));
+  CK(c64_real_to_f32(P->w64a, P->b, 1.0 / (double)P->n, cnt, P->ws));
+  P->have_b = true;
+  P->vis_b = true;
+  P->have_y = false;
+  s = upload_cube_const(P);
+  if (s == MUFFIN_OK) s = pi::leave(P, true);
+  return s;
+}
+
 muffin_status muffin_plan_load_psf(muffin_plan P, int32_t b0, int32_t b1, const float *psf) {
   if (!P || !psf) return fail(MUFFIN_EINVAL, "NULL argument");
   if (b0 < 0 || b1 > P->B || b0 >= b1) return fail(MUFFIN_EINVAL, "cube range [%d, %d) invalid", b0, b1);
@@ -940,7 +986,8 @@ muffin_status muffin_solve_batch(muffin_plan P, const float *dirty, float *x,
       return fail(MUFFIN_EINVAL, "mu and gamma must be finite and >= 0");
   const bool warm = flags & MUFFIN_WARM;
   if (warm && !P->have_state) return fail(MUFFIN_ESTATE, "no state to continue from");
-  if (!dirty && !(warm && P->have_b)) return fail(MUFFIN_EINVAL, "dirty is NULL");
+  if (!dirty && !(P->have_b && (warm || P->vis_b)))
+    return fail(MUFFIN_EINVAL, "dirty is NULL (and no visibilities are loaded)");
   muffin_status s = pi::enter(P);
   if (s != MUFFIN_OK) return s;
   if (dirty) {

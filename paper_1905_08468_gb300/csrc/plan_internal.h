@@ -102,6 +102,7 @@ struct muffin_plan_s {
 
   std::vector<double> lips, Asum, Amax2, Bsum, Bmax2, psc, mu, gamma;
   bool have_b = false, have_state = false, have_sure_state = false;
+  bool vis_b = false;     // b and the spectra come from loaded visibilities
   long long k_done = 0;
 
   muffin::Prof *pp() { return profiling ? &prof : nullptr; }

@@ -134,6 +134,7 @@ SIGNATURES = {
     "muffin_op_dct": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32]),
     "muffin_plan_estimate_bytes": (c_int32, [ctypes.POINTER(Params), ctypes.POINTER(c_size_t)]),
     "muffin_plan_load_psf": (c_int32, [c_void_p, c_int32, c_int32, c_void_p]),
+    "muffin_plan_load_visibilities": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "muffin_server_params_default": (None, [ctypes.POINTER(ServerParams)]),
     "muffin_server_create": (c_int32, [ctypes.POINTER(ServerParams), c_void_p,
                                        ctypes.POINTER(c_void_p)]),
