@@ -495,6 +495,8 @@ def main() -> None:
     ap.add_argument("--plain", action="store_true",
                     help="plain MUFFIN (Algorithm 2, fixed mu = gamma = --mu) instead of ADA-PT")
     ap.add_argument("--mu", type=float, default=1e-2)
+    ap.add_argument("--schedule", default="",
+                    help="schedule overrides after tuning, e.g. ana_pipe=0,group_order=1")
     ap.add_argument("--precision", default="tf32", choices=["tf32", "fp32"],
                     help="spectral DCT: 3xTF32 tensor-core products (default) or the FP32 "
                          "fast DCT on the CUDA cores")
@@ -656,6 +658,9 @@ def run_gpu(args) -> None:
                   "iter_ms_tuned": ti.ms_best}
     if args.grad_chunk >= 0:
         plan.set_schedule(grad_chunk=args.grad_chunk)
+    if args.schedule:
+        plan.set_schedule(**{k: int(v) for k, v in
+                             (kv.split("=") for kv in args.schedule.split(","))})
     if tuning is not None:
         tuning["schedule"] = plan.schedule()
     if mode == "adapt":

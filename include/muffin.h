@@ -214,15 +214,17 @@ typedef struct {
   int32_t fft_radix;       /* chosen FFT plan */
   int32_t group_order;     /* chosen kernel order of the ADA-PT groups */
   int32_t ana_ring;        /* chosen analysis U staging */
+  int32_t ana_pipe;        /* chosen level-1 analysis kernel */
 } muffin_tune_info;
 
 /* Times each candidate configuration on this plan's own buffers (a few
  * iterations of every chain group it advances: two groups of three chains
  * with sure = 1, one plain group otherwise), keeps the fastest and caches it
- * per shape (n, bands, batch, chains, levels, bases, SM count, device name):
- * in process, and in the text file `cache_path` when it is not NULL (read
- * first, one line "muffin-tune-5 <key> <syn_packed> <dct_ctas> <tcgen05> <grad_chunk>
- * <fft_radix> <group_order> <ana_ring>"
+ * per shape (n, bands, batch, chains, levels, bases, spectral precision, SM
+ * count, device name): in process, and in the text file `cache_path` when it
+ * is not NULL (read first, one line "muffin-tune-6 <key> <syn_packed>
+ * <dct_ctas> <tcgen05> <grad_chunk> <fft_radix> <group_order> <ana_ring>
+ * <ana_pipe>"
  * appended per new shape; lines that do not parse are ignored).  The timing iterations overwrite the plan's iterate state: a
  * following solve or sure_tune must start cold (warm = 0; a warm call
  * returns MUFFIN_ESTATE), and captured graphs are rebuilt.  info may be NULL.
@@ -280,6 +282,13 @@ typedef struct {
                                tiles staged two steps ahead in a shared-memory
                                ring by cp.async (3 CTAs per SM instead of 4;
                                identical results) */
+  int32_t ana_pipe;         /* level-1 analysis of an iteration (levels > 1):
+                               0 (default) = basis-major steps with two
+                               barriers each; 1 = chain-major steps with the
+                               row pass of one step and the column pass +
+                               dual update of the previous one in the same
+                               phase (two lo/hi buffers, one barrier per
+                               step); identical results */
 } muffin_schedule;
 
 /* Reads / sets the schedule (set drops captured graphs and the iterate

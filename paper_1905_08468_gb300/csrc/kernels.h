@@ -223,6 +223,8 @@ struct WaveArgs {
   int dict;                // 0: union of K Daubechies bases, 1: IUWT (K = J + 1 planes)
   int ana_ring;            // analysis of the size-specialised levels: 1 stages the
                            // U detail tiles in a shared-memory ring by cp.async
+  int ana_pipe;            // level-1 analysis (iteration, J > 1): 1 runs the
+                           // chain-major kernel with one barrier per step
   int syn_packed;          // synthesis variant: bit 0 coarse levels, bit 1
                            // level 1 (0 scalar row pass, 1 packed row pairs)
   Prof *prof;              // optional per-kernel timing

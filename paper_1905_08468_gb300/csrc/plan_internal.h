@@ -86,6 +86,7 @@ struct muffin_plan_s {
   bool use_graphs = true;
   int syn_packed = 0;     // synthesis variant bits (see WaveArgs::syn_packed)
   int ana_ring = 0;       // analysis U staging (see WaveArgs::ana_ring)
+  int ana_pipe = 0;       // level-1 analysis kernel (see WaveArgs::ana_pipe)
   int dct_ctas = 0;       // spectral kernel CTAs per SM (0: all resident)
   int dct_tc = 0;         // spectral step on tcgen05 (L = 64)
   int grad_chunk = 0;     // images per pass of the gradient FFTs (0: all at once)
@@ -137,6 +138,7 @@ struct muffin_plan_s {
     for (int j = 0; j < 16; ++j) w.lvl_off[j] = lvl_off[j];
     w.syn_packed = syn_packed;
     w.ana_ring = ana_ring;
+    w.ana_pipe = ana_pipe;
     w.prof = pp();
     return w;
   }

@@ -27,6 +27,7 @@ struct Choice {
   int fft_radix = 16;  // largest radix of the gradient FFT plan
   int group_order = 0; // ADA-PT groups: 0 one after the other, 1 phase by phase, 2 two streams
   int ana_ring = 0;    // analysis U staging in a shared-memory ring
+  int ana_pipe = 0;    // level-1 analysis: chain-major, one barrier per step
 };
 
 std::mutex g_mu;
@@ -49,23 +50,24 @@ std::string shape_key(muffin_plan P) {
   return buf;
 }
 
-// the last line "muffin-tune-4 <key> <syn_packed> <dct_ctas> <dct_tc> <grad_chunk>
-// <fft_radix> <group_order>" with this key
+// the last line "muffin-tune-6 <key> <syn_packed> <dct_ctas> <dct_tc> <grad_chunk>
+// <fft_radix> <group_order> <ana_ring> <ana_pipe>" with this key
 bool file_lookup(const char *path, const std::string &key, Choice *c) {
   FILE *f = std::fopen(path, "r");
   if (!f) return false;
   char line[512], tag[32], k[400];
   bool found = false;
   while (std::fgets(line, sizeof line, f)) {
-    int a = 0, b = 0, t = 0, g = 0, r = 0, o = 0, ar = 0;
-    if (std::sscanf(line, "%31s %399s %d %d %d %d %d %d %d", tag, k, &a, &b, &t, &g, &r, &o,
-                    &ar) != 9)
+    int a = 0, b = 0, t = 0, g = 0, r = 0, o = 0, ar = 0, ap = 0;
+    if (std::sscanf(line, "%31s %399s %d %d %d %d %d %d %d %d", tag, k, &a, &b, &t, &g, &r, &o,
+                    &ar, &ap) != 10)
       continue;
-    if (std::strcmp(tag, "muffin-tune-5") != 0 || key != k) continue;
+    if (std::strcmp(tag, "muffin-tune-6") != 0 || key != k) continue;
     if (a < 0 || a > 3 || b < 0 || t < 0 || t > 1 || g < 0 || (r != 8 && r != 16) ||
-        o < 0 || o > 2 || ar < 0 || ar > 1)
+        o < 0 || o > 2 || ar < 0 || ar > 1 || ap < 0 || ap > 1)
       continue;
     c->ana_ring = ar;
+    c->ana_pipe = ap;
     c->syn_packed = a;
     c->dct_ctas = b;
     c->dct_tc = t;
@@ -81,8 +83,9 @@ bool file_lookup(const char *path, const std::string &key, Choice *c) {
 void file_append(const char *path, const std::string &key, const Choice &c) {
   FILE *f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "muffin-tune-5 %s %d %d %d %d %d %d %d\n", key.c_str(), c.syn_packed,
-               c.dct_ctas, c.dct_tc, c.grad_chunk, c.fft_radix, c.group_order, c.ana_ring);
+  std::fprintf(f, "muffin-tune-6 %s %d %d %d %d %d %d %d %d\n", key.c_str(), c.syn_packed,
+               c.dct_ctas, c.dct_tc, c.grad_chunk, c.fft_radix, c.group_order, c.ana_ring,
+               c.ana_pipe);
   std::fclose(f);
 }
 
@@ -94,6 +97,7 @@ void apply(muffin_plan P, const Choice &c) {
   P->fft_radix = P->n >= 64 ? c.fft_radix : 16;
   P->group_order = P->p.sure ? c.group_order : 0;
   P->ana_ring = c.ana_ring;
+  P->ana_pipe = c.ana_pipe;
 }
 
 // mean time of one iteration of every chain group with choice c
@@ -185,6 +189,15 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
     ++cand;
     if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
   }
+  // the other level-1 analysis kernel (iterations with more than one level)
+  if (P->J > 1 && P->dict == 0 && s == MUFFIN_OK) {
+    Choice c = *best;
+    c.ana_pipe = 1 - c.ana_pipe;
+    double t = 0.0;
+    s = time_choice(P, c, reps, e0, e1, &t);
+    ++cand;
+    if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
+  }
   // the analysis U ring, where the size-specialised analysis runs
   if ((P->n == 512 || P->n == 1024 || P->n == 2048) && P->J > 1 && P->dict == 0 &&
       s == MUFFIN_OK) {
@@ -260,6 +273,7 @@ muffin_status muffin_plan_get_schedule(muffin_plan P, muffin_schedule *s) {
   s->fft_radix = P->fft_radix;
   s->group_order = P->group_order;
   s->ana_ring = P->ana_ring;
+  s->ana_pipe = P->ana_pipe;
   return MUFFIN_OK;
 }
 
@@ -268,7 +282,7 @@ muffin_status muffin_plan_set_schedule(muffin_plan P, const muffin_schedule *s) 
   if (s->syn_packed < 0 || s->syn_packed > 3 || s->dct_ctas_per_sm < 0 || s->grad_chunk < 0 ||
       (s->spectral_tcgen05 != 0 && s->spectral_tcgen05 != 1) ||
       (s->fft_radix != 16 && s->fft_radix != 8) || s->group_order < 0 || s->group_order > 2 ||
-      s->ana_ring < 0 || s->ana_ring > 1)
+      s->ana_ring < 0 || s->ana_ring > 1 || s->ana_pipe < 0 || s->ana_pipe > 1)
     return fail(MUFFIN_EINVAL, "schedule value out of range");
   if (s->spectral_tcgen05 && P->L != 64)
     return fail(MUFFIN_EINVAL, "the tcgen05 spectral kernel needs 64 bands (plan has %d)", P->L);
@@ -282,6 +296,7 @@ muffin_status muffin_plan_set_schedule(muffin_plan P, const muffin_schedule *s) 
   P->fft_radix = P->n >= 64 ? s->fft_radix : 16;
   P->group_order = P->p.sure ? s->group_order : 0;
   P->ana_ring = s->ana_ring;
+  P->ana_pipe = s->ana_pipe;
   return MUFFIN_OK;
 }
 
@@ -312,6 +327,7 @@ muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin
       info->fft_radix = P->fft_radix;
       info->group_order = P->group_order;
       info->ana_ring = P->ana_ring;
+      info->ana_pipe = P->ana_pipe;
       info->from_cache = 1;
     }
     return MUFFIN_OK;
@@ -334,6 +350,7 @@ muffin_status muffin_plan_autotune(muffin_plan P, const char *cache_path, muffin
     info->fft_radix = P->fft_radix;
     info->group_order = P->group_order;
     info->ana_ring = P->ana_ring;
+    info->ana_pipe = P->ana_pipe;
     info->from_cache = 0;
   }
   return MUFFIN_OK;

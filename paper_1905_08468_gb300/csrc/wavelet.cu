@@ -435,6 +435,105 @@ __global__ void __launch_bounds__(NT, RING ? 3 : 4) k_ana(AnaArgs a) {
   }
 }
 
+// Level-1 analysis + dual update, pipelined: steps run chain-major (chain
+// s / K, basis s % K), and one phase holds the row pass of step s and the
+// column pass + dual update of step s - 1, with two lo/hi buffers and one
+// barrier per step, so the threads that have no row-pass item (short
+// filters) go straight to the column work.  Only z0 and one derivative
+// chain's input tile are resident (the second tile holds chain 1's input,
+// then chain 2's), and chain 0's masks of every basis stay in a 64-bit
+// register (8 bits per basis), so shared memory stays at 4 CTAs per SM.  The
+// U values of a step are requested one phase ahead.  The row and column
+// passes, the inputs and the dual update are k_ana's, so the results are
+// bit-identical.  Not the last level (J > 1).
+constexpr size_t ana_pipe_smem(int ch) {
+  return ((size_t)(ch == 3 ? 2 : 1) * A_RP * A_IP + 4 * A_RP * A_LP) * sizeof(float2);
+}
+
+template <int CH, int NS, int MS>
+__global__ void __launch_bounds__(NT, 4) k_ana_pipe(AnaArgs a) {
+  static_assert(CH == 1 || CH == 3, "one or three chains");
+  extern __shared__ float2 smem2[];
+  constexpr int TILE = A_RP * A_IP, LH = A_RP * A_LP;
+  float2 *in0 = smem2;                           // chain 0: z0
+  float2 *in1 = in0 + (CH == 3 ? TILE : 0);      // chain 1, then chain 2
+  float2 *lohi = in0 + (CH == 3 ? 2 : 1) * TILE; // [2 buffers][lo, hi]
+  const int n = NS ? NS : a.n, M = MS ? MS : a.M;
+  const int h = M >> 1;
+  const int ntx = (h + TX - 1) / TX;
+  const int kx0 = (blockIdx.x % ntx) * TX, ky0 = (blockIdx.x / ntx) * TY;
+  const int l = blockIdx.y;
+  const int K = a.K;
+  const int RP = TY + K - 1, RW = 2 * TX + 2 * K - 2;
+  const int Mm = M - 1;
+  const size_t NN = (size_t)n * n;
+  const size_t CS = (size_t)a.L * NN;
+  const DevScalars &S = a.sc[l / a.Lc];
+  const float mu = (float)S.mu;
+  const float sbl = (float)(S.sigma * (double)a.beta[l]);
+  auto zval = [&](int c, size_t pix) { return 2.f * a.xt[c * CS + pix] - a.x[c * CS + pix]; };
+  // z0 into in0 and (three chains) z0 + mu z1 into in1
+  for (int it = threadIdx.x; it < RP * RW; it += NT) {
+    const int rp = it / RW, cc = it - rp * RW;
+    const int xx = (2 * kx0 + cc) & Mm;
+    float z0[2], w1[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int yy = (2 * ky0 + 2 * rp + e) & Mm;
+      const size_t pix = (size_t)l * NN + (size_t)yy * n + xx;
+      z0[e] = zval(0, pix);
+      if (CH == 3) w1[e] = fmaf(mu, zval(1, pix), z0[e]);
+    }
+    in0[rp * A_IP + cc] = make_float2(z0[0], z0[1]);
+    if (CH == 3) in1[rp * A_IP + cc] = make_float2(w1[0], w1[1]);
+  }
+  const int nsteps = K * CH;
+  uint64_t keep = 0;
+  float pre[4][QY];
+  ana_prefetch<WAVE_ITERATE, NS, MS>(a, l, 0, 0, kx0, ky0, pre);
+  __syncthreads();
+#pragma unroll 1
+  for (int s = 0; s <= nsteps; ++s) {
+    if (CH == 3 && s == 2 * K) {
+      // chain 2's input replaces chain 1's (whose last row pass ended before
+      // the previous barrier)
+      for (int it = threadIdx.x; it < RP * RW; it += NT) {
+        const int rp = it / RW, cc = it - rp * RW;
+        const int xx = (2 * kx0 + cc) & Mm;
+        float z2[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int yy = (2 * ky0 + 2 * rp + e) & Mm;
+          z2[e] = zval(2, (size_t)l * NN + (size_t)yy * n + xx);
+        }
+        in1[rp * A_IP + cc] = make_float2(z2[0], z2[1]);
+      }
+      __syncthreads();
+    }
+    if (s < nsteps) {
+      const int c = s / K, bb = s - c * K;
+      float2 *lh = lohi + (s & 1) * 2 * LH;
+      ana_rows_dispatch(bb + 1, c == 0 ? in0 : in1, lh, lh + LH);
+    }
+    if (s >= 1) {
+      const int t = s - 1, c = t / K, bb = t - c * K;
+      const float2 *lh = lohi + (t & 1) * 2 * LH;
+      float cf[4][QY];
+      ana_cols_dispatch(bb + 1, lh, lh + LH, cf);
+      // dual step scale: sigma mu_l (primal, d/dgamma), sigma beta_l (d/dmu)
+      const float qc = c == 1 ? sbl : sbl * mu;
+      uint32_t kb = c == 0 ? 0u : (uint32_t)(keep >> (8 * bb)) & 0xffu;
+      ana_emit_step<WAVE_ITERATE, NS, MS>(a, l, bb, c, kx0, ky0, qc, cf, pre, kb);
+      if (c == 0) keep |= (uint64_t)kb << (8 * bb);
+      if (s < nsteps) {
+        const int c2 = s / K;
+        ana_prefetch<WAVE_ITERATE, NS, MS>(a, l, s - c2 * K, c2, kx0, ky0, pre);
+      }
+    }
+    if (s < nsteps) __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------ synthesis
 // Inverse of one level: lo/hi along y from (LL, DY) and (DX, HH), then the
 // rows.  x[2k+e] = sum_s h[2s+e] a[k-s] + g[2s+e] d[k-s] (transpose of the
@@ -948,6 +1047,24 @@ cudaError_t launch_ana(const AnaArgs &a, int nblk_y, cudaStream_t st, Prof *prof
   return cudaGetLastError();
 }
 
+template <int CH, int NS, int MS>
+cudaError_t launch_ana_pipe(const AnaArgs &a, int nblk_y, cudaStream_t st, Prof *prof) {
+  const double h = a.M >> 1;
+  const double in = (double)CH * a.L * a.M * a.M * 8.0;
+  const double det = (double)CH * a.L * a.K * 3.0 * h * h * 4.0 * 2.0;
+  const double ll = (double)CH * a.L * a.K * h * h * 4.0;
+  ProfScope ps(prof, "ana_level1_dual", in + det + ll, level_flops(CH, a.L, a.K, (int)h), st);
+  constexpr size_t smem = ana_pipe_smem(CH);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_ana_pipe<CH, NS, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr = true;
+  }
+  k_ana_pipe<CH, NS, MS><<<dim3(tiles(a.M >> 1), nblk_y), NT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 // the size-specialised analysis launch, with or without the U ring
 template <int CH, int MODE, bool L1, int NS, int MS>
 cudaError_t launch_ana_sized(const AnaArgs &a, int nblk_y, bool ring, cudaStream_t st,
@@ -1025,7 +1142,18 @@ cudaError_t analysis_all(const WaveArgs &w, const AnaArgs &base, cudaStream_t st
   a.ll_out = a.last ? nullptr : w.scratch + w.lvl_off[1];
   // the size-specialised kernels assume a level below (J > level)
   const bool ring = w.ana_ring != 0;
-  cudaError_t e = (w.n == 2048 && w.J > 1) ? launch_ana_sized<CH, MODE, true, 2048, 2048>(a, w.L, ring, st, w.prof)
+  cudaError_t e = cudaSuccess;
+  bool piped = false;
+  if constexpr (MODE == WAVE_ITERATE && (CH == 1 || CH == 3)) {
+    if (w.ana_pipe && w.J > 1) {
+      piped = true;
+      e = w.n == 2048 ? launch_ana_pipe<CH, 2048, 2048>(a, w.L, st, w.prof)
+          : w.n == 1024 ? launch_ana_pipe<CH, 1024, 1024>(a, w.L, st, w.prof)
+          : w.n == 512 ? launch_ana_pipe<CH, 512, 512>(a, w.L, st, w.prof)
+                       : launch_ana_pipe<CH, 0, 0>(a, w.L, st, w.prof);
+    }
+  }
+  if (!piped) e = (w.n == 2048 && w.J > 1) ? launch_ana_sized<CH, MODE, true, 2048, 2048>(a, w.L, ring, st, w.prof)
                   : (w.n == 1024 && w.J > 1) ? launch_ana_sized<CH, MODE, true, 1024, 1024>(a, w.L, ring, st, w.prof)
                   : (w.n == 512 && w.J > 1) ? launch_ana_sized<CH, MODE, true, 512, 512>(a, w.L, ring, st, w.prof)
                                             : launch_ana<CH, MODE, true>(a, w.L, st, w.prof);

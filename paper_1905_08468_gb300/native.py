@@ -61,13 +61,15 @@ class TuneInfo(ctypes.Structure):
                 ("spectral_tcgen05", c_int32),
                 ("from_cache", c_int32), ("candidates", c_int32),
                 ("ms_default", c_double), ("ms_best", c_double), ("grad_chunk", c_int32),
-                ("fft_radix", c_int32), ("group_order", c_int32), ("ana_ring", c_int32)]
+                ("fft_radix", c_int32), ("group_order", c_int32), ("ana_ring", c_int32),
+                ("ana_pipe", c_int32)]
 
 
 class Schedule(ctypes.Structure):
     _fields_ = [("syn_packed", c_int32), ("dct_ctas_per_sm", c_int32),
                 ("spectral_tcgen05", c_int32), ("grad_chunk", c_int32),
-                ("fft_radix", c_int32), ("group_order", c_int32), ("ana_ring", c_int32)]
+                ("fft_radix", c_int32), ("group_order", c_int32), ("ana_ring", c_int32),
+                ("ana_pipe", c_int32)]
 
 
 class KernelStat(ctypes.Structure):

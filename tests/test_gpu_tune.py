@@ -91,6 +91,38 @@ def test_analysis_ring_bit_identical(sure):
         assert np.array_equal(res[0][3][k], res[1][3][k]), k
 
 
+@pytest.mark.parametrize("n,L,sure,levels", [(512, 2, False, 3), (512, 2, True, 3),
+                                             (1024, 2, True, 3), (2048, 1, False, 2),
+                                             (64, 8, True, 3), (64, 8, False, 3),
+                                             (32, 4, True, 1)])
+def test_analysis_pipe_bit_identical(n, L, sure, levels):
+    """The chain-major level-1 analysis with one barrier per step gives the
+    same bits as the basis-major kernel: size-specialised (512, 1024, 2048 px)
+    and run-time sizes, one and three chains; with one level the plan keeps
+    the basis-major kernel (the setting has no effect)."""
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    c = make_cube(n, L, max(4, n // 16), 2, 12 * n, seed=900 + n + L)
+    eps = fdmc_eps(c.noise_var)
+    res = []
+    for pipe in (0, 1):
+        x = torch.zeros((c.L, c.n, c.n), device="cuda")
+        with pkg.Plan(c.n, c.L, c.psf, sure=sure, levels=levels) as p:
+            p.set_schedule(ana_pipe=pipe)
+            assert p.schedule()["ana_pipe"] == pipe
+            if sure:
+                th, tr, _ = p.sure_tune(dev(c.dirty, torch), dev(c.delta, torch), c.noise_var, x,
+                                        (1e-2, 1e-2), 7, window=3, eta=(2e-3, 2e-2), eps=eps)
+            else:
+                p.solve(dev(c.dirty, torch), x, 5, 1e-2, 1e-2)
+                th, tr = None, None
+            st = p.state_arrays()
+        res.append((x, th, tr, st))
+    assert torch.equal(res[0][0], res[1][0]) and res[0][1] == res[1][1] and res[0][2] == res[1][2]
+    for k in ("x", "u", "v", "t"):
+        assert np.array_equal(res[0][3][k], res[1][3][k]), k
+
+
 def test_group_order_bit_identical():
     """ADA-PT: the two chain groups' kernels phase by phase, or concurrently
     on two streams, give the same bits as group after group."""
@@ -143,7 +175,8 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         x = torch.zeros_like(ref)
         p.solve(dev(c.dirty, torch), x, 3, 1e-2, 2e-2)
         info = p.autotune(str(cache))
-        assert info.from_cache == 0 and info.candidates == 7    # 4 syn, 2 grids, radix 8
+        # default, 3 more syn variants, 2 grids, radix 8, the other analysis kernel
+        assert info.from_cache == 0 and info.candidates == 8
         assert 0 <= info.syn_packed <= 3 and info.dct_ctas_per_sm >= 0
         assert 0 < info.ms_best <= info.ms_default
         # the timing iterations replaced the iterate state: no warm start
@@ -154,7 +187,8 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         p.solve(dev(c.dirty, torch), x, 13, 1e-2, 2e-2)
         assert torch.equal(x, ref)
     lines = [ln.split() for ln in cache.read_text().splitlines()]
-    assert len(lines) == 1 and lines[0][0] == "muffin-tune-5" and "n=64,L=8" in lines[0][1]
+    assert len(lines) == 1 and lines[0][0] == "muffin-tune-6" and "n=64,L=8" in lines[0][1]
+    assert len(lines[0]) == 10
     # the same shape again: in-process cache
     with pkg.Plan(64, 8, c.psf) as p:
         again = p.autotune(str(cache))
@@ -162,13 +196,14 @@ def test_autotune_choice_state_and_file_cache(tmp_path):
         assert (again.syn_packed, again.dct_ctas_per_sm) == (info.syn_packed, info.dct_ctas_per_sm)
     # a shape only the file knows (written by hand), beside lines to ignore
     key = lines[0][1].replace("n=64,L=8", "n=16,L=8")
-    cache.write_text("garbage line\nmuffin-tune-5 %s 9 1 0 0 16 0 0\nmuffin-tune-4 %s 3 2 0 1 16 0\n"
-                     "muffin-tune-5 %s 2 1 0 3 8 0 0\n" % (key, key, key))
+    cache.write_text("garbage line\nmuffin-tune-6 %s 9 1 0 0 16 0 0 0\nmuffin-tune-5 %s 3 2 0 1 16 0 0\n"
+                     "muffin-tune-6 %s 2 1 0 3 8 0 0 1\n" % (key, key, key))
     c16 = make_cube(16, 8, 4, 1, 480, seed=841)
     with pkg.Plan(16, 8, c16.psf) as p:
         got = p.autotune(str(cache))
         assert got.from_cache == 1
         assert (got.syn_packed, got.dct_ctas_per_sm, got.grad_chunk) == (2, 1, 3)
+        assert got.ana_pipe == 1 and p.schedule()["ana_pipe"] == 1
         # a 16 px side has no radix-8 plan: the cached radix falls back to 16
         assert p.schedule()["grad_chunk"] == 3 and p.schedule()["fft_radix"] == 16
 
