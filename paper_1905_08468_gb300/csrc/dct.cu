@@ -204,6 +204,8 @@ __global__ void __launch_bounds__(NTHR) k_dct(DctKArgs a) {
   const size_t cb = (size_t)cube * L * N;    // the cube's first band
   const float *__restrict__ alpha = a.alpha + (size_t)cube * N;
 
+  // loads of several rounds in flight before their first use
+#pragma unroll 8
   for (int it = threadIdx.x; it < Lp * PT; it += NTHR) {
     const int l = it / PT, p = it - l * PT;
     const size_t pix = n0 + p;

@@ -79,7 +79,7 @@ __device__ __forceinline__ int mpos(int l) {
 }
 
 template <int L, int CH, int MODE>
-__global__ void __launch_bounds__(FT) k_dct_f32(F32Args a) {
+__global__ void __launch_bounds__(FT, 2) k_dct_f32(F32Args a) {
   using S = FShape<L>;
   constexpr int NB = S::NB, PT = S::PT, PITCH = S::PITCH;
   extern __shared__ float2 fsm[];
@@ -105,6 +105,9 @@ __global__ void __launch_bounds__(FT) k_dct_f32(F32Args a) {
 
   // ---- z of every band of the tile, reordered
   if (!inv_op) {
+    // loads of several rounds in flight before their first use
+    constexpr int UNR = CH == 3 ? 3 : 8;
+#pragma unroll UNR
     for (int it = tid; it < L * NB; it += FT) {
       const int s = it % NB, l = it / NB;
       const size_t pix = n0 + 2 * s;
@@ -236,6 +239,7 @@ __global__ void __launch_bounds__(FT) k_dct_f32(F32Args a) {
   for (int c = 0; c < CH; ++c) fft_inplace<L, true>(dat + c * NB * PITCH, NB, PITCH, tw);
 
   // ---- back in band order: t (iteration) or C^T in (operator)
+#pragma unroll 4
   for (int it = tid; it < L * NB; it += FT) {
     const int s = it % NB, l = it / NB;
     const size_t pix = n0 + 2 * s;
