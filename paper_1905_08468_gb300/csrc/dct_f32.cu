@@ -132,6 +132,31 @@ __global__ void __launch_bounds__(FT, 2) k_dct_f32(F32Args a) {
 #pragma unroll
       for (int c = 0; c < CH; ++c) dat[c * NB * PITCH + o] = z[c];
     }
+  }
+  // one chain: the old duals and the pixel weights of this thread's tasks,
+  // requested now so that their latency is covered by the forward DFT
+  // (three chains have no registers to spare for it)
+  constexpr bool PREF = MODE == WAVE_ITERATE && CH == 1;
+  constexpr int PF = PREF ? S::TPT : 1;
+  float2 pv1[PF], pv2[PF], pal[PF];
+  if constexpr (PREF) {
+#pragma unroll
+    for (int r = 0; r < S::TPT; ++r) {
+      const int it = tid + r * FT;
+      pv1[r] = pv2[r] = pal[r] = make_float2(0.f, 0.f);
+      if (it < S::NTASK) {
+        const int s = it % NB, kk = it / NB;
+        const int k1 = kk, k2 = kk ? L - kk : L / 2;
+        const size_t pix = n0 + 2 * s;
+        if (pix < N) {
+          pv1[r] = ld2(a.v + cb + (size_t)k1 * N + pix);
+          pv2[r] = ld2(a.v + cb + (size_t)k2 * N + pix);
+          pal[r] = ld2(alpha + pix);
+        }
+      }
+    }
+  }
+  if (!inv_op) {
     __syncthreads();
 #pragma unroll 1
     for (int c = 0; c < CH; ++c) fft_inplace<L, false>(dat + c * NB * PITCH, NB, PITCH, tw);
@@ -181,12 +206,20 @@ __global__ void __launch_bounds__(FT, 2) k_dct_f32(F32Args a) {
         Y1 = valid ? ld2(a.in + cb + (size_t)k1 * N + pix) : make_float2(0.f, 0.f);
         Y2 = valid ? ld2(a.in + cb + (size_t)k2 * N + pix) : make_float2(0.f, 0.f);
       } else {
-        const float2 al = valid ? ld2(alpha + pix) : make_float2(0.f, 0.f);
+        float2 al;
+        if constexpr (PREF) al = pal[r];
+        else al = valid ? ld2(alpha + pix) : make_float2(0.f, 0.f);
         const float sa = (c == 2) ? sigma : sigma * gamma;
         float *v1p = a.v + c * CS + cb + (size_t)k1 * N + pix;
         float *v2p = a.v + c * CS + cb + (size_t)k2 * N + pix;
-        const float2 o1 = valid ? ld2(v1p) : make_float2(0.f, 0.f);
-        const float2 o2 = valid ? ld2(v2p) : make_float2(0.f, 0.f);
+        float2 o1, o2;
+        if constexpr (PREF) {
+          o1 = pv1[r];
+          o2 = pv2[r];
+        } else {
+          o1 = valid ? ld2(v1p) : make_float2(0.f, 0.f);
+          o2 = valid ? ld2(v2p) : make_float2(0.f, 0.f);
+        }
         float vt[4] = {fmaf(sa * al.x, X1.x, o1.x), fmaf(sa * al.y, X1.y, o1.y),
                        fmaf(sa * al.x, X2.x, o2.x), fmaf(sa * al.y, X2.y, o2.y)};
         float vn[4];

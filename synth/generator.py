@@ -51,6 +51,7 @@ WORKLOADS = {
     "prof_512x512x32": (512, 32, 500, 25, 50000, 6),
     "prof_512x512x64": (512, 64, 500, 25, 50000, 7),
     "prof_256x256x64": (256, 64, 125, 6, 12500, 8),
+    "prof_256x256x256": (256, 256, 125, 6, 12500, 9),
 }
 
 
