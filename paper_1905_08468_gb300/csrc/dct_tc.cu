@@ -114,6 +114,20 @@ __device__ __forceinline__ void stage_raw(const float *xt, const float *x, size_
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
+// the band rows stage_raw will read for (base, p0), into L2 ahead of time:
+// one bulk prefetch per (band, array), 16-byte aligned (p0 is a multiple of
+// the 128-pixel tile) and cut at the end of the pixel range
+__device__ __forceinline__ void prefetch_raw(const float *xt, const float *x, size_t base,
+                                             size_t N, size_t p0, int gt) {
+  if (gt >= 2 * TL || p0 >= N) return;
+  const size_t cnt = (N - p0 < (size_t)TM ? N - p0 : (size_t)TM) & ~(size_t)3;
+  if (cnt == 0) return;
+  const int l = gt >> 1;
+  const float *src = (gt & 1 ? x : xt) + base + (size_t)l * N + p0;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"((uint32_t)(cnt * 4))
+               : "memory");
+}
+
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(GT) : "memory");
 }
@@ -262,6 +276,15 @@ __global__ void __launch_bounds__(CTA_T, 1) k_dct_tc(TcArgs a) {
       const size_t p0 = p - row;
       float z[32];
       stage_raw(a.xt + c * CS, a.x + c * CS, tile_base, N, p0, gt, ahi, alo);
+      {   // the next (tile, chain) of this group, into L2 while this one runs
+        const int nt = c + 1 < CH ? tile : tile + (int)gridDim.x * NG;
+        const int nc = c + 1 < CH ? c + 1 : 0;
+        if (nt < ntiles) {
+          const int ncube = nt / tpc;
+          prefetch_raw(a.xt + nc * CS, a.x + nc * CS, (size_t)ncube * TL * N, N,
+                       (size_t)(nt - ncube * tpc) * TM, gt);
+        }
+      }
       asm volatile("cp.async.wait_group 0;" ::: "memory");
       group_sync(g);
 #pragma unroll
