@@ -189,20 +189,21 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
     ++cand;
     if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
   }
-  // the other level-1 analysis kernel (iterations with more than one level)
-  if (P->J > 1 && P->dict == 0 && s == MUFFIN_OK) {
-    Choice c = *best;
-    c.ana_pipe = 1 - c.ana_pipe;
-    double t = 0.0;
-    s = time_choice(P, c, reps, e0, e1, &t);
-    ++cand;
-    if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
-  }
   // the analysis U ring, where the size-specialised analysis runs
   if ((P->n == 512 || P->n == 1024 || P->n == 2048) && P->J > 1 && P->dict == 0 &&
       s == MUFFIN_OK) {
     Choice c = *best;
     c.ana_ring = 1;
+    double t = 0.0;
+    s = time_choice(P, c, reps, e0, e1, &t);
+    ++cand;
+    if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
+  }
+  // the other level-1 analysis kernel (iterations with more than one level),
+  // after the ring so that the pair is judged with the ring choice in place
+  if (P->J > 1 && P->dict == 0 && s == MUFFIN_OK) {
+    Choice c = *best;
+    c.ana_pipe = 1 - c.ana_pipe;
     double t = 0.0;
     s = time_choice(P, c, reps, e0, e1, &t);
     ++cand;
