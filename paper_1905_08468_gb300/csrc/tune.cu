@@ -200,7 +200,7 @@ muffin_status tune(muffin_plan P, Choice *best, muffin_tune_info *info) {
     if (s == MUFFIN_OK && t < t_best) { t_best = t; *best = c; }
   }
   // the other level-1 analysis kernel (iterations with more than one level),
-  // after the ring so that the pair is judged with the ring choice in place
+  // after the ring, so that it is timed with the ring choice in place
   if (P->J > 1 && P->dict == 0 && s == MUFFIN_OK) {
     Choice c = *best;
     c.ana_pipe = 1 - c.ana_pipe;
