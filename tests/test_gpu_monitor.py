@@ -29,13 +29,16 @@ def weighted_problem(c, seed=5):
     return prob, alpha.astype(np.float32), beta.astype(np.float32)
 
 
-def test_objective_matches_oracle():
+@pytest.mark.parametrize("precision", ["tf32", "fp32"])
+def test_objective_matches_oracle(precision):
+    """Eqs. probopt + RegAll with weights; with precision fp32 the spectral
+    term's DCT is the FP32 fast transform."""
     torch = cuda()
     import paper_1905_08468_gb300 as pkg
     c = make_cube(32, 8, 10, 2, 800, seed=71)
     prob, alpha, beta = weighted_problem(c)
     x = np.abs(np.random.default_rng(3).standard_normal(c.dirty.shape)).astype(np.float32) * 0.1
-    with pkg.Plan(c.n, c.L, c.psf, alpha=alpha.ravel(), beta=beta) as plan:
+    with pkg.Plan(c.n, c.L, c.psf, alpha=alpha.ravel(), beta=beta, precision=precision) as plan:
         for mu, gamma in ((1e-2, 2e-2), (0.0, 0.0), (0.3, 0.0)):
             f = plan.objective(dev(c.dirty, torch), dev(x, torch), mu, gamma)
             ref = om.objective(x.astype(np.float64), prob, mu, gamma)
