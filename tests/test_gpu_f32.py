@@ -109,6 +109,14 @@ def test_fp32_rejections():
     with pytest.raises(ValueError):
         pkg.Plan(8, 64, psf, precision="fp16")
     assert pkg.estimate_bytes(8, 64, precision="fp32") > pkg.estimate_bytes(8, 64)
+    # the footprint estimate is exact for FP32-precision plans too
+    for n, L, sure, batch in [(16, 64, True, 1), (32, 256, False, 2), (8, 2, False, 1)]:
+        psf = np.zeros((batch, L, n, n), np.float32)
+        psf[:, :, 0, 0] = 1
+        with pkg.Plan(n, L, psf if batch > 1 else psf[0], sure=sure, batch=batch,
+                      precision="fp32") as p:
+            assert p.device_bytes == pkg.estimate_bytes(n, L, sure=sure, batch=batch,
+                                                        precision="fp32")
 
 
 def test_tau_override_plain_and_adapt():
