@@ -12,7 +12,9 @@ at 2048 fixed voxels, its per-band norms and 32 Rademacher projections
   theta and every window's SUGAR and PSURE.
 
 Tolerances: cube relative L2 1e-5 (on the sampled voxels, and as estimated
-from the projections), theta 1e-3, SUGAR/PSURE 1e-3.
+from the projections), theta 1e-3, SUGAR/PSURE 1e-3.  The plain runs are
+repeated with the FP32 spectral step (precision "fp32") against the same
+stored oracle runs.
 """
 import json
 import os
@@ -48,14 +50,15 @@ def check_cube(x, s, tol=1e-5):
     assert e["band_norm"] <= tol, e
 
 
+@pytest.mark.parametrize("precision", ["tf32", "fp32"])
 @pytest.mark.parametrize("key", ["c2", "c5crop"])
-def test_plain_long_run(key):
+def test_plain_long_run(key, precision):
     torch = cuda()
     import paper_1905_08468_gb300 as pkg
     g = golden(key)
     c = make_workload(g["workload"])
     x = dev(np.zeros_like(c.dirty), torch)
-    with pkg.Plan(c.n, c.L, c.psf) as plan:
+    with pkg.Plan(c.n, c.L, c.psf, precision=precision) as plan:
         info = plan.solve(dev(c.dirty, torch), x, g["iters"], g["mu"], g["gamma"])
     assert info.tau == pytest.approx(g["tau"], rel=1e-12)
     check_cube(host(x), g["x"])
