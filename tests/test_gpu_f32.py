@@ -62,6 +62,35 @@ def test_plain_fp32_matches_oracle_and_tf32(n, L, iters):
     assert rel_l2(xs["fp32"], xs["tf32"]) <= 1e-5
 
 
+@pytest.mark.parametrize("n,L,levels,sure", [(16, 2, 3, True), (4, 1024, 2, False),
+                                             (8, 512, 3, True)])
+def test_fp32_band_count_extremes(n, L, levels, sure):
+    """The iteration at the smallest and largest band counts of the FP32
+    step (one task per pixel pair at L = 2; 8-pixel tiles at L = 1024)."""
+    torch = cuda()
+    import paper_1905_08468_gb300 as pkg
+    from oracle import sure as osure
+    from synth import fdmc_eps
+    c = make_cube(n, L, 2, 1, 20 * n, seed=4500 + L)
+    prob = om.make_problem(c.dirty, c.psf, J=levels)
+    x = torch.zeros((L, n, n), device="cuda")
+    with pkg.Plan(n, L, c.psf, levels=levels, sure=sure, precision="fp32") as p:
+        if sure:
+            eps = fdmc_eps(c.noise_var)
+            th, _, _ = p.sure_tune(dev(c.dirty, torch), dev(c.delta, torch), c.noise_var, x,
+                                   (0.05, 0.05), 10, window=5, eta=(2e-5, 2e-4), eps=eps)
+            ref = osure.ada_pt(prob, c.delta, eps, c.noise_var, (0.05, 0.05), 10, Delta=5,
+                               eta=(2e-5, 2e-4))
+            refx = ref.x
+            assert np.max(np.abs(np.array(th) / ref.theta - 1)) <= 1e-3
+        else:
+            p.solve(dev(c.dirty, torch), x, 15, 1e-2, 2e-2)
+            refx = om.solve(prob, 1e-2, 2e-2, 15)[0].x
+    e = rel_l2(host(x), refx)
+    print(f"fp32 {n}^2 x {L} sure={sure}: {e:.1e}")
+    assert e <= 1e-5
+
+
 def test_adapt_fp32_states_match_oracle():
     """ADA-PT with the FP32 spectral step: every chain's X, U, V, T element by
     element against the oracle (64 bands, so the d/dgamma chain's spectral
